@@ -1,0 +1,442 @@
+/*
+ * FP64 CPU oracle for the variable-density pressure-Poisson solve.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the package's smoke check and the CPU
+ * baseline leg of the benchmark do.  It shares no code with the CUDA path.
+ *
+ * The paper (Section 2) fixes a staggered-grid, finite-difference,
+ * fractional-step projection method: vectors on faces, scalars at cell
+ * centres, a level set phi that is positive in gas and negative in liquid
+ * (Fig. 2 caption), variable density from phi (varDens configuration,
+ * Section 3) and a multigrid Poisson solve (Grid_solvePoisson, Section 3).
+ * It prints no formulas for the solve; the discretisation written out here
+ * is the published ghost-fluid method for a variable-coefficient Poisson
+ * equation with a pressure jump [p] = sigma*kappa across the interface
+ * (Liu, Fedkiw & Kang 2000; Kang, Fedkiw & Liu 2000):
+ *
+ *   A p = b,  (A p)_c = sum_faces beta_f (p_nb - p_c) / h^2,
+ *   b = rhs + J - mean(rhs + J),   gauge mean(p) = 0.
+ *
+ * Storage here is deliberately different from the CUDA path: every axis
+ * keeps n+1 faces (face f between cells f-1 and f); on a periodic axis
+ * faces 0 and n are the same physical face, on a wall axis both are walls
+ * with beta = 0.  Cell arrays are (nz, ny, nx), x fastest.
+ *
+ * Entry points are plain loops, one formula at a time; nothing is blocked,
+ * fused or reordered beyond the definitions.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define IDX(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)ny * (size_t)(k)))
+/* face arrays: fx (nz, ny, nx+1), fy (nz, ny+1, nx), fz (nz+1, ny, nx) */
+#define FX(i, j, k) ((size_t)(i) + (size_t)(nx + 1) * ((size_t)(j) + (size_t)ny * (size_t)(k)))
+#define FY(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)(ny + 1) * (size_t)(k)))
+#define FZ(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)ny * (size_t)(k)))
+
+/* Neighbour index along one axis: periodic wrap, or mirror at a wall
+ * (even reflection: ghost -1 -> 0, ghost n -> n-1). */
+static int ghost(int i, int n, int periodic) {
+  if (i < 0) return periodic ? i + n : -1 - i;
+  if (i >= n) return periodic ? i - n : 2 * n - 1 - i;
+  return i;
+}
+
+static int is_gas(double phi) { return phi > 0.0; } /* phi = 0 counts as liquid */
+
+/*
+ * Curvature kappa = -div(grad phi / |grad phi|) at cell centres, from
+ * second-order central differences of phi (mirror ghosts at walls):
+ *   kappa = -[phi_x^2 (phi_yy + phi_zz) + phi_y^2 (phi_xx + phi_zz)
+ *             + phi_z^2 (phi_xx + phi_yy)
+ *             - 2 (phi_x phi_y phi_xy + phi_x phi_z phi_xz + phi_y phi_z phi_yz)]
+ *           / |grad phi|^3,
+ * |grad phi| floored at 1e-12, result clamped to |kappa| <= 1/h.
+ * With phi > 0 in gas a spherical bubble of radius R has kappa = +2/R.
+ * Surface tension enters through the jump [p] = sigma kappa (the paper's
+ * mph_invWeber parameter, Fig. 14; MultiphaseMain, Section 3).
+ */
+void oracle_curvature(int nx, int ny, int nz, double h, const int periodic[3],
+                      const double *phi, double *kappa) {
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        int im = ghost(i - 1, nx, periodic[0]), ip = ghost(i + 1, nx, periodic[0]);
+        int jm = ghost(j - 1, ny, periodic[1]), jp = ghost(j + 1, ny, periodic[1]);
+        int km = ghost(k - 1, nz, periodic[2]), kp = ghost(k + 1, nz, periodic[2]);
+        double c = phi[IDX(i, j, k)];
+        double px = (phi[IDX(ip, j, k)] - phi[IDX(im, j, k)]) / (2.0 * h);
+        double py = (phi[IDX(i, jp, k)] - phi[IDX(i, jm, k)]) / (2.0 * h);
+        double pz = (phi[IDX(i, j, kp)] - phi[IDX(i, j, km)]) / (2.0 * h);
+        double pxx = (phi[IDX(ip, j, k)] - 2.0 * c + phi[IDX(im, j, k)]) / (h * h);
+        double pyy = (phi[IDX(i, jp, k)] - 2.0 * c + phi[IDX(i, jm, k)]) / (h * h);
+        double pzz = (phi[IDX(i, j, kp)] - 2.0 * c + phi[IDX(i, j, km)]) / (h * h);
+        double pxy = (phi[IDX(ip, jp, k)] - phi[IDX(ip, jm, k)] - phi[IDX(im, jp, k)] +
+                      phi[IDX(im, jm, k)]) / (4.0 * h * h);
+        double pxz = (phi[IDX(ip, j, kp)] - phi[IDX(ip, j, km)] - phi[IDX(im, j, kp)] +
+                      phi[IDX(im, j, km)]) / (4.0 * h * h);
+        double pyz = (phi[IDX(i, jp, kp)] - phi[IDX(i, jp, km)] - phi[IDX(i, jm, kp)] +
+                      phi[IDX(i, jm, km)]) / (4.0 * h * h);
+        double g = sqrt(px * px + py * py + pz * pz);
+        if (g < 1e-12) g = 1e-12;
+        double num = px * px * (pyy + pzz) + py * py * (pxx + pzz) + pz * pz * (pxx + pyy) -
+                     2.0 * (px * py * pxy + px * pz * pxz + py * pz * pyz);
+        double kap = -num / (g * g * g);
+        if (kap > 1.0 / h) kap = 1.0 / h;
+        if (kap < -1.0 / h) kap = -1.0 / h;
+        kappa[IDX(i, j, k)] = kap;
+      }
+}
+
+/*
+ * Ghost-fluid face coefficient between a cell a (low side) and b (high side)
+ * (Liu, Fedkiw & Kang 2000; variable density from phi, varDens):
+ * both cells on one side -> beta = 1/rho(side); otherwise the interface sits
+ * at fraction theta = |phi_a| / (|phi_a| + |phi_b|) of the way from a to b,
+ * the two fluid layers act in series and
+ *   beta = 1 / (theta rho(a) + (1 - theta) rho(b)).
+ */
+static double face_beta(double pa, double pb, double rho_l, double rho_g) {
+  double ra = is_gas(pa) ? rho_g : rho_l;
+  double rb = is_gas(pb) ? rho_g : rho_l;
+  if (is_gas(pa) == is_gas(pb)) return 1.0 / ra;
+  double theta = fabs(pa) / (fabs(pa) + fabs(pb));
+  return 1.0 / (theta * ra + (1.0 - theta) * rb);
+}
+
+/* Face coefficients for every face; walls get beta = 0 (no flux). */
+void oracle_faces(int nx, int ny, int nz, const int periodic[3], const double *phi,
+                  double rho_l, double rho_g, double *fx, double *fy, double *fz) {
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i <= nx; ++i) {
+        double v;
+        if (i == 0 || i == nx) {
+          v = periodic[0] ? face_beta(phi[IDX(nx - 1, j, k)], phi[IDX(0, j, k)], rho_l, rho_g) : 0.0;
+        } else {
+          v = face_beta(phi[IDX(i - 1, j, k)], phi[IDX(i, j, k)], rho_l, rho_g);
+        }
+        fx[FX(i, j, k)] = v;
+      }
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double v;
+        if (j == 0 || j == ny) {
+          v = periodic[1] ? face_beta(phi[IDX(i, ny - 1, k)], phi[IDX(i, 0, k)], rho_l, rho_g) : 0.0;
+        } else {
+          v = face_beta(phi[IDX(i, j - 1, k)], phi[IDX(i, j, k)], rho_l, rho_g);
+        }
+        fy[FY(i, j, k)] = v;
+      }
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k <= nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double v;
+        if (k == 0 || k == nz) {
+          v = periodic[2] ? face_beta(phi[IDX(i, j, nz - 1)], phi[IDX(i, j, 0)], rho_l, rho_g) : 0.0;
+        } else {
+          v = face_beta(phi[IDX(i, j, k - 1)], phi[IDX(i, j, k)], rho_l, rho_g);
+        }
+        fz[FZ(i, j, k)] = v;
+      }
+}
+
+/*
+ * Pressure jump across the face from a to b: [p]_{a->b} = p(b side) - p(a side)
+ * at the interface.  With [p] = p_gas - p_liquid = sigma kappa_G it is
+ * +sigma kappa_G when b is gas, -sigma kappa_G when b is liquid, and 0 on
+ * faces that do not cross the interface.  kappa_G interpolates the cell
+ * curvatures linearly to the interface point:
+ *   kappa_G = (|phi_b| kappa_a + |phi_a| kappa_b) / (|phi_a| + |phi_b|).
+ */
+static double face_jump(double pa, double pb, double ka, double kb, double sigma) {
+  if (is_gas(pa) == is_gas(pb)) return 0.0;
+  double kg = (fabs(pb) * ka + fabs(pa) * kb) / (fabs(pa) + fabs(pb));
+  return is_gas(pb) ? sigma * kg : -sigma * kg;
+}
+
+/*
+ * Jump source J of the ghost-fluid discretisation (Kang, Fedkiw & Liu 2000):
+ * the flux across a face a->b is beta (p_b - p_a - [p]_{a->b}) / h, so every
+ * interface face adds +beta [p]_{a->b} / h^2 to row a and -beta [p]_{a->b} / h^2
+ * to row b.  J sums to zero.  Face loops visit each physical face once.
+ */
+void oracle_jump(int nx, int ny, int nz, double h, const int periodic[3], const double *phi,
+                 const double *kappa, const double *fx, const double *fy, const double *fz,
+                 double sigma, double *J) {
+  size_t n = (size_t)nx * ny * nz;
+  memset(J, 0, n * sizeof(double));
+  double ih2 = 1.0 / (h * h);
+  /* serial: each face updates two rows */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t b = IDX(i, j, k);
+        /* low x face of cell b: between a = (i-1) and b */
+        if (i > 0 || periodic[0]) {
+          size_t a = IDX(i > 0 ? i - 1 : nx - 1, j, k);
+          double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
+          double t = fx[FX(i, j, k)] * jp * ih2;
+          J[a] += t;
+          J[b] -= t;
+        }
+        if (j > 0 || periodic[1]) {
+          size_t a = IDX(i, j > 0 ? j - 1 : ny - 1, k);
+          double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
+          double t = fy[FY(i, j, k)] * jp * ih2;
+          J[a] += t;
+          J[b] -= t;
+        }
+        if (k > 0 || periodic[2]) {
+          size_t a = IDX(i, j, k > 0 ? k - 1 : nz - 1);
+          double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
+          double t = fz[FZ(i, j, k)] * jp * ih2;
+          J[a] += t;
+          J[b] -= t;
+        }
+      }
+}
+
+/* Neighbour across a face on a possibly periodic axis; on a wall the face
+ * coefficient is zero so any in-range index will do (use the cell itself). */
+static int nb(int i, int n, int periodic) {
+  if (i < 0) return periodic ? n - 1 : 0;
+  if (i >= n) return periodic ? 0 : n - 1;
+  return i;
+}
+
+/* y = A x, (A x)_c = sum over the six faces of beta_f (x_nb - x_c) / h^2. */
+void oracle_apply(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+                  const double *fy, const double *fz, const double *x, double *y) {
+  double ih2 = 1.0 / (h * h);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double xc = x[IDX(i, j, k)];
+        double s = 0.0;
+        s += fx[FX(i, j, k)] * (x[IDX(nb(i - 1, nx, periodic[0]), j, k)] - xc);
+        s += fx[FX(i + 1, j, k)] * (x[IDX(nb(i + 1, nx, periodic[0]), j, k)] - xc);
+        s += fy[FY(i, j, k)] * (x[IDX(i, nb(j - 1, ny, periodic[1]), k)] - xc);
+        s += fy[FY(i, j + 1, k)] * (x[IDX(i, nb(j + 1, ny, periodic[1]), k)] - xc);
+        s += fz[FZ(i, j, k)] * (x[IDX(i, j, nb(k - 1, nz, periodic[2]))] - xc);
+        s += fz[FZ(i, j, k + 1)] * (x[IDX(i, j, nb(k + 1, nz, periodic[2]))] - xc);
+        y[IDX(i, j, k)] = s * ih2;
+      }
+}
+
+/* Diagonal of -A: sum of the six face coefficients over h^2. */
+static void neg_diag(int nx, int ny, int nz, double h, const double *fx, const double *fy,
+                     const double *fz, double *d) {
+  double ih2 = 1.0 / (h * h);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        d[IDX(i, j, k)] = (fx[FX(i, j, k)] + fx[FX(i + 1, j, k)] + fy[FY(i, j, k)] +
+                           fy[FY(i, j + 1, k)] + fz[FZ(i, j, k)] + fz[FZ(i, j, k + 1)]) * ih2;
+}
+
+static double dot(size_t n, const double *a, const double *b) {
+  double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
+  for (size_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+/* r = b - A x; returns ||r||_2. */
+double oracle_residual(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+                       const double *fy, const double *fz, const double *b, const double *x,
+                       double *r) {
+  size_t n = (size_t)nx * ny * nz;
+  oracle_apply(nx, ny, nz, h, periodic, fx, fy, fz, x, r);
+#pragma omp parallel for schedule(static)
+  for (size_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+  return sqrt(dot(n, r, r));
+}
+
+/* Remove the mean (the operator annihilates constants: periodic/wall
+ * boundaries leave p determined up to a constant; gauge mean(p) = 0). */
+void oracle_remove_mean(size_t n, double *x) {
+  double s = 0.0;
+  for (size_t i = 0; i < n; ++i) s += x[i];
+  s /= (double)n;
+  for (size_t i = 0; i < n; ++i) x[i] -= s;
+}
+
+/* y = M x with M = -A (symmetric positive semidefinite). */
+static void apply_neg(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+                      const double *fy, const double *fz, const double *x, double *y) {
+  size_t n = (size_t)nx * ny * nz;
+  oracle_apply(nx, ny, nz, h, periodic, fx, fy, fz, x, y);
+#pragma omp parallel for schedule(static)
+  for (size_t i = 0; i < n; ++i) y[i] = -y[i];
+}
+
+/* rho = f - M x, returns ||rho||_2 */
+static double neg_residual(int nx, int ny, int nz, double h, const int periodic[3],
+                           const double *fx, const double *fy, const double *fz, const double *f,
+                           const double *x, double *rho) {
+  size_t n = (size_t)nx * ny * nz;
+  apply_neg(nx, ny, nz, h, periodic, fx, fy, fz, x, rho);
+#pragma omp parallel for schedule(static)
+  for (size_t i = 0; i < n; ++i) rho[i] = f[i] - rho[i];
+  return sqrt(dot(n, rho, rho));
+}
+
+/*
+ * Jacobi-preconditioned conjugate gradients (textbook PCG) on M x = f with
+ * M = -A, f = -b: M is symmetric positive semidefinite with null space the
+ * constants, and b must be mean-free so the system is consistent.
+ * x is the initial guess on entry and the mean-free solution on exit.
+ * Stops when ||b - A x|| <= tol ||b||; the recurrence residual is replaced
+ * by the true one every 50 iterations and checked again at the end.
+ * Returns iterations, or -1 if maxit was hit; *relres gets the final
+ * relative residual.
+ */
+int oracle_cg(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+              const double *fy, const double *fz, const double *b, double *x, double tol,
+              int maxit, double *relres) {
+  size_t n = (size_t)nx * ny * nz;
+  double *f = malloc(n * sizeof(double)), *rho = malloc(n * sizeof(double));
+  double *z = malloc(n * sizeof(double)), *p = malloc(n * sizeof(double));
+  double *q = malloc(n * sizeof(double)), *d = malloc(n * sizeof(double));
+  neg_diag(nx, ny, nz, h, fx, fy, fz, d);
+  for (size_t i = 0; i < n; ++i) f[i] = -b[i];
+  double fn = sqrt(dot(n, f, f));
+  int status = -1;
+  if (fn == 0.0) {
+    memset(x, 0, n * sizeof(double));
+    status = 0;
+  } else {
+    double rn = neg_residual(nx, ny, nz, h, periodic, fx, fy, fz, f, x, rho);
+    double rz_old = 0.0;
+    for (int it = 0; it <= maxit; ++it) {
+      if (rn <= tol * fn) { status = it; break; }
+      if (it == maxit) break;
+#pragma omp parallel for schedule(static)
+      for (size_t i = 0; i < n; ++i) z[i] = rho[i] / d[i];
+      double rz = dot(n, rho, z);
+      if (it == 0) {
+        memcpy(p, z, n * sizeof(double));
+      } else {
+        double beta = rz / rz_old;
+#pragma omp parallel for schedule(static)
+        for (size_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+      }
+      rz_old = rz;
+      apply_neg(nx, ny, nz, h, periodic, fx, fy, fz, p, q);
+      double alpha = rz / dot(n, p, q);
+#pragma omp parallel for schedule(static)
+      for (size_t i = 0; i < n; ++i) {
+        x[i] += alpha * p[i];
+        rho[i] -= alpha * q[i];
+      }
+      if ((it + 1) % 50 == 0)
+        rn = neg_residual(nx, ny, nz, h, periodic, fx, fy, fz, f, x, rho);
+      else
+        rn = sqrt(dot(n, rho, rho));
+    }
+  }
+  oracle_remove_mean(n, x);
+  double tn = neg_residual(nx, ny, nz, h, periodic, fx, fy, fz, f, x, rho);
+  *relres = fn > 0.0 ? tn / fn : 0.0;
+  if (status >= 0 && tn > tol * fn) status = -1;
+  free(f); free(rho); free(z); free(p); free(q); free(d);
+  return status;
+}
+
+/*
+ * Lexicographic Gauss-Seidel for small grids: each cell in turn takes
+ *   x_c = (sum_f beta_f x_nb - h^2 b_c) / sum_f beta_f,
+ * i.e. row c of A x = b solved for x_c.  Sweeps until ||b - A x|| <= tol ||b||.
+ */
+int oracle_gs(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+              const double *fy, const double *fz, const double *b, double *x, double tol,
+              int maxsweeps, double *relres) {
+  size_t n = (size_t)nx * ny * nz;
+  double *r = malloc(n * sizeof(double));
+  double bn = sqrt(dot(n, b, b));
+  int status = -1;
+  for (int s = 0; s <= maxsweeps; ++s) {
+    double rn = oracle_residual(nx, ny, nz, h, periodic, fx, fy, fz, b, x, r);
+    if (rn <= tol * bn) { status = s; break; }
+    if (s == maxsweeps) break;
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          double wxm = fx[FX(i, j, k)], wxp = fx[FX(i + 1, j, k)];
+          double wym = fy[FY(i, j, k)], wyp = fy[FY(i, j + 1, k)];
+          double wzm = fz[FZ(i, j, k)], wzp = fz[FZ(i, j, k + 1)];
+          double num = wxm * x[IDX(nb(i - 1, nx, periodic[0]), j, k)] +
+                       wxp * x[IDX(nb(i + 1, nx, periodic[0]), j, k)] +
+                       wym * x[IDX(i, nb(j - 1, ny, periodic[1]), k)] +
+                       wyp * x[IDX(i, nb(j + 1, ny, periodic[1]), k)] +
+                       wzm * x[IDX(i, j, nb(k - 1, nz, periodic[2]))] +
+                       wzp * x[IDX(i, j, nb(k + 1, nz, periodic[2]))];
+          double den = wxm + wxp + wym + wyp + wzm + wzp;
+          x[IDX(i, j, k)] = (num - h * h * b[IDX(i, j, k)]) / den;
+        }
+  }
+  oracle_remove_mean(n, x);
+  *relres = oracle_residual(nx, ny, nz, h, periodic, fx, fy, fz, b, x, r) / bn;
+  free(r);
+  return status;
+}
+
+/* Cell-centred divergence of face velocities (n+1 faces per axis):
+ * (div u)_c = sum over axes of (u_high - u_low) / h. */
+void oracle_divergence(int nx, int ny, int nz, double h, const double *ux, const double *uy,
+                       const double *uz, double *div) {
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        div[IDX(i, j, k)] = (ux[FX(i + 1, j, k)] - ux[FX(i, j, k)] + uy[FY(i, j + 1, k)] -
+                             uy[FY(i, j, k)] + uz[FZ(i, j, k + 1)] - uz[FZ(i, j, k)]) / h;
+}
+
+/*
+ * Velocity correction of the projection step (Delta t = 1):
+ *   u_f = u*_f - beta_f (p_b - p_a - [p]_{a->b}) / h
+ * on every face between a (low) and b (high); wall faces keep u*.
+ * Updates ux, uy, uz (n+1 faces per axis) in place.
+ */
+void oracle_project(int nx, int ny, int nz, double h, const int periodic[3], const double *phi,
+                    const double *kappa, const double *fx, const double *fy, const double *fz,
+                    double sigma, const double *p, double *ux, double *uy, double *uz) {
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i <= nx; ++i) {
+        if ((i == 0 || i == nx) && !periodic[0]) continue;
+        size_t a = IDX(i == 0 ? nx - 1 : i - 1, j, k), b = IDX(i == nx ? 0 : i, j, k);
+        double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
+        ux[FX(i, j, k)] -= fx[FX(i, j, k)] * (p[b] - p[a] - jp) / h;
+      }
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if ((j == 0 || j == ny) && !periodic[1]) continue;
+        size_t a = IDX(i, j == 0 ? ny - 1 : j - 1, k), b = IDX(i, j == ny ? 0 : j, k);
+        double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
+        uy[FY(i, j, k)] -= fy[FY(i, j, k)] * (p[b] - p[a] - jp) / h;
+      }
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k <= nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if ((k == 0 || k == nz) && !periodic[2]) continue;
+        size_t a = IDX(i, j, k == 0 ? nz - 1 : k - 1), b = IDX(i, j, k == nz ? 0 : k);
+        double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
+        uz[FZ(i, j, k)] -= fz[FZ(i, j, k)] * (p[b] - p[a] - jp) / h;
+      }
+}
