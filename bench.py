@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Projection-step throughput of the GB300 pressure-Poisson path.
+
+One step = one pass of the whole hot path on a 256^3 grid: geometry setup
+from phi (curvature, ghost-fluid faces, jump source, coarse hierarchy,
+coarsest inverse), rhs = div u* with the jump, the pressure solve to relative
+residual 1e-10 (MG-preconditioned CG; FP64, or mixed FP32/FP64 refinement),
+the gauge and the face-velocity correction.  Every step gets a fresh seeded
+16-mode u*.  The headline value is the mixed-precision form; the plain FP64
+form is measured on the same inputs and reported under "modes".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs independent replicas (the solve does
+not shard: one grid per GPU); value = steps of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pressure solves/s at 256³ to res 1e-10: FP64 MG vs mixed+learned; HBM % peak"
+UNIT = "solves/s"
+WORKLOAD = "bubble256"
+TOL = 1e-10
+
+
+def workload_desc(n):
+    return ("bubble256: %d^3 cells on the unit cube, periodic x,y / wall z, one gas bubble "
+            "R=0.15 at (0.5,0.5,0.4), rho_l=1, rho_g=1e-3, sigma=0.07, fresh seeded 16-mode u* "
+            "per step, solve to relative residual 1e-10" % n)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(index)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), max=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["max"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_baseline(n, cg_iters=100):
+    """The FP64 CPU oracle as it stands, on this host's cores: assembly and
+    projection plus `cg_iters` Jacobi-PCG iterations at n^3 are timed; the
+    iterations a solve to 1e-10 needs come from a full oracle solve of the
+    same workload at (n/2)^3, doubled (CG iterations grow linearly in n)."""
+    import oracle
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    bc = (synth.PERIODIC, synth.PERIODIC, synth.NEUMANN)
+    cores = os.cpu_count() or 1
+    # iteration count from the half-size solve (untimed)
+    m = n // 2
+    hm = 1.0 / m
+    phi_m = synth.level_set((m, m, m), hm, w["bubbles"])
+    u_m = synth.velocity(w["useed"], (m, m, m), hm)
+    res_m = oracle.solve(phi_m, oracle.divergence(*u_m, hm), hm, w["rho_l"], w["rho_g"],
+                         w["sigma"], bc, tol=TOL)
+    iters_est = 2 * max(res_m["iters"], 1)
+    h = 1.0 / n
+    phi = synth.level_set((n, n, n), h, w["bubbles"])
+    u = synth.velocity(w["useed"], (n, n, n), h)
+    t0 = time.perf_counter()
+    rhs = oracle.divergence(*u, h)
+    kap, f, J, b = oracle.assemble(phi, rhs, h, w["rho_l"], w["rho_g"], w["sigma"], bc)
+    t1 = time.perf_counter()
+    x, _, _ = oracle.cg(f, b, h, bc, tol=1e-30, maxit=cg_iters)
+    t2 = time.perf_counter()
+    oracle.project(phi, kap, f, x, *u, h, w["sigma"], bc)
+    t3 = time.perf_counter()
+    t_solve = (t1 - t0) + (t3 - t2) + (t2 - t1) / cg_iters * iters_est
+    return {"value": 1.0 / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": ("C oracle (OpenMP, %d threads): assembly + projection + %d Jacobi-PCG "
+                       "iterations timed at %d^3 (%.2f s); %d iterations to 1e-10 estimated as 2x "
+                       "a full oracle solve of the same workload at %d^3 (%d iterations)"
+                       % (cores, cg_iters, n, t3 - t0, iters_est, m, res_m["iters"])),
+            "seconds_per_solve_est": t_solve}
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle itself on this host's cores."""
+    if rank != 0:
+        return
+    n = args.n
+    cg_iters = 40
+    import oracle
+    import synth
+    oracle.build()
+    w = synth.WORKLOADS[WORKLOAD]
+    bc = (synth.PERIODIC, synth.PERIODIC, synth.NEUMANN)
+    m = n // 2
+    hm = 1.0 / m
+    phi_m = synth.level_set((m, m, m), hm, w["bubbles"])
+    u_m = synth.velocity(w["useed"], (m, m, m), hm)
+    res_m = oracle.solve(phi_m, oracle.divergence(*u_m, hm), hm, w["rho_l"], w["rho_g"],
+                         w["sigma"], bc, tol=TOL)
+    iters_est = 2 * max(res_m["iters"], 1)
+    h = 1.0 / n
+    phi = synth.level_set((n, n, n), h, w["bubbles"])
+    times = []
+    for step in range(args.warmup + args.steps):
+        u = synth.velocity(1000 + step, (n, n, n), h)
+        t0 = time.perf_counter()
+        rhs = oracle.divergence(*u, h)
+        kap, f, J, b = oracle.assemble(phi, rhs, h, w["rho_l"], w["rho_g"], w["sigma"], bc)
+        t1 = time.perf_counter()
+        x, _, _ = oracle.cg(f, b, h, bc, tol=1e-30, maxit=cg_iters)
+        t2 = time.perf_counter()
+        oracle.project(phi, kap, f, x, *u, h, w["sigma"], bc)
+        t3 = time.perf_counter()
+        if step >= args.warmup:
+            times.append((t1 - t0) + (t3 - t2) + (t2 - t1) / cg_iters * iters_est)
+    t = sum(times)
+    value = len(times) / t
+    cores = os.cpu_count() or 1
+    sample = ("each step: C oracle (OpenMP, %d threads) assembly + projection + %d Jacobi-PCG "
+              "iterations at %d^3, CG time scaled to %d iterations (2x a full oracle solve at "
+              "%d^3: %d iterations)" % (cores, cg_iters, n, iters_est, m, res_m["iters"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_desc(n), "grid": [n, n, n]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+def run_mine(args, rank, world, local_rank):
+    import torch
+    import synth
+    from paper_2312_11740_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2312_11740_gb300 import Poisson, mp_poisson_project_step_host
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n = args.n
+    h = 1.0 / n
+    shape = (n, n, n)
+    w = synth.WORKLOADS[WORKLOAD]
+    bc = (synth.PERIODIC, synth.PERIODIC, synth.NEUMANN)
+    phi = torch.from_numpy(synth.level_set(shape, h, w["bubbles"])).to(dev)
+    nprof = min(args.steps, 3)
+    nsteps = args.warmup + args.steps + nprof
+    seeds = [100000 * (rank + 1) + s for s in range(nsteps)]
+
+    def fresh_u(count=nsteps):
+        return [synth.velocity(sd, shape, h, device=dev) for sd in seeds[:count]]
+
+    stream = torch.cuda.Stream(device=dev)
+    results = {}
+    modes = [(m, {"fp64": 0, "mixed": 1}[m]) for m in args.modes.split(",")]
+    for name, precision in modes:
+        us = fresh_u()
+        ps = [torch.zeros(shape, dtype=torch.float64, device=dev) for _ in range(nsteps)]
+        torch.cuda.synchronize()
+        s = Poisson(phi, h, bc, w["rho_l"], w["rho_g"], w["sigma"], precision=precision,
+                    stream=stream)
+
+        def step(k):
+            s.set_geometry(phi, w["rho_l"], w["rho_g"], w["sigma"])
+            it = s.project_step(*us[k], ps[k], tol=TOL)
+            return it, s.stats()["relres"]
+
+        for k in range(args.warmup):
+            step(k)
+        # timed region: launch counting only (no per-launch events)
+        s.set_profiling(False)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(local_rank) if name == "mixed" else None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, relres = [], []
+        for k in range(args.warmup, args.warmup + args.steps):
+            it, rr = step(k)
+            its.append(it)
+            relres.append(rr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        launches = sum(e["launches"] for e in s.profile())
+        # profiled pass on further inputs: every launch bracketed by CUDA events on
+        # the library's stream (per-kernel durations for the roofline)
+        s.set_profiling(True)
+        for k in range(args.warmup + args.steps, nsteps):
+            step(k)
+        prof = s.profile()
+        s.set_profiling(False)
+        st = s.stats()
+        results[name] = dict(ms=ms, iters=its, relres=max(relres), prof=prof, clocks=clocks,
+                             levels=st["levels"], outer=st["outer_steps"], launches=launches,
+                             prof_steps=nprof)
+        # end to end through the host-buffer entry point (pinned host memory)
+        if name == "mixed":
+            hx = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(3)]
+            hp = torch.empty(shape, dtype=torch.float64).pin_memory()
+            e2e_steps = max(2, min(args.steps, 5))
+            src = fresh_u(e2e_steps)
+            host_u = [[c.cpu().pin_memory() for c in u3] for u3 in src]
+            torch.cuda.synchronize()
+            t_e2e = 0.0
+            for k in range(e2e_steps):
+                for dst, srcc in zip(hx, host_u[k]):
+                    dst.copy_(srcc)
+                t0 = time.perf_counter()
+                s.set_geometry(phi, w["rho_l"], w["rho_g"], w["sigma"])
+                mp_poisson_project_step_host(s.handle, hx[0], hx[1], hx[2], hp, TOL)
+                t_e2e += time.perf_counter() - t0
+            results[name]["e2e"] = dict(steps=e2e_steps, seconds=t_e2e)
+        s.close()
+        del us, ps
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return
+    K = args.steps
+    mixed = results["mixed"]
+    fp64 = results.get("fp64", mixed)
+    value = world * K / (mixed["ms"] * 1e-3)
+    # dominant (kernel, level) by time in the mixed timed region
+    prof = mixed["prof"]
+    top = max(prof, key=lambda e: e["total_ms"])
+    hbm, peak_kind = peaks()
+    achieved = top["alg_bytes"] / (top["total_ms"] * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tr = json.load(open(tpath))
+            key = "%s@L%d" % (top["name"], top["level"])
+            if key in tr and tr[key].get("cells") == top["cells"]:
+                traffic = tr[key]["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+    launches = mixed["launches"]
+    total_prof_ms = sum(e["total_ms"] for e in prof)
+
+    def mode_line(r):
+        return {"solves_per_s": world * K / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / K,
+                "iterations": r["iters"], "outer_steps_last": r["outer"],
+                "max_relres": r["relres"], "levels": r["levels"]}
+
+    e2e = mixed["e2e"]
+    nbytes = n * n * n * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": mixed["ms"] / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_desc(n), "grid": [n, n, n], "tol": TOL,
+                   "form": "mixed FP32/FP64 iterative refinement, MG-preconditioned CG",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2: each step touches ~2 GB of fields"},
+        "modes": {"mixed": mode_line(mixed), "fp64": mode_line(fp64),
+                  "mixed_over_fp64": fp64["ms"] / mixed["ms"]} if "fp64" in results else
+                 {"mixed": mode_line(mixed)},
+        "roofline": {"kernel": "%s@L%d" % (top["name"], top["level"]), "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": peak_kind, "traffic": traffic,
+                     "share_of_profiled_time": top["total_ms"] / total_prof_ms,
+                     "timing": "CUDA events around every launch on the library stream, "
+                               "%d further steps after the timed region" % mixed["prof_steps"],
+                     "launches": top["launches"],
+                     "alg_bytes_per_launch": top["alg_bytes"] / top["launches"],
+                     "avg_launch_us": 1e3 * top["total_ms"] / top["launches"]},
+        "e2e": {"value": e2e["steps"] / e2e["seconds"], "unit": UNIT,
+                "h2d_bytes_per_step": 3 * nbytes, "d2h_bytes_per_step": 4 * nbytes},
+        "gpu_launches": launches,
+        "clocks": mixed["clocks"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            line["cpu_baseline"] = cpu_baseline(n)
+        except Exception as ex:  # reported, never silently replaced
+            line["cpu_baseline"] = {"value": None, "error": repr(ex)}
+    if args.profile_out:
+        with open(args.profile_out, "w") as f:
+            json.dump({"mixed": mixed["prof"], "fp64": fp64["prof"]}, f, indent=1)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid cells per axis (default 256)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--modes", default="fp64,mixed", help="comma list of fp64,mixed (mixed last)")
+    ap.add_argument("--profile-out", default=None, help="write per-kernel profile JSON here")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_mine(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * mp_poisson — GB300 (sm_103a) variable-density pressure-Poisson solve of the
+ * projection step of an incompressible liquid–gas solver.
+ *
+ * The paper (arXiv 2312.11740, Section 2) fixes a staggered-grid,
+ * finite-difference, fractional-step projection method: velocities on faces,
+ * pressure and the level set phi at cell centres (Fig. 2 caption), phi > 0 in
+ * gas and phi < 0 in liquid, variable density from phi (varDens, Section 3),
+ * a multigrid Poisson solve (Grid_solvePoisson, Section 3).  The discrete
+ * problem solved here is the ghost-fluid discretisation (Liu, Fedkiw & Kang
+ * 2000) of  div((1/rho) grad p) = div u*  with the jump [p] = sigma*kappa:
+ *
+ *   (A p)_c = sum over the 6 faces f of c of beta_f (p_nb - p_c) / h^2,
+ *   A p = b,  b = div_h u* + J - mean(div_h u* + J),  mean(p) = 0,
+ *
+ * beta_f the two-fluid face coefficient from phi, J the jump source, then
+ * u = u* - beta_f (grad_h p - [p]) on every face (Delta t = 1).
+ *
+ * Memory layout (all arrays): C order, x fastest, idx = i + nx*(j + ny*k),
+ * float64 unless stated.  Face arrays use low-face ownership: element idx of
+ * an x-face array sits on the face between cells (i-1,j,k) and (i,j,k),
+ * wrapped (face 0 is the face between cell nx-1 and cell 0); on a wall axis
+ * face 0 is the wall, shared by the bottom and top walls.
+ *
+ * Pointers: "_dev" arguments are device pointers to caller-owned memory; the
+ * library never frees them and keeps no pointer to them after a call
+ * returns.  "_host" arguments are host memory (pageable or pinned).
+ * Streams: all device work is enqueued on opts->stream; a call returns after
+ * the work it enqueued is complete unless stated otherwise.
+ * Errors: every call returns an mp_status and never aborts or traps; on
+ * MP_ERR_CUDA the handle may be unusable and should be destroyed.
+ * Threads: one handle must not be used by two host threads at once.
+ */
+#ifndef MP_POISSON_H
+#define MP_POISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MP_OK = 0,
+  MP_ERR_INVALID_ARG = 1,   /* bad size, pointer, option or boundary type */
+  MP_ERR_NOT_CONVERGED = 2, /* max_iters reached; p and history hold the last iterate */
+  MP_ERR_DIVERGED = 3,      /* NaN/Inf residual; p is unspecified */
+  MP_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  MP_ERR_OOM = 5,           /* device or pinned allocation failed */
+  MP_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+  MP_ERR_NO_NET = 7         /* learned initial guess requested without weights */
+} mp_status;
+
+typedef enum { MP_BC_PERIODIC = 0, MP_BC_NEUMANN = 1 } mp_bc; /* Neumann = zero-flux wall */
+
+typedef struct {
+  int nx, ny, nz;
+} mp_grid;
+
+/* Solver options.  mp_opts_default() fills the defaults given here. */
+typedef struct {
+  int precision;     /* 0 = FP64 throughout; 1 = mixed: FP32 smoothing/transfers and inner
+                        iterations, FP64 outer residual, accumulation and coarsest solve.
+                        Default 0. */
+  int method;        /* 0 = conjugate gradients preconditioned by one symmetric V-cycle
+                        (default); 1 = stationary V-cycle iteration. */
+  int initial_guess; /* 0 = zero (default); 1 = the caller's p; 2 = learned network
+                        (requires mp_poisson_set_net). */
+  int max_iters;     /* outer iterations (FP64) or total inner iterations (mixed). Default 200. */
+  int nu1, nu2;      /* pre/post red-black Gauss–Seidel sweeps on the finest level. Default 2, 2. */
+  int nu_growth;     /* sweeps multiply by this per coarser level. Default 2. */
+  int nu_max;        /* cap on sweeps per level. Default 16. */
+  double inner_rtol; /* mixed: inner FP32 solve reduces its residual by this factor per
+                        outer refinement step. Default 1e-4. */
+  int inner_max;     /* mixed: cap on inner iterations per outer step. Default 12. */
+  void *stream;      /* cudaStream_t; NULL = legacy default stream. */
+} mp_opts;
+
+/* Statistics of the last mp_poisson_solve / mp_poisson_project_step. */
+typedef struct {
+  int iterations;      /* V-cycle applications (preconditioner or stationary steps) */
+  int outer_steps;     /* mixed: FP64 refinement steps; FP64 mode: equals iterations */
+  double relres;       /* final ||b - A p|| / ||b||, FP64, true residual */
+  double r0;           /* initial ||b - A p0|| / ||b|| */
+  int used_net;        /* 1 if the learned guess was kept, 0 if not requested or rejected */
+  int levels;          /* multigrid levels */
+  int coarse_n;        /* unknowns of the coarsest (direct) level */
+} mp_stats;
+
+typedef struct mp_poisson *mp_handle;
+
+/* Fill *opts with the defaults documented in mp_opts. */
+void mp_opts_default(mp_opts *opts);
+
+/*
+ * Allocate a solver for grid g (cell edge h > 0, boundary bc[axis] per axis)
+ * and set its geometry from phi_dev (device, nx*ny*nz f64, phi > 0 gas),
+ * liquid density rho_l > 0, gas density rho_g > 0, surface tension sigma >= 0.
+ * Every axis must be >= 2 and even on periodic axes.  The hierarchy halves
+ * all dims while they are all even and >= 4 and the level has more than 64
+ * cells; the coarsest level must have at most 512 cells (else
+ * MP_ERR_INVALID_ARG).  Allocates all device memory
+ * the solver needs; no later call allocates.  opts may be NULL (defaults).
+ */
+mp_status mp_poisson_setup(mp_handle *out, mp_grid g, double h, const mp_bc bc[3],
+                           const double *phi_dev, double rho_l, double rho_g, double sigma,
+                           const mp_opts *opts);
+
+/*
+ * Recompute the geometry-dependent data (curvature, face coefficients, jump
+ * source, coarse hierarchy, coarsest inverse) for a new phi on the same grid.
+ * No allocation.
+ */
+mp_status mp_poisson_set_geometry(mp_handle hd, const double *phi_dev, double rho_l, double rho_g,
+                                  double sigma);
+
+/* Replace the options (stream, precision, method, ...). */
+mp_status mp_poisson_set_opts(mp_handle hd, const mp_opts *opts);
+
+/*
+ * Solve A p = b with b = rhs + J - mean, to ||b - A p|| <= tol ||b||.
+ * rhs_dev: device, N f64 (e.g. div u*).  p_dev: device, N f64, in/out
+ * (read only if initial_guess = 1), mean-free on exit.  iterations (may be
+ * NULL) gets mp_stats.iterations.  res_hist (host, may be NULL) gets up to
+ * res_hist_cap relative residuals: [0] is the initial one, then one per
+ * outer iteration; res_hist_len (may be NULL) gets the count written.
+ * Returns MP_OK, MP_ERR_NOT_CONVERGED (p holds the last iterate) or an error.
+ */
+mp_status mp_poisson_solve(mp_handle hd, const double *rhs_dev, double *p_dev, double tol,
+                           int *iterations, double *res_hist, int res_hist_cap, int *res_hist_len);
+
+/*
+ * One projection step on device data: rhs = div_h u*, solve as
+ * mp_poisson_solve, then correct the face velocities in place,
+ * u = u* - beta (grad_h p - [p]).  ux/uy/uz_dev: device, N f64 each
+ * (low-face ownership), in/out.  p_dev as in mp_poisson_solve.
+ */
+mp_status mp_poisson_project_step(mp_handle hd, double *ux_dev, double *uy_dev, double *uz_dev,
+                                  double *p_dev, double tol, int *iterations);
+
+/*
+ * The same step on HOST buffers: copies u* (3N f64) and, for
+ * initial_guess = 1, p (N f64) to the device, runs mp_poisson_project_step
+ * and copies the corrected velocities and p back.  Uses device staging
+ * buffers allocated at setup.
+ */
+mp_status mp_poisson_project_step_host(mp_handle hd, double *ux_host, double *uy_host,
+                                       double *uz_host, double *p_host, double tol,
+                                       int *iterations);
+
+/* y = A x (unscaled operator, device N f64 each). */
+mp_status mp_poisson_apply(mp_handle hd, const double *x_dev, double *y_dev);
+
+/* div_dev = div_h u (device, N f64). */
+mp_status mp_poisson_divergence(mp_handle hd, const double *ux_dev, const double *uy_dev,
+                                const double *uz_dev, double *div_dev);
+
+/* b_dev = rhs + J - mean(rhs + J), the right-hand side the solve uses. */
+mp_status mp_poisson_rhs(mp_handle hd, const double *rhs_dev, double *b_dev);
+
+/* u -= beta (grad_h p - [p]) on every face, in place. */
+mp_status mp_poisson_project(mp_handle hd, const double *p_dev, double *ux_dev, double *uy_dev,
+                             double *uz_dev);
+
+/* Copy setup fields out (device pointers, each N f64; any may be NULL):
+ * curvature kappa, face coefficients beta_x/y/z (low-face ownership, wall
+ * faces 0), jump source J (unscaled, sums to zero). */
+mp_status mp_poisson_get_fields(mp_handle hd, double *kappa_dev, double *bx_dev, double *by_dev,
+                                double *bz_dev, double *J_dev);
+
+/* Statistics of the last solve. */
+mp_status mp_poisson_get_stats(mp_handle hd, mp_stats *st);
+
+/* Per-(kernel, level) launch record, filled by mp_poisson_get_profile. */
+typedef struct {
+  char name[40];        /* kernel name, e.g. "rbgs_f32" */
+  int level;            /* multigrid level (0 = finest) */
+  long long cells;      /* cells of that level */
+  long long launches;   /* launches since the last mp_poisson_set_profiling */
+  double total_ms;      /* summed CUDA-event durations (0 unless profiling is on) */
+  double alg_bytes;     /* summed algorithmic bytes: unique bytes each launch must move */
+} mp_kernel_prof;
+
+/*
+ * Launch accounting.  Every kernel launch is counted per (kernel, level).
+ * enable = 1 also brackets every launch with CUDA events on the handle's
+ * stream (host-side cost ~1 us per launch).  Resets all counters.
+ */
+mp_status mp_poisson_set_profiling(mp_handle hd, int enable);
+
+/* Copy up to cap records to out (host memory); *count (may be NULL) gets
+ * the number of records available. */
+mp_status mp_poisson_get_profile(mp_handle hd, mp_kernel_prof *out, int cap, int *count);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void mp_poisson_destroy(mp_handle hd);
+
+/* Static text for a status code. */
+const char *mp_status_str(mp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MP_POISSON_H */

@@ -1,0 +1,580 @@
+// Device kernels of the pressure-Poisson hot path (sm_103a).
+//
+// Conventions: cell arrays are C order, x fastest; face arrays use low-face
+// ownership (element (i,j,k) of the x-face array is the face between cells
+// i-1 and i, wrapped; on a wall axis face 0 is the wall and holds beta = 0).
+// Inside the solver every level works with the h^2-scaled system
+//   At e = bt,  (At e)_c = sum_f beta_f e_nb - diag_c e_c,  bt = h^2 b,
+// so no kernel multiplies by 1/h^2; diag_c = sum of the six face betas.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mp {
+
+struct Dims {
+  int nx, ny, nz;
+};
+
+constexpr int BX = 32, BY = 8;  // per-cell launch tile (x fastest)
+
+__device__ __forceinline__ size_t at(const Dims &d, int i, int j, int k) {
+  return (size_t)i + (size_t)d.nx * ((size_t)j + (size_t)d.ny * (size_t)k);
+}
+__device__ __forceinline__ int wlo(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int whi(int i, int n) { return i == n - 1 ? 0 : i + 1; }
+// ghost index for one-sided stencils of phi: wrap on periodic axes, even
+// mirror (ghost -1 -> 0, ghost n -> n-1) on wall axes
+__device__ __forceinline__ int glo(int i, int n, bool per) { return i > 0 ? i - 1 : (per ? n - 1 : 0); }
+__device__ __forceinline__ int ghi(int i, int n, bool per) { return i < n - 1 ? i + 1 : (per ? 0 : n - 1); }
+
+// ---------------------------------------------------------------- reductions
+template <typename A>
+__device__ __forceinline__ A warp_sum(A v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum in a fixed order (deterministic for a fixed launch shape).
+// Every thread must call it; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  int lane = (threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) & 31;
+  int warp = (threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) >> 5;
+  int nwarp = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < nwarp ? red[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+__device__ __forceinline__ int block_linear_id() {
+  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+__device__ __forceinline__ bool thread0() {
+  return threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
+}
+
+// ------------------------------------------------------------ A1: curvature
+// kappa = -div(grad phi/|grad phi|) by central differences at cell centres,
+// |grad phi| floored at 1e-12, |kappa| clamped to 1/h.  Gas-positive phi
+// gives kappa = +2/R for a spherical bubble.
+__global__ void k_curvature(const double *__restrict__ phi, double *__restrict__ kap, Dims d,
+                            double h, int per) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nx || j >= d.ny) return;
+  bool px = per & 1, py = per & 2, pz = per & 4;
+  int im = glo(i, d.nx, px), ip = ghi(i, d.nx, px);
+  int jm = glo(j, d.ny, py), jp = ghi(j, d.ny, py);
+  int km = glo(k, d.nz, pz), kp = ghi(k, d.nz, pz);
+  double c = phi[at(d, i, j, k)];
+  double xm = phi[at(d, im, j, k)], xp = phi[at(d, ip, j, k)];
+  double ym = phi[at(d, i, jm, k)], yp = phi[at(d, i, jp, k)];
+  double zm = phi[at(d, i, j, km)], zp = phi[at(d, i, j, kp)];
+  double i2h = 0.5 / h, ih2 = 1.0 / (h * h), i4h2 = 0.25 / (h * h);
+  double gx = (xp - xm) * i2h, gy = (yp - ym) * i2h, gz = (zp - zm) * i2h;
+  double gxx = (xp - 2.0 * c + xm) * ih2, gyy = (yp - 2.0 * c + ym) * ih2,
+         gzz = (zp - 2.0 * c + zm) * ih2;
+  double gxy = (phi[at(d, ip, jp, k)] - phi[at(d, ip, jm, k)] - phi[at(d, im, jp, k)] +
+                phi[at(d, im, jm, k)]) * i4h2;
+  double gxz = (phi[at(d, ip, j, kp)] - phi[at(d, ip, j, km)] - phi[at(d, im, j, kp)] +
+                phi[at(d, im, j, km)]) * i4h2;
+  double gyz = (phi[at(d, i, jp, kp)] - phi[at(d, i, jp, km)] - phi[at(d, i, jm, kp)] +
+                phi[at(d, i, jm, km)]) * i4h2;
+  double g = sqrt(gx * gx + gy * gy + gz * gz);
+  g = g < 1e-12 ? 1e-12 : g;
+  double num = gx * gx * (gyy + gzz) + gy * gy * (gxx + gzz) + gz * gz * (gxx + gyy) -
+               2.0 * (gx * gy * gxy + gx * gz * gxz + gy * gz * gyz);
+  double kv = -num / (g * g * g);
+  double lim = 1.0 / h;
+  kv = kv > lim ? lim : (kv < -lim ? -lim : kv);
+  kap[at(d, i, j, k)] = kv;
+}
+
+// ------------------------------------------------- A2: ghost-fluid faces
+// Two cells on one side: 1/rho of that fluid.  Across the interface the
+// fluids act in series over the fractions theta, 1-theta of the spacing:
+// beta = 1/(theta rho_a + (1-theta) rho_b), theta = |phi_a|/(|phi_a|+|phi_b|).
+__device__ __forceinline__ double gfm_beta(double pa, double pb, double rl, double rg) {
+  bool ga = pa > 0.0, gb = pb > 0.0;
+  double ra = ga ? rg : rl, rb = gb ? rg : rl;
+  if (ga == gb) return 1.0 / ra;
+  double th = fabs(pa) / (fabs(pa) + fabs(pb));
+  return 1.0 / (th * ra + (1.0 - th) * rb);
+}
+
+// Pressure jump [p]_{a->b} = p(b side) - p(a side) = +-sigma kappa_G,
+// kappa_G linearly interpolated to the interface; 0 off the interface.
+__device__ __forceinline__ double gfm_jump(double pa, double pb, double ka, double kb, double sig) {
+  bool ga = pa > 0.0, gb = pb > 0.0;
+  if (ga == gb) return 0.0;
+  double aa = fabs(pa), ab = fabs(pb);
+  double kg = (ab * ka + aa * kb) / (aa + ab);
+  return gb ? sig * kg : -sig * kg;
+}
+
+__global__ void k_faces(const double *__restrict__ phi, double *__restrict__ bx,
+                        double *__restrict__ by, double *__restrict__ bz, Dims d, double rl,
+                        double rg, int per) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nx || j >= d.ny) return;
+  size_t c = at(d, i, j, k);
+  double pc = phi[c];
+  bx[c] = (i == 0 && !(per & 1)) ? 0.0 : gfm_beta(phi[at(d, wlo(i, d.nx), j, k)], pc, rl, rg);
+  by[c] = (j == 0 && !(per & 2)) ? 0.0 : gfm_beta(phi[at(d, i, wlo(j, d.ny), k)], pc, rl, rg);
+  bz[c] = (k == 0 && !(per & 4)) ? 0.0 : gfm_beta(phi[at(d, i, j, wlo(k, d.nz))], pc, rl, rg);
+}
+
+// -------------------------------------------------------- A3: jump source
+// Flux across a face a->b is beta (p_b - p_a - [p]_{a->b}); moving the known
+// jump to the right-hand side adds +beta [p]_{a->b} to row a and -beta
+// [p]_{a->b} to row b.  Gathered per cell (no atomics); h^2-scaled.
+__global__ void k_jump(const double *__restrict__ phi, const double *__restrict__ kap,
+                       const double *__restrict__ bx, const double *__restrict__ by,
+                       const double *__restrict__ bz, double *__restrict__ Jt, Dims d,
+                       double sig) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nx || j >= d.ny) return;
+  size_t c = at(d, i, j, k);
+  double pc = phi[c], kc = kap[c];
+  size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
+  size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
+  size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+  double s = 0.0;
+  s += bx[xh] * gfm_jump(pc, phi[xh], kc, kap[xh], sig) - bx[c] * gfm_jump(phi[xl], pc, kap[xl], kc, sig);
+  s += by[yh] * gfm_jump(pc, phi[yh], kc, kap[yh], sig) - by[c] * gfm_jump(phi[yl], pc, kap[yl], kc, sig);
+  s += bz[zh] * gfm_jump(pc, phi[zh], kc, kap[zh], sig) - bz[c] * gfm_jump(phi[zl], pc, kap[zl], kc, sig);
+  Jt[c] = s;
+}
+
+// diag = sum of the six face betas, idiag = 1/diag; f64 and f32 copies
+__global__ void k_diag(const double *__restrict__ bx, const double *__restrict__ by,
+                       const double *__restrict__ bz, double *__restrict__ diag,
+                       double *__restrict__ idiag, float *__restrict__ bx32,
+                       float *__restrict__ by32, float *__restrict__ bz32,
+                       float *__restrict__ diag32, float *__restrict__ idiag32, Dims d) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nx || j >= d.ny) return;
+  size_t c = at(d, i, j, k);
+  double s = bx[c] + bx[at(d, whi(i, d.nx), j, k)] + by[c] + by[at(d, i, whi(j, d.ny), k)] + bz[c] +
+             bz[at(d, i, j, whi(k, d.nz))];
+  double is = 1.0 / s;
+  diag[c] = s;
+  idiag[c] = is;
+  bx32[c] = (float)bx[c];
+  by32[c] = (float)by[c];
+  bz32[c] = (float)bz[c];
+  diag32[c] = (float)s;
+  idiag32[c] = (float)is;
+}
+
+// ------------------------------------------- A5: coarse face coefficients
+// A coarse face is the mean of the four fine faces that tile it.
+__global__ void k_coarsen_faces(const double *__restrict__ fx, const double *__restrict__ fy,
+                                const double *__restrict__ fz, Dims df, double *__restrict__ cx,
+                                double *__restrict__ cy, double *__restrict__ cz, Dims dc) {
+  int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+  if (I >= dc.nx || J >= dc.ny) return;
+  int i = 2 * I, j = 2 * J, k = 2 * K;
+  size_t c = at(dc, I, J, K);
+  cx[c] = 0.25 * (fx[at(df, i, j, k)] + fx[at(df, i, j + 1, k)] + fx[at(df, i, j, k + 1)] +
+                  fx[at(df, i, j + 1, k + 1)]);
+  cy[c] = 0.25 * (fy[at(df, i, j, k)] + fy[at(df, i + 1, j, k)] + fy[at(df, i, j, k + 1)] +
+                  fy[at(df, i + 1, j, k + 1)]);
+  cz[c] = 0.25 * (fz[at(df, i, j, k)] + fz[at(df, i + 1, j, k)] + fz[at(df, i, j + 1, k)] +
+                  fz[at(df, i + 1, j + 1, k)]);
+}
+
+// ---------------------------------------------- A9: coarsest direct solve
+// Dense M = -At + 11^T/n (symmetric positive definite) as the left half of
+// [M | I] (row-major, n x 2n); one thread per row, each row written once.
+__global__ void k_dense_build(const double *__restrict__ bx, const double *__restrict__ by,
+                              const double *__restrict__ bz, const double *__restrict__ diag,
+                              double *__restrict__ M, Dims d) {
+  int n = d.nx * d.ny * d.nz;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int i = r % d.nx, j = (r / d.nx) % d.ny, k = r / (d.nx * d.ny);
+  double *row = M + (size_t)r * 2 * n;
+  double inv_n = 1.0 / n;
+  for (int c = 0; c < n; ++c) row[c] = inv_n;
+  for (int c = 0; c < n; ++c) row[n + c] = (c == r) ? 1.0 : 0.0;
+  row[r] += diag[r];
+  row[at(d, wlo(i, d.nx), j, k)] -= bx[r];
+  row[at(d, whi(i, d.nx), j, k)] -= bx[at(d, whi(i, d.nx), j, k)];
+  row[at(d, i, wlo(j, d.ny), k)] -= by[r];
+  row[at(d, i, whi(j, d.ny), k)] -= by[at(d, i, whi(j, d.ny), k)];
+  row[at(d, i, j, wlo(k, d.nz))] -= bz[r];
+  row[at(d, i, j, whi(k, d.nz))] -= bz[at(d, i, j, whi(k, d.nz))];
+}
+
+// Gauss-Jordan elimination of [M | I] -> [I | M^-1] by one block (M is SPD,
+// so no pivoting).  n <= 512.  The inverse (symmetric) is copied to Minv.
+__global__ void k_gauss_jordan(double *__restrict__ M, double *__restrict__ Minv, int n) {
+  __shared__ double col[512];
+  const int w = 2 * n;
+  for (int p = 0; p < n; ++p) {
+    for (int r = threadIdx.x; r < n; r += blockDim.x) col[r] = M[(size_t)r * w + p];
+    __syncthreads();
+    double inv = 1.0 / col[p];
+    for (int c = threadIdx.x; c < w; c += blockDim.x) M[(size_t)p * w + c] *= inv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
+      int r = e / w, c = e - r * w;
+      if (r != p) M[(size_t)r * w + c] -= col[r] * M[(size_t)p * w + c];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    Minv[e] = M[(size_t)r * w + n + c];
+  }
+}
+
+// e = M^-1 (-(b - mean b)), FP64 internally for any storage type T.
+// One block of 512 threads; n <= 512.
+template <typename T>
+__global__ void k_coarse_solve(const double *__restrict__ Minv, const T *__restrict__ b,
+                               T *__restrict__ e, int n) {
+  __shared__ double sb[512];
+  __shared__ double mean;
+  int t = threadIdx.x;
+  double v = t < n ? (double)b[t] : 0.0;
+  double s = block_sum(v);
+  if (t == 0) mean = s / n;
+  __syncthreads();
+  sb[t] = t < n ? v - mean : 0.0;
+  __syncthreads();
+  if (t < n) {
+    double acc = 0.0;
+    for (int c = 0; c < n; ++c) acc = fma(Minv[(size_t)c * n + t], sb[c], acc);
+    e[t] = (T)(-acc);
+  }
+}
+
+// ------------------------------------------------- A6: red-black smoother
+// One colour ((i+j+k) & 1 == colour): x_c = (sum_f beta_f x_nb - bt_c) / diag_c.
+// zero != 0 treats x as zero before the update (first sweep of a cycle).
+template <typename T>
+__global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__restrict__ bx,
+                       const T *__restrict__ by, const T *__restrict__ bz,
+                       const T *__restrict__ idiag, Dims d, int colour, int zero) {
+  int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (t >= (d.nx >> 1) || j >= d.ny) return;
+  int i = 2 * t + ((j + k + colour) & 1);
+  size_t c = at(d, i, j, k);
+  T s = -b[c];
+  if (!zero) {
+    size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
+    size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
+    size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+    s = fma(bx[c], x[xl], s);
+    s = fma(bx[xh], x[xh], s);
+    s = fma(by[c], x[yl], s);
+    s = fma(by[yh], x[yh], s);
+    s = fma(bz[c], x[zl], s);
+    s = fma(bz[zh], x[zh], s);
+  }
+  x[c] = s * idiag[c];
+}
+
+// scaled residual at one cell: rt = bt - sum_f beta_f x_nb + diag x_c
+template <typename T>
+__device__ __forceinline__ T resid_at(const T *__restrict__ x, const T *__restrict__ b,
+                                      const T *__restrict__ bx, const T *__restrict__ by,
+                                      const T *__restrict__ bz, const T *__restrict__ diag,
+                                      const Dims &d, int i, int j, int k) {
+  size_t c = at(d, i, j, k);
+  size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
+  size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
+  size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+  T s = -b[c];
+  s = fma(bx[c], x[xl], s);
+  s = fma(bx[xh], x[xh], s);
+  s = fma(by[c], x[yl], s);
+  s = fma(by[yh], x[yh], s);
+  s = fma(bz[c], x[zl], s);
+  s = fma(bz[zh], x[zh], s);
+  return fma(diag[c], x[c], -s);
+}
+
+// ------------------------------------- A7: residual + restriction (fused)
+// Coarse scaled rhs = (2h)^2 * mean of the 8 children's residuals
+//                   = 0.5 * sum of the children's scaled residuals.
+template <typename T>
+__global__ void k_resid_restrict(const T *__restrict__ x, const T *__restrict__ b,
+                                 const T *__restrict__ bx, const T *__restrict__ by,
+                                 const T *__restrict__ bz, const T *__restrict__ diag, Dims df,
+                                 T *__restrict__ bc, Dims dc) {
+  int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+  if (I >= dc.nx || J >= dc.ny) return;
+  T s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    s += resid_at(x, b, bx, by, bz, diag, df, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1),
+                  2 * K + (q >> 2));
+  bc[at(dc, I, J, K)] = (T)0.5 * s;
+}
+
+// ------------------------------------- A8: prolongation + correction
+// piecewise-constant: each fine cell adds its parent's correction
+template <typename T>
+__global__ void k_prolong(T *__restrict__ x, const T *__restrict__ ec, Dims df, Dims dc) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= df.nx || j >= df.ny) return;
+  x[at(df, i, j, k)] += ec[at(dc, i >> 1, j >> 1, k >> 1)];
+}
+
+// --------------------------------------------------------- Krylov kernels
+// Scalars kept on the device between kernels (no host round trip).
+enum { S_RZ = 0, S_RZOLD, S_DQ, S_ALPHA, S_BETA, S_RR, S_BB, S_MEAN, S_TMP, S_COUNT };
+enum { OP_STORE = 0, OP_ALPHA, OP_BETA, OP_MEAN };
+
+// q = At d; per-block partial of d.q
+template <typename T>
+__global__ void k_apply_dot(const T *__restrict__ dv, T *__restrict__ q, const T *__restrict__ bx,
+                            const T *__restrict__ by, const T *__restrict__ bz,
+                            const T *__restrict__ diag, Dims d, double *__restrict__ partial) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  double acc = 0.0;
+  if (i < d.nx && j < d.ny) {
+    size_t c = at(d, i, j, k);
+    size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
+    size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
+    size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+    T dc = dv[c];
+    T s = -diag[c] * dc;
+    s = fma(bx[c], dv[xl], s);
+    s = fma(bx[xh], dv[xh], s);
+    s = fma(by[c], dv[yl], s);
+    s = fma(by[yh], dv[yh], s);
+    s = fma(bz[c], dv[zl], s);
+    s = fma(bz[zh], dv[zh], s);
+    q[c] = s;
+    acc = (double)(s * dc);
+  }
+  double t = block_sum(acc);
+  if (thread0()) partial[block_linear_id()] = t;
+}
+
+// r = b - At x (scaled), per-block partial of r.r; zero != 0: x = 0, r = b.
+template <typename T>
+__global__ void k_residual(const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r,
+                           const T *__restrict__ bx, const T *__restrict__ by,
+                           const T *__restrict__ bz, const T *__restrict__ diag, Dims d,
+                           double *__restrict__ partial, int zero) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  double acc = 0.0;
+  if (i < d.nx && j < d.ny) {
+    size_t c = at(d, i, j, k);
+    T v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, d, i, j, k);
+    r[c] = v;
+    acc = (double)v * (double)v;
+  }
+  double t = block_sum(acc);
+  if (thread0()) partial[block_linear_id()] = t;
+}
+
+// mixed precision outer residual: r64 = b - At64 x64 (FP64), r32 = fl32(r64)
+__global__ void k_residual_mixed(const double *__restrict__ x, const double *__restrict__ b,
+                                 float *__restrict__ r32, const double *__restrict__ bx,
+                                 const double *__restrict__ by, const double *__restrict__ bz,
+                                 const double *__restrict__ diag, Dims d,
+                                 double *__restrict__ partial, int zero) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  double acc = 0.0;
+  if (i < d.nx && j < d.ny) {
+    size_t c = at(d, i, j, k);
+    double v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, d, i, j, k);
+    r32[c] = (float)v;
+    acc = v * v;
+  }
+  double t = block_sum(acc);
+  if (thread0()) partial[block_linear_id()] = t;
+}
+
+// Grid-stride vector kernels: fixed grid (deterministic partial order).
+constexpr int VEC_THREADS = 256;
+
+template <typename T>
+__global__ void k_dot(const T *__restrict__ a, const T *__restrict__ b, size_t n,
+                      double *__restrict__ partial) {
+  T acc = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    acc = fma(a[e], b[e], acc);
+  double t = block_sum((double)acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// x += alpha d; r -= alpha q; partial r.r
+template <typename T>
+__global__ void k_axpy2(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ dv,
+                        const T *__restrict__ q, size_t n, const double *__restrict__ scal,
+                        double *__restrict__ partial) {
+  T alpha = (T)scal[S_ALPHA];
+  T acc = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    x[e] = fma(alpha, dv[e], x[e]);
+    T rv = fma(-alpha, q[e], r[e]);
+    r[e] = rv;
+    acc = fma(rv, rv, acc);
+  }
+  double t = block_sum((double)acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// d = z + beta d (first iteration: d = z)
+template <typename T>
+__global__ void k_xpby(T *__restrict__ dv, const T *__restrict__ z, size_t n,
+                       const double *__restrict__ scal, int first) {
+  T beta = (T)scal[S_BETA];
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    dv[e] = first ? z[e] : fma(beta, dv[e], z[e]);
+}
+
+// x += y (stationary iteration update)
+template <typename T>
+__global__ void k_add(T *__restrict__ x, const T *__restrict__ y, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    x[e] += y[e];
+}
+
+// x64 += e32 (refinement step accumulation in FP64)
+__global__ void k_add_f32(double *__restrict__ x, const float *__restrict__ e, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    x[k] += (double)e[k];
+}
+
+template <typename T>
+__global__ void k_sum(const T *__restrict__ a, size_t n, double *__restrict__ partial) {
+  double acc = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    acc += (double)a[e];
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// x -= mean (scal[S_MEAN]); optional partial of the new x.x
+__global__ void k_sub_mean(double *__restrict__ x, size_t n, const double *__restrict__ scal,
+                           double *__restrict__ partial) {
+  double m = scal[S_MEAN];
+  double acc = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double v = x[e] - m;
+    x[e] = v;
+    acc = fma(v, v, acc);
+  }
+  double t = block_sum(acc);
+  if (partial != nullptr && threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// Single-block final reduction of the partials in a fixed order, then an
+// operation on the device scalars.
+__global__ void k_reduce(const double *__restrict__ partial, int np, double *__restrict__ scal,
+                         int op, int slot, double count) {
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) acc += partial[e];
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) {
+    switch (op) {
+      case OP_STORE: scal[slot] = s; break;
+      case OP_ALPHA: scal[S_DQ] = s; scal[S_ALPHA] = scal[S_RZ] / s; break;
+      case OP_BETA:
+        scal[S_RZOLD] = scal[S_RZ];
+        scal[S_RZ] = s;
+        scal[S_BETA] = s / scal[S_RZOLD];
+        break;
+      case OP_MEAN: scal[S_MEAN] = s / count; break;
+    }
+  }
+}
+
+// --------------------------------------------------------- assembly (A3)
+// bt = h^2 rhs + Jt; per-block partial sum (for the mean)
+__global__ void k_assemble(const double *__restrict__ rhs, const double *__restrict__ Jt,
+                           double *__restrict__ b, size_t n, double h2,
+                           double *__restrict__ partial) {
+  double acc = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double v = fma(h2, rhs[e], Jt[e]);
+    b[e] = v;
+    acc += v;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// bt = h^2 div_h u* + Jt = h * sum(u_high - u_low) + Jt, fused divergence
+__global__ void k_assemble_u(const double *__restrict__ ux, const double *__restrict__ uy,
+                             const double *__restrict__ uz, const double *__restrict__ Jt,
+                             double *__restrict__ b, Dims d, double h,
+                             double *__restrict__ partial) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  double acc = 0.0;
+  if (i < d.nx && j < d.ny) {
+    size_t c = at(d, i, j, k);
+    double s = ux[at(d, whi(i, d.nx), j, k)] - ux[c] + uy[at(d, i, whi(j, d.ny), k)] - uy[c] +
+               uz[at(d, i, j, whi(k, d.nz))] - uz[c];
+    double v = fma(h, s, Jt[c]);
+    b[c] = v;
+    acc = v;
+  }
+  double t = block_sum(acc);
+  if (thread0()) partial[block_linear_id()] = t;
+}
+
+// div_h u = sum over axes of (u_high - u_low) / h
+__global__ void k_divergence(const double *__restrict__ ux, const double *__restrict__ uy,
+                             const double *__restrict__ uz, double *__restrict__ dv, Dims d,
+                             double h) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nx || j >= d.ny) return;
+  size_t c = at(d, i, j, k);
+  double s = ux[at(d, whi(i, d.nx), j, k)] - ux[c] + uy[at(d, i, whi(j, d.ny), k)] - uy[c] +
+             uz[at(d, i, j, whi(k, d.nz))] - uz[c];
+  dv[c] = s / h;
+}
+
+// ------------------------------------------------- A15: velocity correction
+// u_f -= beta_f (p_b - p_a - [p]_{a->b}) / h on the three low faces of each
+// cell; wall faces have beta = 0 and keep u*.
+__global__ void k_project(const double *__restrict__ p, const double *__restrict__ phi,
+                          const double *__restrict__ kap, const double *__restrict__ bx,
+                          const double *__restrict__ by, const double *__restrict__ bz,
+                          double *__restrict__ ux, double *__restrict__ uy,
+                          double *__restrict__ uz, Dims d, double sig, double h) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nx || j >= d.ny) return;
+  size_t c = at(d, i, j, k);
+  double pc = p[c], fc = phi[c], kc = kap[c];
+  size_t xl = at(d, wlo(i, d.nx), j, k), yl = at(d, i, wlo(j, d.ny), k),
+         zl = at(d, i, j, wlo(k, d.nz));
+  ux[c] -= bx[c] * (pc - p[xl] - gfm_jump(phi[xl], fc, kap[xl], kc, sig)) / h;
+  uy[c] -= by[c] * (pc - p[yl] - gfm_jump(phi[yl], fc, kap[yl], kc, sig)) / h;
+  uz[c] -= bz[c] * (pc - p[zl] - gfm_jump(phi[zl], fc, kap[zl], kc, sig)) / h;
+}
+
+// y = scale * v (used to unscale J and the operator for the test API)
+__global__ void k_scale(const double *__restrict__ v, double *__restrict__ y, size_t n,
+                        double scale) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    y[e] = v[e] * scale;
+}
+
+}  // namespace mp

@@ -1,0 +1,834 @@
+// Host driver and C-ABI of the pressure-Poisson hot path (see include/mp_poisson.h).
+//
+// Solver: conjugate gradients on the h^2-scaled system At x = bt,
+// preconditioned by one symmetric geometric-multigrid V-cycle (red-black
+// Gauss-Seidel: red then black before the coarse correction, black then red
+// after; mean restriction; piecewise-constant prolongation; face-averaged
+// coarse coefficients; dense FP64 inverse on the coarsest level).  Mixed
+// precision wraps an FP32 inner solve in FP64 iterative refinement: the
+// outer residual, the solution accumulation and the coarsest solve are FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mp_poisson.h"
+#include "mp_kernels.cuh"
+
+using namespace mp;
+
+namespace {
+
+constexpr int MAX_COARSE = 512;
+constexpr int VEC_BLOCKS = 152 * 8;  // fixed grid for vector kernels (152 SMs)
+
+struct Level {
+  Dims d;
+  size_t n = 0;
+  int nu1 = 2, nu2 = 2;
+  double *bx = nullptr, *by = nullptr, *bz = nullptr, *diag = nullptr, *idiag = nullptr;
+  float *bx32 = nullptr, *by32 = nullptr, *bz32 = nullptr, *diag32 = nullptr, *idiag32 = nullptr;
+  double *b = nullptr, *e = nullptr;   // coarse-level rhs / correction (levels >= 1)
+  float *b32 = nullptr, *e32 = nullptr;
+};
+
+enum KernelId {
+  K_CURV, K_FACES, K_JUMP, K_DIAG, K_COARSEN, K_DENSE, K_GJ,
+  K_RBGS64, K_RBGS32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
+  K_APPLY64, K_APPLY32, K_RESID64, K_RESID32, K_RESIDMIX, K_DOT64, K_DOT32, K_AXPY64, K_AXPY32,
+  K_XPBY64, K_XPBY32, K_ADD64, K_ADD32, K_ADDF32, K_SUM, K_SUBMEAN, K_REDUCE, K_ASSEMBLE,
+  K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_COUNT
+};
+const char *const kKernelNames[K_COUNT] = {
+  "curvature", "gfm_faces", "jump", "diag", "coarsen_faces", "dense_build", "gauss_jordan",
+  "rbgs_f64", "rbgs_f32", "resid_restrict_f64", "resid_restrict_f32", "prolong_f64",
+  "prolong_f32", "coarse_solve_f64", "coarse_solve_f32io", "apply_dot_f64", "apply_dot_f32",
+  "residual_f64", "residual_f32", "residual_mixed", "dot_f64", "dot_f32", "axpy2_f64",
+  "axpy2_f32", "xpby_f64", "xpby_f32", "add_f64", "add_f32", "add_f32_to_f64", "sum",
+  "sub_mean", "reduce", "assemble", "assemble_u", "project", "divergence", "scale"};
+constexpr int MAX_LEVELS = 16;
+constexpr int EVENT_POOL = 4096;
+
+struct ProfEntry {
+  long long launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+struct Pending {
+  int id, level;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+}  // namespace
+
+struct mp_poisson {
+  mp_grid g{};
+  int per = 0;
+  double h = 1.0, rho_l = 1.0, rho_g = 1.0, sigma = 0.0;
+  mp_opts opts{};
+  cudaStream_t st = nullptr;
+  std::vector<Level> L;
+  size_t n = 0;
+  // fine-level FP64 fields
+  double *phi = nullptr, *kap = nullptr, *Jt = nullptr, *b = nullptr;
+  double *r = nullptr, *z = nullptr, *dv = nullptr, *q = nullptr;
+  // fine-level FP32 inner-solve vectors
+  float *r32 = nullptr, *e32 = nullptr, *z32 = nullptr, *d32 = nullptr, *q32 = nullptr;
+  // host-buffer step staging
+  double *ux = nullptr, *uy = nullptr, *uz = nullptr, *pst = nullptr;
+  // coarsest level
+  double *Maug = nullptr, *Minv = nullptr;
+  int nc = 0;
+  // reductions
+  double *partial = nullptr, *scal = nullptr, *scal_h = nullptr;
+  int npart = 0;
+  double bnorm = 0.0;
+  mp_stats stats{};
+  std::vector<void *> allocs;
+  // launch accounting / CUDA-event profiling
+  ProfEntry prof[K_COUNT][MAX_LEVELS];
+  int prof_on = 0;
+  std::vector<cudaEvent_t> events;
+  size_t ev_next = 0;
+  std::vector<Pending> pending;
+};
+
+namespace {
+
+#define CK(call)                                    \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return MP_ERR_CUDA;      \
+  } while (0)
+#define CKS(call)                       \
+  do {                                  \
+    mp_status s_ = (call);              \
+    if (s_ != MP_OK) return s_;         \
+  } while (0)
+
+dim3 cell_grid(const Dims &d) { return dim3((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, d.nz); }
+dim3 half_grid(const Dims &d) {
+  return dim3(((d.nx >> 1) + BX - 1) / BX, (d.ny + BY - 1) / BY, d.nz);
+}
+int cell_blocks(const Dims &d) {
+  dim3 g = cell_grid(d);
+  return (int)(g.x * g.y * g.z);
+}
+const dim3 kBlock(BX, BY, 1);
+
+template <typename T>
+mp_status dalloc(mp_poisson *hd, T **p, size_t count) {
+  void *v = nullptr;
+  if (cudaMalloc(&v, count * sizeof(T) + 16) != cudaSuccess) {
+    cudaGetLastError();
+    return MP_ERR_OOM;
+  }
+  hd->allocs.push_back(v);
+  *p = (T *)v;
+  return MP_OK;
+}
+
+mp_status launch_ok() { return cudaGetLastError() == cudaSuccess ? MP_OK : MP_ERR_CUDA; }
+
+// Resolve recorded event pairs into per-kernel times (stream must be idle).
+void prof_resolve(mp_poisson *hd) {
+  for (const Pending &p : hd->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      hd->prof[p.id][p.level].ms += ms;
+      hd->prof[p.id][p.level].bytes += p.bytes;
+    }
+  }
+  hd->pending.clear();
+  hd->ev_next = 0;
+}
+
+void prof_begin(mp_poisson *hd, int id, int level) {
+  hd->prof[id][level].launches++;
+  if (!hd->prof_on) return;
+  if (hd->ev_next + 2 > hd->events.size()) {
+    cudaStreamSynchronize(hd->st);
+    prof_resolve(hd);
+  }
+  cudaEventRecord(hd->events[hd->ev_next], hd->st);
+}
+
+void prof_end(mp_poisson *hd, int id, int level, double bytes) {
+  if (!hd->prof_on) return;
+  cudaEvent_t a = hd->events[hd->ev_next], b = hd->events[hd->ev_next + 1];
+  cudaEventRecord(b, hd->st);
+  hd->ev_next += 2;
+  hd->pending.push_back(Pending{id, level, a, b, bytes});
+}
+
+// Launch on the handle's stream, counted per (kernel, level) and, when
+// profiling is on, bracketed by CUDA events.  BYTES is the algorithmic
+// traffic of the launch (unique bytes it must read and write).
+#define LAUNCH(hd, id, level, bytes, kern, grid, block, ...)      \
+  do {                                                            \
+    prof_begin((hd), (id), (level));                              \
+    kern<<<(grid), (block), 0, (hd)->st>>>(__VA_ARGS__);          \
+    prof_end((hd), (id), (level), (double)(bytes));               \
+  } while (0)
+
+template <typename T>
+constexpr int kid(int id64, int id32) {
+  return sizeof(T) == 8 ? id64 : id32;
+}
+
+// ---- reductions
+mp_status reduce(mp_poisson *hd, int np, int op, int slot, double count = 0.0) {
+  LAUNCH(hd, K_REDUCE, 0, np * 8.0, k_reduce, 1, 1024, hd->partial, np, hd->scal, op, slot, count);
+  return launch_ok();
+}
+
+mp_status read_scalars(mp_poisson *hd) {
+  CK(cudaMemcpyAsync(hd->scal_h, hd->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                     hd->st));
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+// ---- per-precision level accessors
+template <typename T> struct LV;
+template <> struct LV<double> {
+  static double *bx(Level &l) { return l.bx; }
+  static double *by(Level &l) { return l.by; }
+  static double *bz(Level &l) { return l.bz; }
+  static double *diag(Level &l) { return l.diag; }
+  static double *idiag(Level &l) { return l.idiag; }
+  static double *b(Level &l) { return l.b; }
+  static double *e(Level &l) { return l.e; }
+};
+template <> struct LV<float> {
+  static float *bx(Level &l) { return l.bx32; }
+  static float *by(Level &l) { return l.by32; }
+  static float *bz(Level &l) { return l.bz32; }
+  static float *diag(Level &l) { return l.diag32; }
+  static float *idiag(Level &l) { return l.idiag32; }
+  static float *b(Level &l) { return l.b32; }
+  static float *e(Level &l) { return l.e32; }
+};
+
+// One symmetric V-cycle with zero initial guess: x ~= At^-1 rhs on level l.
+template <typename T>
+mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
+  Level &lv = hd->L[l];
+  if (l == (int)hd->L.size() - 1) {
+    LAUNCH(hd, kid<T>(K_COARSE64, K_COARSE32), l, lv.n * (lv.n * 8.0 + 2.0 * sizeof(T)),
+           k_coarse_solve<T>, 1, 512, hd->Minv, rhs, x, (int)lv.n);
+    return launch_ok();
+  }
+  Level &lc = hd->L[l + 1];
+  T *bx = LV<T>::bx(lv), *by = LV<T>::by(lv), *bz = LV<T>::bz(lv);
+  T *diag = LV<T>::diag(lv), *idiag = LV<T>::idiag(lv);
+  dim3 hg = half_grid(lv.d);
+  const int krb = kid<T>(K_RBGS64, K_RBGS32);
+  const double sz = sizeof(T), nl = (double)lv.n;
+  for (int s = 0; s < lv.nu1; ++s) {
+    LAUNCH(hd, krb, l, (s == 0 ? 4.5 : 5.0) * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz,
+           idiag, lv.d, 0, s == 0);
+    LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1, 0);
+  }
+  LAUNCH(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
+         cell_grid(lc.d), kBlock, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
+  CKS(launch_ok());
+  CKS(vcycle<T>(hd, l + 1, LV<T>::b(lc), LV<T>::e(lc)));
+  LAUNCH(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong<T>, cell_grid(lv.d),
+         kBlock, x, LV<T>::e(lc), lv.d, lc.d);
+  for (int s = 0; s < lv.nu2; ++s) {
+    LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1, 0);
+    LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 0, 0);
+  }
+  return launch_ok();
+}
+
+bool bad(double v) { return !std::isfinite(v); }
+
+// Preconditioned CG on At x = (rhs), starting from x with residual r already
+// formed and scal[S_RR] = r.r.  Stops when sqrt(r.r) <= tol_abs or after
+// maxit iterations.  hist (may be null) receives sqrt(r.r)/bnorm.
+template <typename T>
+mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int maxit,
+              int *iters, std::vector<double> *hist, double hist_scale) {
+  Level &l0 = hd->L[0];
+  T *bx = LV<T>::bx(l0), *by = LV<T>::by(l0), *bz = LV<T>::bz(l0), *diag = LV<T>::diag(l0);
+  size_t n = hd->n;
+  int it = 0;
+  CKS(read_scalars(hd));
+  double rn = std::sqrt(hd->scal_h[S_RR]);
+  while (true) {
+    if (bad(rn)) return MP_ERR_DIVERGED;
+    if (rn <= tol_abs) break;
+    if (it >= maxit) {
+      *iters = it;
+      return MP_ERR_NOT_CONVERGED;
+    }
+    CKS(vcycle<T>(hd, 0, r, z));
+    const double nsz = (double)n * sizeof(T);
+    LAUNCH(hd, kid<T>(K_DOT64, K_DOT32), 0, 2.0 * nsz, k_dot<T>, VEC_BLOCKS, VEC_THREADS, r, z, n,
+           hd->partial);
+    CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
+    LAUNCH(hd, kid<T>(K_XPBY64, K_XPBY32), 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<T>, VEC_BLOCKS,
+           VEC_THREADS, dv, z, n, hd->scal, it == 0);
+    LAUNCH(hd, kid<T>(K_APPLY64, K_APPLY32), 0, 6.0 * nsz, k_apply_dot<T>, cell_grid(l0.d), kBlock,
+           dv, q, bx, by, bz, diag, l0.d, hd->partial);
+    CKS(reduce(hd, cell_blocks(l0.d), OP_ALPHA, 0));
+    LAUNCH(hd, kid<T>(K_AXPY64, K_AXPY32), 0, 6.0 * nsz, k_axpy2<T>, VEC_BLOCKS, VEC_THREADS, x,
+           r, dv, q, n, hd->scal, hd->partial);
+    CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
+    ++it;
+    CKS(read_scalars(hd));
+    rn = std::sqrt(hd->scal_h[S_RR]);
+    if (hist) hist->push_back(rn * hist_scale);
+  }
+  *iters = it;
+  return MP_OK;
+}
+
+// Stationary V-cycle iteration: x += V(r); r = bt - At x.
+template <typename T>
+mp_status stationary(mp_poisson *hd, T *x, const T *bt, T *r, T *z, double tol_abs, int maxit,
+                     int *iters, std::vector<double> *hist, double hist_scale) {
+  Level &l0 = hd->L[0];
+  T *bx = LV<T>::bx(l0), *by = LV<T>::by(l0), *bz = LV<T>::bz(l0), *diag = LV<T>::diag(l0);
+  int it = 0;
+  CKS(read_scalars(hd));
+  double rn = std::sqrt(hd->scal_h[S_RR]);
+  while (true) {
+    if (bad(rn)) return MP_ERR_DIVERGED;
+    if (rn <= tol_abs) break;
+    if (it >= maxit) {
+      *iters = it;
+      return MP_ERR_NOT_CONVERGED;
+    }
+    CKS(vcycle<T>(hd, 0, r, z));
+    const double nsz = (double)hd->n * sizeof(T);
+    LAUNCH(hd, kid<T>(K_ADD64, K_ADD32), 0, 3.0 * nsz, k_add<T>, VEC_BLOCKS, VEC_THREADS, x, z,
+           hd->n);
+    LAUNCH(hd, kid<T>(K_RESID64, K_RESID32), 0, 7.0 * nsz, k_residual<T>, cell_grid(l0.d), kBlock,
+           x, bt, r, bx, by, bz, diag, l0.d, hd->partial, 0);
+    CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+    ++it;
+    CKS(read_scalars(hd));
+    rn = std::sqrt(hd->scal_h[S_RR]);
+    if (hist) hist->push_back(rn * hist_scale);
+  }
+  *iters = it;
+  return MP_OK;
+}
+
+// mean removal of a device FP64 vector (gauge)
+mp_status remove_mean(mp_poisson *hd, double *x) {
+  LAUNCH(hd, K_SUM, 0, hd->n * 8.0, k_sum<double>, VEC_BLOCKS, VEC_THREADS, x, hd->n, hd->partial);
+  CKS(reduce(hd, VEC_BLOCKS, OP_MEAN, 0, (double)hd->n));
+  LAUNCH(hd, K_SUBMEAN, 0, hd->n * 16.0, k_sub_mean, VEC_BLOCKS, VEC_THREADS, x, hd->n, hd->scal,
+         nullptr);
+  return launch_ok();
+}
+
+// bt (already holding h^2 rhs + Jt with block sums in partial, np blocks)
+// -> subtract mean, store ||bt||^2 in S_BB
+mp_status finish_rhs(mp_poisson *hd, int np) {
+  CKS(reduce(hd, np, OP_MEAN, 0, (double)hd->n));
+  LAUNCH(hd, K_SUBMEAN, 0, hd->n * 16.0, k_sub_mean, VEC_BLOCKS, VEC_THREADS, hd->b, hd->n,
+         hd->scal, hd->partial);
+  CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_BB));
+  return launch_ok();
+}
+
+mp_status assemble_rhs(mp_poisson *hd, const double *rhs) {
+  LAUNCH(hd, K_ASSEMBLE, 0, hd->n * 24.0, k_assemble, VEC_BLOCKS, VEC_THREADS, rhs, hd->Jt, hd->b,
+         hd->n, hd->h * hd->h, hd->partial);
+  CKS(launch_ok());
+  return finish_rhs(hd, VEC_BLOCKS);
+}
+
+mp_status assemble_rhs_u(mp_poisson *hd, const double *ux, const double *uy, const double *uz) {
+  Level &l0 = hd->L[0];
+  LAUNCH(hd, K_ASSEMBLE_U, 0, hd->n * 40.0, k_assemble_u, cell_grid(l0.d), kBlock, ux, uy, uz,
+         hd->Jt, hd->b, l0.d, hd->h, hd->partial);
+  CKS(launch_ok());
+  return finish_rhs(hd, cell_blocks(l0.d));
+}
+
+// Solve At p = bt (bt in hd->b, S_BB set).  p: device FP64, in/out.
+mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<double> *hist) {
+  Level &l0 = hd->L[0];
+  const mp_opts &o = hd->opts;
+  CKS(read_scalars(hd));
+  hd->bnorm = std::sqrt(hd->scal_h[S_BB]);
+  hd->stats = mp_stats{};
+  hd->stats.levels = (int)hd->L.size();
+  hd->stats.coarse_n = hd->nc;
+  if (o.initial_guess == 2) return MP_ERR_NO_NET;
+  int zero = o.initial_guess == 0;
+  if (zero) CK(cudaMemsetAsync(p, 0, hd->n * sizeof(double), hd->st));
+  if (hd->bnorm == 0.0) {
+    CK(cudaMemsetAsync(p, 0, hd->n * sizeof(double), hd->st));
+    CK(cudaStreamSynchronize(hd->st));
+    if (hist) hist->push_back(0.0);
+    return MP_OK;
+  }
+  double inv_b = 1.0 / hd->bnorm;
+  double tol_abs = tol * hd->bnorm;
+  mp_status st = MP_OK;
+  int iters = 0;
+  if (o.precision == 0) {
+    LAUNCH(hd, K_RESID64, 0, hd->n * (zero ? 16.0 : 56.0), k_residual<double>, cell_grid(l0.d),
+           kBlock, p, hd->b, hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial, zero);
+    CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+    CKS(read_scalars(hd));
+    hd->stats.r0 = std::sqrt(hd->scal_h[S_RR]) * inv_b;
+    if (hist) hist->push_back(hd->stats.r0);
+    if (o.method == 0)
+      st = pcg<double>(hd, p, hd->r, hd->z, hd->dv, hd->q, tol_abs, o.max_iters, &iters, hist,
+                       inv_b);
+    else
+      st = stationary<double>(hd, p, hd->b, hd->r, hd->z, tol_abs, o.max_iters, &iters, hist,
+                              inv_b);
+    hd->stats.iterations = iters;
+    hd->stats.outer_steps = iters;
+  } else {
+    // FP64 iterative refinement around an FP32 inner solve
+    LAUNCH(hd, K_RESIDMIX, 0, hd->n * (zero ? 12.0 : 52.0), k_residual_mixed, cell_grid(l0.d),
+           kBlock, p, hd->b, hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial, zero);
+    CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+    CKS(read_scalars(hd));
+    double rn = std::sqrt(hd->scal_h[S_RR]);
+    hd->stats.r0 = rn * inv_b;
+    if (hist) hist->push_back(hd->stats.r0);
+    int total = 0, outer = 0;
+    while (true) {
+      if (bad(rn)) { st = MP_ERR_DIVERGED; break; }
+      if (rn <= tol_abs) { st = MP_OK; break; }
+      if (total >= o.max_iters) { st = MP_ERR_NOT_CONVERGED; break; }
+      int inner = 0;
+      CK(cudaMemsetAsync(hd->e32, 0, hd->n * sizeof(float), hd->st));
+      if (o.method == 0) {
+        double inner_tol = std::fmax(o.inner_rtol * rn, 0.25 * tol_abs);
+        int cap = std::min(o.inner_max, o.max_iters - total);
+        mp_status si = pcg<float>(hd, hd->e32, hd->r32, hd->z32, hd->d32, hd->q32, inner_tol,
+                                  cap, &inner, nullptr, 0.0);
+        if (si == MP_ERR_DIVERGED) { st = si; break; }
+        if (si != MP_OK && si != MP_ERR_NOT_CONVERGED) return si;
+      } else {
+        CKS(vcycle<float>(hd, 0, hd->r32, hd->e32));
+        inner = 1;
+      }
+      total += inner;
+      ++outer;
+      LAUNCH(hd, K_ADDF32, 0, hd->n * 20.0, k_add_f32, VEC_BLOCKS, VEC_THREADS, p, hd->e32,
+             hd->n);
+      LAUNCH(hd, K_RESIDMIX, 0, hd->n * 52.0, k_residual_mixed, cell_grid(l0.d), kBlock, p, hd->b,
+             hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial, 0);
+      CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+      CKS(read_scalars(hd));
+      rn = std::sqrt(hd->scal_h[S_RR]);
+      if (hist) hist->push_back(rn * inv_b);
+    }
+    hd->stats.iterations = total;
+    hd->stats.outer_steps = outer;
+  }
+  if (st == MP_OK || st == MP_ERR_NOT_CONVERGED) {
+    CKS(remove_mean(hd, p));
+    // final true FP64 residual of the returned p
+    LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, cell_grid(l0.d), kBlock, p, hd->b,
+           hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial, 0);
+    CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+    CKS(read_scalars(hd));
+    hd->stats.relres = std::sqrt(hd->scal_h[S_RR]) * inv_b;
+  }
+  return st;
+}
+
+bool valid_opts(const mp_opts &o) {
+  return (o.precision == 0 || o.precision == 1) && (o.method == 0 || o.method == 1) &&
+         o.initial_guess >= 0 && o.initial_guess <= 2 && o.max_iters >= 0 && o.nu1 >= 1 &&
+         o.nu2 >= 1 && o.nu_growth >= 1 && o.nu_max >= 1 && o.inner_rtol > 0.0 &&
+         o.inner_rtol < 1.0 && o.inner_max >= 1;
+}
+
+void apply_nu(mp_poisson *hd) {
+  long f = 1;
+  for (size_t l = 0; l < hd->L.size(); ++l) {
+    hd->L[l].nu1 = (int)std::min<long>(hd->opts.nu_max, (long)hd->opts.nu1 * f);
+    hd->L[l].nu2 = (int)std::min<long>(hd->opts.nu_max, (long)hd->opts.nu2 * f);
+    f = std::min<long>(f * hd->opts.nu_growth, 1L << 20);
+  }
+}
+
+mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g, double sigma) {
+  if (!phi || !(rho_l > 0.0) || !(rho_g > 0.0) || !(sigma >= 0.0) || !std::isfinite(rho_l) ||
+      !std::isfinite(rho_g) || !std::isfinite(sigma))
+    return MP_ERR_INVALID_ARG;
+  hd->rho_l = rho_l;
+  hd->rho_g = rho_g;
+  hd->sigma = sigma;
+  Level &l0 = hd->L[0];
+  CK(cudaMemcpyAsync(hd->phi, phi, hd->n * sizeof(double), cudaMemcpyDeviceToDevice, hd->st));
+  const double n0 = (double)hd->n;
+  LAUNCH(hd, K_CURV, 0, n0 * 16.0, k_curvature, cell_grid(l0.d), kBlock, hd->phi, hd->kap, l0.d,
+         hd->h, hd->per);
+  LAUNCH(hd, K_FACES, 0, n0 * 32.0, k_faces, cell_grid(l0.d), kBlock, hd->phi, l0.bx, l0.by,
+         l0.bz, l0.d, rho_l, rho_g, hd->per);
+  LAUNCH(hd, K_JUMP, 0, n0 * 48.0, k_jump, cell_grid(l0.d), kBlock, hd->phi, hd->kap, l0.bx,
+         l0.by, l0.bz, hd->Jt, l0.d, sigma);
+  CKS(launch_ok());
+  for (size_t l = 0; l < hd->L.size(); ++l) {
+    Level &lv = hd->L[l];
+    if (l > 0) {
+      Level &lf = hd->L[l - 1];
+      LAUNCH(hd, K_COARSEN, (int)l, lv.n * 120.0, k_coarsen_faces, cell_grid(lv.d), kBlock, lf.bx,
+             lf.by, lf.bz, lf.d, lv.bx, lv.by, lv.bz, lv.d);
+    }
+    LAUNCH(hd, K_DIAG, (int)l, lv.n * 60.0, k_diag, cell_grid(lv.d), kBlock, lv.bx, lv.by, lv.bz,
+           lv.diag, lv.idiag, lv.bx32, lv.by32, lv.bz32, lv.diag32, lv.idiag32, lv.d);
+    CKS(launch_ok());
+  }
+  Level &lc = hd->L.back();
+  const int lcl = (int)hd->L.size() - 1;
+  const double nc = (double)hd->nc;
+  LAUNCH(hd, K_DENSE, lcl, nc * 2.0 * nc * 8.0, k_dense_build, (hd->nc + 127) / 128, 128, lc.bx,
+         lc.by, lc.bz, lc.diag, hd->Maug, lc.d);
+  LAUNCH(hd, K_GJ, lcl, nc * 3.0 * nc * 8.0, k_gauss_jordan, 1, 1024, hd->Maug, hd->Minv, hd->nc);
+  CKS(launch_ok());
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
+  int dims[3] = {g.nx, g.ny, g.nz};
+  hd->g = g;
+  hd->h = h;
+  hd->per = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (bc[a] != MP_BC_PERIODIC && bc[a] != MP_BC_NEUMANN) return MP_ERR_INVALID_ARG;
+    if (dims[a] < 2 || dims[a] > (1 << 16)) return MP_ERR_INVALID_ARG;
+    if (bc[a] == MP_BC_PERIODIC) {
+      if (dims[a] & 1) return MP_ERR_INVALID_ARG;
+      hd->per |= 1 << a;
+    }
+  }
+  if (!(h > 0.0) || !std::isfinite(h)) return MP_ERR_INVALID_ARG;
+  // hierarchy
+  Dims d{g.nx, g.ny, g.nz};
+  while (true) {
+    Level lv;
+    lv.d = d;
+    lv.n = (size_t)d.nx * d.ny * d.nz;
+    hd->L.push_back(lv);
+    // halve while every dim is even and >= 4 and the level has more than 64 cells
+    bool can = (d.nx % 2 == 0) && (d.ny % 2 == 0) && (d.nz % 2 == 0) && d.nx >= 4 && d.ny >= 4 &&
+               d.nz >= 4 && (size_t)d.nx * d.ny * d.nz > 64;
+    if (!can) break;
+    d = Dims{d.nx / 2, d.ny / 2, d.nz / 2};
+  }
+  hd->nc = (int)hd->L.back().n;
+  if (hd->nc > MAX_COARSE) return MP_ERR_INVALID_ARG;
+  // a level that is smoothed must have even x (red-black pairs along x)
+  for (size_t l = 0; l + 1 < hd->L.size(); ++l)
+    if (hd->L[l].d.nx & 1) return MP_ERR_INVALID_ARG;
+  hd->n = hd->L[0].n;
+  size_t n = hd->n;
+  for (size_t l = 0; l < hd->L.size(); ++l) {
+    Level &lv = hd->L[l];
+    CKS(dalloc(hd, &lv.bx, lv.n));
+    CKS(dalloc(hd, &lv.by, lv.n));
+    CKS(dalloc(hd, &lv.bz, lv.n));
+    CKS(dalloc(hd, &lv.diag, lv.n));
+    CKS(dalloc(hd, &lv.idiag, lv.n));
+    CKS(dalloc(hd, &lv.bx32, lv.n));
+    CKS(dalloc(hd, &lv.by32, lv.n));
+    CKS(dalloc(hd, &lv.bz32, lv.n));
+    CKS(dalloc(hd, &lv.diag32, lv.n));
+    CKS(dalloc(hd, &lv.idiag32, lv.n));
+    if (l > 0) {
+      CKS(dalloc(hd, &lv.b, lv.n));
+      CKS(dalloc(hd, &lv.e, lv.n));
+      CKS(dalloc(hd, &lv.b32, lv.n));
+      CKS(dalloc(hd, &lv.e32, lv.n));
+    }
+  }
+  CKS(dalloc(hd, &hd->phi, n));
+  CKS(dalloc(hd, &hd->kap, n));
+  CKS(dalloc(hd, &hd->Jt, n));
+  CKS(dalloc(hd, &hd->b, n));
+  CKS(dalloc(hd, &hd->r, n));
+  CKS(dalloc(hd, &hd->z, n));
+  CKS(dalloc(hd, &hd->dv, n));
+  CKS(dalloc(hd, &hd->q, n));
+  CKS(dalloc(hd, &hd->r32, n));
+  CKS(dalloc(hd, &hd->e32, n));
+  CKS(dalloc(hd, &hd->z32, n));
+  CKS(dalloc(hd, &hd->d32, n));
+  CKS(dalloc(hd, &hd->q32, n));
+  CKS(dalloc(hd, &hd->ux, n));
+  CKS(dalloc(hd, &hd->uy, n));
+  CKS(dalloc(hd, &hd->uz, n));
+  CKS(dalloc(hd, &hd->pst, n));
+  CKS(dalloc(hd, &hd->Maug, (size_t)hd->nc * 2 * hd->nc));
+  CKS(dalloc(hd, &hd->Minv, (size_t)hd->nc * hd->nc));
+  hd->npart = std::max(cell_blocks(hd->L[0].d), VEC_BLOCKS);
+  CKS(dalloc(hd, &hd->partial, (size_t)hd->npart));
+  CKS(dalloc(hd, &hd->scal, (size_t)S_COUNT));
+  if (cudaMallocHost((void **)&hd->scal_h, S_COUNT * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    hd->scal_h = nullptr;
+    return MP_ERR_OOM;
+  }
+  CK(cudaMemsetAsync(hd->scal, 0, S_COUNT * sizeof(double), hd->st));
+  return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mp_opts_default(mp_opts *o) {
+  if (!o) return;
+  o->precision = 0;
+  o->method = 0;
+  o->initial_guess = 0;
+  o->max_iters = 200;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->nu_growth = 2;
+  o->nu_max = 16;
+  o->inner_rtol = 1e-4;
+  o->inner_max = 12;
+  o->stream = nullptr;
+}
+
+const char *mp_status_str(mp_status s) {
+  switch (s) {
+    case MP_OK: return "ok";
+    case MP_ERR_INVALID_ARG: return "invalid argument";
+    case MP_ERR_NOT_CONVERGED: return "not converged (max_iters reached)";
+    case MP_ERR_DIVERGED: return "diverged (non-finite residual)";
+    case MP_ERR_CUDA: return "CUDA error";
+    case MP_ERR_OOM: return "out of memory";
+    case MP_ERR_TIMEOUT: return "device wait timed out";
+    case MP_ERR_NO_NET: return "learned initial guess requested but no network is set";
+  }
+  return "unknown status";
+}
+
+mp_status mp_poisson_setup(mp_handle *out, mp_grid g, double h, const mp_bc bc[3],
+                           const double *phi_dev, double rho_l, double rho_g, double sigma,
+                           const mp_opts *opts) {
+  if (!out || !bc || !phi_dev) return MP_ERR_INVALID_ARG;
+  *out = nullptr;
+  mp_opts o;
+  mp_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_opts(o)) return MP_ERR_INVALID_ARG;
+  mp_poisson *hd = new (std::nothrow) mp_poisson();
+  if (!hd) return MP_ERR_OOM;
+  hd->opts = o;
+  hd->st = (cudaStream_t)o.stream;
+  mp_status s = create(hd, g, h, bc);
+  if (s == MP_OK) {
+    apply_nu(hd);
+    s = geometry(hd, phi_dev, rho_l, rho_g, sigma);
+  }
+  if (s != MP_OK) {
+    mp_poisson_destroy(hd);
+    return s;
+  }
+  *out = hd;
+  return MP_OK;
+}
+
+mp_status mp_poisson_set_geometry(mp_handle hd, const double *phi_dev, double rho_l, double rho_g,
+                                  double sigma) {
+  if (!hd) return MP_ERR_INVALID_ARG;
+  return geometry(hd, phi_dev, rho_l, rho_g, sigma);
+}
+
+mp_status mp_poisson_set_opts(mp_handle hd, const mp_opts *opts) {
+  if (!hd || !opts || !valid_opts(*opts)) return MP_ERR_INVALID_ARG;
+  hd->opts = *opts;
+  hd->st = (cudaStream_t)opts->stream;
+  apply_nu(hd);
+  return MP_OK;
+}
+
+mp_status mp_poisson_solve(mp_handle hd, const double *rhs_dev, double *p_dev, double tol,
+                           int *iterations, double *res_hist, int res_hist_cap,
+                           int *res_hist_len) {
+  if (!hd || !rhs_dev || !p_dev || !(tol > 0.0) || res_hist_cap < 0 ||
+      (res_hist_cap > 0 && !res_hist))
+    return MP_ERR_INVALID_ARG;
+  std::vector<double> hist;
+  CKS(assemble_rhs(hd, rhs_dev));
+  mp_status s = solve_assembled(hd, p_dev, tol, &hist);
+  if (iterations) *iterations = hd->stats.iterations;
+  int m = std::min<int>((int)hist.size(), res_hist_cap);
+  for (int i = 0; i < m; ++i) res_hist[i] = hist[i];
+  if (res_hist_len) *res_hist_len = m;
+  return s;
+}
+
+mp_status mp_poisson_project_step(mp_handle hd, double *ux, double *uy, double *uz, double *p,
+                                  double tol, int *iterations) {
+  if (!hd || !ux || !uy || !uz || !p || !(tol > 0.0)) return MP_ERR_INVALID_ARG;
+  CKS(assemble_rhs_u(hd, ux, uy, uz));
+  mp_status s = solve_assembled(hd, p, tol, nullptr);
+  if (iterations) *iterations = hd->stats.iterations;
+  if (s != MP_OK) return s;
+  Level &l0 = hd->L[0];
+  LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
+         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, hd->h);
+  CKS(launch_ok());
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+mp_status mp_poisson_project_step_host(mp_handle hd, double *ux_h, double *uy_h, double *uz_h,
+                                       double *p_h, double tol, int *iterations) {
+  if (!hd || !ux_h || !uy_h || !uz_h || !p_h || !(tol > 0.0)) return MP_ERR_INVALID_ARG;
+  size_t bytes = hd->n * sizeof(double);
+  CK(cudaMemcpyAsync(hd->ux, ux_h, bytes, cudaMemcpyHostToDevice, hd->st));
+  CK(cudaMemcpyAsync(hd->uy, uy_h, bytes, cudaMemcpyHostToDevice, hd->st));
+  CK(cudaMemcpyAsync(hd->uz, uz_h, bytes, cudaMemcpyHostToDevice, hd->st));
+  if (hd->opts.initial_guess == 1)
+    CK(cudaMemcpyAsync(hd->pst, p_h, bytes, cudaMemcpyHostToDevice, hd->st));
+  mp_status s = mp_poisson_project_step(hd, hd->ux, hd->uy, hd->uz, hd->pst, tol, iterations);
+  if (s != MP_OK) return s;
+  CK(cudaMemcpyAsync(ux_h, hd->ux, bytes, cudaMemcpyDeviceToHost, hd->st));
+  CK(cudaMemcpyAsync(uy_h, hd->uy, bytes, cudaMemcpyDeviceToHost, hd->st));
+  CK(cudaMemcpyAsync(uz_h, hd->uz, bytes, cudaMemcpyDeviceToHost, hd->st));
+  CK(cudaMemcpyAsync(p_h, hd->pst, bytes, cudaMemcpyDeviceToHost, hd->st));
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+mp_status mp_poisson_apply(mp_handle hd, const double *x, double *y) {
+  if (!hd || !x || !y) return MP_ERR_INVALID_ARG;
+  Level &l0 = hd->L[0];
+  LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, cell_grid(l0.d), kBlock, x, y,
+         l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial);
+  LAUNCH(hd, K_SCALE, 0, hd->n * 16.0, k_scale, VEC_BLOCKS, VEC_THREADS, y, y, hd->n,
+         1.0 / (hd->h * hd->h));
+  CKS(launch_ok());
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+mp_status mp_poisson_divergence(mp_handle hd, const double *ux, const double *uy,
+                                const double *uz, double *dv) {
+  if (!hd || !ux || !uy || !uz || !dv) return MP_ERR_INVALID_ARG;
+  Level &l0 = hd->L[0];
+  LAUNCH(hd, K_DIV, 0, hd->n * 32.0, k_divergence, cell_grid(l0.d), kBlock, ux, uy, uz, dv, l0.d,
+         hd->h);
+  CKS(launch_ok());
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+mp_status mp_poisson_rhs(mp_handle hd, const double *rhs, double *b) {
+  if (!hd || !rhs || !b) return MP_ERR_INVALID_ARG;
+  CKS(assemble_rhs(hd, rhs));
+  LAUNCH(hd, K_SCALE, 0, hd->n * 16.0, k_scale, VEC_BLOCKS, VEC_THREADS, hd->b, b, hd->n,
+         1.0 / (hd->h * hd->h));
+  CKS(launch_ok());
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+mp_status mp_poisson_project(mp_handle hd, const double *p, double *ux, double *uy, double *uz) {
+  if (!hd || !p || !ux || !uy || !uz) return MP_ERR_INVALID_ARG;
+  Level &l0 = hd->L[0];
+  LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
+         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, hd->h);
+  CKS(launch_ok());
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+mp_status mp_poisson_get_fields(mp_handle hd, double *kappa, double *bx, double *by, double *bz,
+                                double *J) {
+  if (!hd) return MP_ERR_INVALID_ARG;
+  Level &l0 = hd->L[0];
+  size_t bytes = hd->n * sizeof(double);
+  if (kappa) CK(cudaMemcpyAsync(kappa, hd->kap, bytes, cudaMemcpyDeviceToDevice, hd->st));
+  if (bx) CK(cudaMemcpyAsync(bx, l0.bx, bytes, cudaMemcpyDeviceToDevice, hd->st));
+  if (by) CK(cudaMemcpyAsync(by, l0.by, bytes, cudaMemcpyDeviceToDevice, hd->st));
+  if (bz) CK(cudaMemcpyAsync(bz, l0.bz, bytes, cudaMemcpyDeviceToDevice, hd->st));
+  if (J) {
+    LAUNCH(hd, K_SCALE, 0, hd->n * 16.0, k_scale, VEC_BLOCKS, VEC_THREADS, hd->Jt, J, hd->n,
+           1.0 / (hd->h * hd->h));
+    CKS(launch_ok());
+  }
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+mp_status mp_poisson_set_profiling(mp_handle hd, int enable) {
+  if (!hd) return MP_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  if (enable && hd->events.empty()) {
+    hd->events.resize(EVENT_POOL);
+    for (auto &e : hd->events) CK(cudaEventCreate(&e));
+  }
+  hd->prof_on = enable ? 1 : 0;
+  for (auto &row : hd->prof)
+    for (auto &e : row) e = ProfEntry{};
+  return MP_OK;
+}
+
+mp_status mp_poisson_get_profile(mp_handle hd, mp_kernel_prof *out, int cap, int *count) {
+  if (!hd || cap < 0 || (cap > 0 && !out)) return MP_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  int m = 0;
+  for (int k = 0; k < K_COUNT; ++k)
+    for (int l = 0; l < MAX_LEVELS; ++l) {
+      const ProfEntry &e = hd->prof[k][l];
+      if (e.launches == 0) continue;
+      if (m < cap) {
+        mp_kernel_prof &o = out[m];
+        std::snprintf(o.name, sizeof(o.name), "%s", kKernelNames[k]);
+        o.level = l;
+        o.cells = l < (int)hd->L.size() ? (long long)hd->L[l].n : 0;
+        o.launches = e.launches;
+        o.total_ms = e.ms;
+        o.alg_bytes = e.bytes;
+      }
+      ++m;
+    }
+  if (count) *count = m;
+  return MP_OK;
+}
+
+mp_status mp_poisson_get_stats(mp_handle hd, mp_stats *st) {
+  if (!hd || !st) return MP_ERR_INVALID_ARG;
+  *st = hd->stats;
+  return MP_OK;
+}
+
+void mp_poisson_destroy(mp_handle hd) {
+  if (!hd) return;
+  cudaStreamSynchronize(hd->st);
+  for (void *p : hd->allocs) cudaFree(p);
+  for (cudaEvent_t e : hd->events) cudaEventDestroy(e);
+  if (hd->scal_h) cudaFreeHost(hd->scal_h);
+  delete hd;
+}
+
+}  // extern "C"

@@ -104,44 +104,75 @@ def random_bubbles(seed, count, rmin, rmax, n, h=None, pool_z0=None, max_tries=2
     return out
 
 
-def _fourier_component(rng, shape, h, origin, modes, kmax):
-    """sum_m a_m cos(2 pi k_m . x + psi_m) sampled at points origin + h*index.
-
-    k_m integer in [-kmax, kmax]^3 minus 0, psi ~ U[0, 2pi), a ~ N(0, 1).
-    Evaluated separably via complex exponentials along each axis.
-    """
-    nz, ny, nx = shape
-    xs = origin[0] + h * np.arange(nx)
-    ys = origin[1] + h * np.arange(ny)
-    zs = origin[2] + h * np.arange(nz)
-    acc = np.zeros(shape, dtype=np.complex128)
-    m = 0
-    while m < modes:
+def _draw_modes(rng, modes, kmax):
+    """Mode list [(k (3 ints), psi, a)]: k in [-kmax, kmax]^3 minus 0,
+    psi ~ U[0, 2pi), a ~ N(0, 1), drawn in that order per mode."""
+    out = []
+    while len(out) < modes:
         k = rng.integers(-kmax, kmax + 1, size=3)
         if not k.any():
             continue
         psi = rng.uniform(0.0, 2.0 * np.pi)
         a = rng.standard_normal()
+        out.append((k, psi, a))
+    return out
+
+
+def _eval_modes_numpy(mode_list, shape, h, origin):
+    """sum_m a_m cos(2 pi k_m . x + psi_m) at points origin + h*index,
+    evaluated separably through complex exponentials along each axis."""
+    nz, ny, nx = shape
+    xs = origin[0] + h * np.arange(nx)
+    ys = origin[1] + h * np.arange(ny)
+    zs = origin[2] + h * np.arange(nz)
+    acc = np.zeros(shape, dtype=np.complex128)
+    for k, psi, a in mode_list:
         ex = np.exp(2j * np.pi * k[0] * xs)[None, None, :]
         ey = np.exp(2j * np.pi * k[1] * ys)[None, :, None]
         ez = np.exp(2j * np.pi * k[2] * zs)[:, None, None]
         acc += (a * np.exp(1j * psi)) * (ez * ey) * ex
-        m += 1
     return acc.real
 
 
-def velocity(seed, shape, h, modes=16, kmax=4, bc=(PERIODIC, PERIODIC, NEUMANN)):
+def _eval_modes_torch(mode_list, shape, h, origin, device):
+    import torch
+    nz, ny, nx = shape
+    f64 = torch.float64
+    xs = origin[0] + h * torch.arange(nx, dtype=f64, device=device)
+    ys = origin[1] + h * torch.arange(ny, dtype=f64, device=device)
+    zs = origin[2] + h * torch.arange(nz, dtype=f64, device=device)
+    acc = torch.zeros(shape, dtype=f64, device=device)
+    tp = 2.0 * np.pi
+    for k, psi, a in mode_list:
+        # cos(A + B + C + psi) with A, B, C the per-axis phases, expanded separably
+        ph_x = tp * float(k[0]) * xs
+        ph_y = tp * float(k[1]) * ys
+        ph_z = tp * float(k[2]) * zs + psi
+        cz, sz = torch.cos(ph_z)[:, None], torch.sin(ph_z)[:, None]
+        cy, sy = torch.cos(ph_y)[None, :], torch.sin(ph_y)[None, :]
+        czy = (cz * cy - sz * sy)[:, :, None]
+        szy = (sz * cy + cz * sy)[:, :, None]
+        acc += a * (czy * torch.cos(ph_x)[None, None, :] - szy * torch.sin(ph_x)[None, None, :])
+    return acc
+
+
+def velocity(seed, shape, h, modes=16, kmax=4, bc=(PERIODIC, PERIODIC, NEUMANN), device=None):
     """Seeded smooth face velocity u* = (ux, uy, uz), each max-normalised to 1.
 
     Each component is a 16-mode random Fourier series evaluated on its own
     faces (low-face ownership, see module doc); the normal component vanishes
-    on wall faces.  Returns three (nz, ny, nx) float64 arrays.
+    on wall faces.  Returns three (nz, ny, nx) float64 numpy arrays, or torch
+    tensors on `device` when given (same modes; values agree to rounding).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     comps = []
     origins = [(0.0, 0.5 * h, 0.5 * h), (0.5 * h, 0.0, 0.5 * h), (0.5 * h, 0.5 * h, 0.0)]
     for axis in range(3):
-        u = _fourier_component(rng, shape, h, origins[axis], modes, kmax)
+        ml = _draw_modes(rng, modes, kmax)
+        if device is None:
+            u = _eval_modes_numpy(ml, shape, h, origins[axis])
+        else:
+            u = _eval_modes_torch(ml, shape, h, origins[axis], device)
         if bc[axis] == NEUMANN:
             if axis == 0:
                 u[:, :, 0] = 0.0
@@ -149,8 +180,8 @@ def velocity(seed, shape, h, modes=16, kmax=4, bc=(PERIODIC, PERIODIC, NEUMANN))
                 u[:, 0, :] = 0.0
             else:
                 u[0, :, :] = 0.0
-        u /= np.abs(u).max()
-        comps.append(np.ascontiguousarray(u))
+        u /= abs(u).max()
+        comps.append(u if device is not None else np.ascontiguousarray(u))
     return tuple(comps)
 
 
