@@ -192,6 +192,34 @@ mp_status mp_poisson_set_profiling(mp_handle hd, int enable);
  * the number of records available. */
 mp_status mp_poisson_get_profile(mp_handle hd, mp_kernel_prof *out, int cap, int *count);
 
+/*
+ * Right-hand side without allocating: b = rhs + J - mean(rhs + J), the same
+ * result as mp_poisson_rhs (to rounding), for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this exists for library
+ * users whose host application owns every device allocation (a memory pool
+ * or budget they may not bypass), or whose code path must not call
+ * cudaMalloc because it can block on or synchronise the device.  It needs
+ * no handle: the caller passes ncells (number of cells), rhs_dev and J_dev
+ * (device, ncells f64 each; J as returned by mp_poisson_get_fields) and
+ * b_dev (device, ncells f64, output).
+ *
+ * Scratch: a fixed array of about 512 KB in device memory that every GPU
+ * loading this library holds until the process exits; it bounds ncells to
+ * MP_NOALLOC_MAX_CELLS (larger sizes return MP_ERR_INVALID_ARG before any
+ * device work).  Every call on a device shares that one array and it keeps
+ * the last call's contents (each call writes every slot it later reads, so
+ * nothing needs clearing): calls that overlap on the GPU (different
+ * streams, or host threads) race and give wrong results.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream
+ * capture.  The work is enqueued on `stream` (cudaStream_t, NULL = legacy
+ * default stream) and the call returns without waiting for it.  Calls no
+ * allocating routine.
+ */
+#define MP_NOALLOC_MAX_CELLS 134217728LL /* 512^3 */
+mp_status mp_poisson_rhs_noalloc(long long ncells, const double *rhs_dev, const double *J_dev,
+                                 double *b_dev, void *stream);
+
 /* Free everything the handle owns.  NULL is ignored. */
 void mp_poisson_destroy(mp_handle hd);
 

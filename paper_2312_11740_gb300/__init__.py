@@ -19,6 +19,7 @@ from .poisson import (  # noqa: F401
     mp_poisson_project_step,
     mp_poisson_project_step_host,
     mp_poisson_rhs,
+    mp_poisson_rhs_noalloc,
     mp_poisson_set_geometry,
     mp_poisson_set_opts,
     mp_poisson_set_profiling,

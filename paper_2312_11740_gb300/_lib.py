@@ -19,6 +19,8 @@ MP_ERR_OOM = 5
 MP_ERR_TIMEOUT = 6
 MP_ERR_NO_NET = 7
 
+MP_NOALLOC_MAX_CELLS = 134217728
+
 MP_BC_PERIODIC = 0
 MP_BC_NEUMANN = 1
 
@@ -91,6 +93,7 @@ SIGNATURES = {
     "mp_poisson_get_stats": (_I, [_P, ctypes.POINTER(mp_stats)]),
     "mp_poisson_set_profiling": (_I, [_P, _I]),
     "mp_poisson_get_profile": (_I, [_P, ctypes.POINTER(mp_kernel_prof), _I, _IP]),
+    "mp_poisson_rhs_noalloc": (_I, [ctypes.c_longlong, _P, _P, _P, _P]),
     "mp_poisson_destroy": (None, [_P]),
 }
 

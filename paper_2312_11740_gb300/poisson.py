@@ -124,6 +124,15 @@ def mp_poisson_rhs(handle, rhs, b):
     return _check(_lib_().mp_poisson_rhs(handle, _ptr(rhs), _ptr(b)), "mp_poisson_rhs")
 
 
+def mp_poisson_rhs_noalloc(rhs, J, b, stream=None):
+    """b = rhs + J - mean(rhs + J) without any device allocation (enqueued on
+    `stream`; the call does not wait for the work)."""
+    n = rhs.numel()
+    return _check(_lib_().mp_poisson_rhs_noalloc(n, _ptr(rhs, numel=n), _ptr(J, numel=n),
+                                                 _ptr(b, numel=n), _stream_ptr(stream)),
+                  "mp_poisson_rhs_noalloc")
+
+
 def mp_poisson_project(handle, p, ux, uy, uz):
     return _check(_lib_().mp_poisson_project(handle, _ptr(p), _ptr(ux), _ptr(uy), _ptr(uz)),
                   "mp_poisson_project")
