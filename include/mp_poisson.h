@@ -163,8 +163,10 @@ mp_status mp_poisson_project(mp_handle hd, const double *p_dev, double *ux_dev, 
                              double *uz_dev);
 
 /* Copy setup fields out (device pointers, each N f64; any may be NULL):
- * curvature kappa, face coefficients beta_x/y/z (low-face ownership, wall
- * faces 0), jump source J (unscaled, sums to zero). */
+ * curvature kappa (evaluated in the interface band -- cells with a face
+ * neighbour of the other fluid -- and 0 elsewhere), face coefficients
+ * beta_x/y/z (low-face ownership, wall faces 0), jump source J (unscaled,
+ * sums to zero). */
 mp_status mp_poisson_get_fields(mp_handle hd, double *kappa_dev, double *bx_dev, double *by_dev,
                                 double *bz_dev, double *J_dev);
 

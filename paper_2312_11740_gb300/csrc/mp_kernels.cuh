@@ -65,7 +65,10 @@ __device__ __forceinline__ bool thread0() {
 // ------------------------------------------------------------ A1: curvature
 // kappa = -div(grad phi/|grad phi|) by central differences at cell centres,
 // |grad phi| floored at 1e-12, |kappa| clamped to 1/h.  Gas-positive phi
-// gives kappa = +2/R for a spherical bubble.
+// gives kappa = +2/R for a spherical bubble.  Only the jump across interface
+// faces uses kappa, so it is evaluated in the interface band (cells with a
+// face neighbour of the other fluid) and set to 0 elsewhere: FP64 division
+// and square root are costly on this part, and the band is a thin shell.
 __global__ void k_curvature(const double *__restrict__ phi, double *__restrict__ kap, Dims d,
                             double h, int per) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
@@ -78,6 +81,13 @@ __global__ void k_curvature(const double *__restrict__ phi, double *__restrict__
   double xm = phi[at(d, im, j, k)], xp = phi[at(d, ip, j, k)];
   double ym = phi[at(d, i, jm, k)], yp = phi[at(d, i, jp, k)];
   double zm = phi[at(d, i, j, km)], zp = phi[at(d, i, j, kp)];
+  bool gc = c > 0.0;
+  bool band = ((xm > 0.0) != gc) || ((xp > 0.0) != gc) || ((ym > 0.0) != gc) ||
+              ((yp > 0.0) != gc) || ((zm > 0.0) != gc) || ((zp > 0.0) != gc);
+  if (!band) {
+    kap[at(d, i, j, k)] = 0.0;
+    return;
+  }
   double i2h = 0.5 / h, ih2 = 1.0 / (h * h), i4h2 = 0.25 / (h * h);
   double gx = (xp - xm) * i2h, gy = (yp - ym) * i2h, gz = (zp - zm) * i2h;
   double gxx = (xp - 2.0 * c + xm) * ih2, gyy = (yp - 2.0 * c + ym) * ih2,
@@ -102,10 +112,13 @@ __global__ void k_curvature(const double *__restrict__ phi, double *__restrict__
 // Two cells on one side: 1/rho of that fluid.  Across the interface the
 // fluids act in series over the fractions theta, 1-theta of the spacing:
 // beta = 1/(theta rho_a + (1-theta) rho_b), theta = |phi_a|/(|phi_a|+|phi_b|).
-__device__ __forceinline__ double gfm_beta(double pa, double pb, double rl, double rg) {
+// irl = 1/rho_l and irg = 1/rho_g come from the host (the same IEEE quotient
+// as computing 1/rho here), so single-fluid faces cost no division.
+__device__ __forceinline__ double gfm_beta(double pa, double pb, double rl, double rg, double irl,
+                                           double irg) {
   bool ga = pa > 0.0, gb = pb > 0.0;
+  if (ga == gb) return ga ? irg : irl;
   double ra = ga ? rg : rl, rb = gb ? rg : rl;
-  if (ga == gb) return 1.0 / ra;
   double th = fabs(pa) / (fabs(pa) + fabs(pb));
   return 1.0 / (th * ra + (1.0 - th) * rb);
 }
@@ -122,14 +135,17 @@ __device__ __forceinline__ double gfm_jump(double pa, double pb, double ka, doub
 
 __global__ void k_faces(const double *__restrict__ phi, double *__restrict__ bx,
                         double *__restrict__ by, double *__restrict__ bz, Dims d, double rl,
-                        double rg, int per) {
+                        double rg, double irl, double irg, int per) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
   double pc = phi[c];
-  bx[c] = (i == 0 && !(per & 1)) ? 0.0 : gfm_beta(phi[at(d, wlo(i, d.nx), j, k)], pc, rl, rg);
-  by[c] = (j == 0 && !(per & 2)) ? 0.0 : gfm_beta(phi[at(d, i, wlo(j, d.ny), k)], pc, rl, rg);
-  bz[c] = (k == 0 && !(per & 4)) ? 0.0 : gfm_beta(phi[at(d, i, j, wlo(k, d.nz))], pc, rl, rg);
+  bx[c] = (i == 0 && !(per & 1)) ? 0.0
+                                 : gfm_beta(phi[at(d, wlo(i, d.nx), j, k)], pc, rl, rg, irl, irg);
+  by[c] = (j == 0 && !(per & 2)) ? 0.0
+                                 : gfm_beta(phi[at(d, i, wlo(j, d.ny), k)], pc, rl, rg, irl, irg);
+  bz[c] = (k == 0 && !(per & 4)) ? 0.0
+                                 : gfm_beta(phi[at(d, i, j, wlo(k, d.nz))], pc, rl, rg, irl, irg);
 }
 
 // -------------------------------------------------------- A3: jump source
@@ -285,24 +301,283 @@ __global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__re
   x[c] = s * idiag[c];
 }
 
-// scaled residual at one cell: rt = bt - sum_f beta_f x_nb + diag x_c
+// ------------------------------------ A6: fused red-black sweep (FP32)
+// One full sweep per launch (colour c1 first, then the other; red = even
+// i+j+k), out of place (xin -> xout) so that no CTA reads a value another CTA
+// has already updated.  A CTA owns an FX x FY x FZ tile: it first computes
+// the new first-colour values on the tile plus a one-cell ring (wrapped)
+// into shared memory, then the second colour of the tile from them, and
+// writes both colours.  1/diag is formed from the six
+// face coefficients on the fly.  DRAM traffic per sweep is one read of x, b
+// and the three face arrays and one write of x (24 B/cell); the ring reads
+// come from L2.  zero != 0: xin is taken as 0 (first sweep of a cycle).
+constexpr int FUSED_THREADS = 256;
+
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <int FX, int FY, int FZ>
+__global__ void __launch_bounds__(FUSED_THREADS)
+k_rbgs_fused(const float *__restrict__ xin, float *__restrict__ xout, const float *__restrict__ b,
+             const float *__restrict__ bx, const float *__restrict__ by,
+             const float *__restrict__ bz, Dims d, int zero, int c1) {
+  constexpr int EX = FX + 2, EY = FY + 2, EZ = FZ + 2, HALF = EX / 2;
+  static_assert(FX % 2 == 0, "first-colour cells alternate along x");
+  __shared__ float sred[EZ][EY][EX];
+  const int nx = d.nx, ny = d.ny, nz = d.nz, sy = nx, sz = nx * ny;
+  const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY, k0 = blockIdx.z * FZ;
+  // phase 1: first-colour cells of the tile and its one-cell ring (wrapped).
+  // Ring cells past the last valid cell of a ragged tile are skipped.
+  for (int e = threadIdx.x; e < EY * EZ * HALF; e += FUSED_THREADS) {
+    const int row = e / HALF, t = e - row * HALF;
+    const int ey = row % EY, ez = row / EY;
+    int j = j0 + ey - 1, k = k0 + ez - 1;
+    if (j > ny || k > nz) continue;
+    j += j < 0 ? ny : 0;
+    j -= j >= ny ? ny : 0;
+    k += k < 0 ? nz : 0;
+    k -= k >= nz ? nz : 0;
+    // parity of unwrapped and wrapped indices agree: smoothed axes are even
+    const int ex = 2 * t + ((i0 - 1 + j + k + c1) & 1);
+    int i = i0 - 1 + ex;
+    if (i > nx) continue;
+    i += i < 0 ? nx : 0;
+    i -= i >= nx ? nx : 0;
+    const int c = i + j * sy + k * sz;
+    const int xp = i == nx - 1 ? c - (nx - 1) : c + 1;
+    const int yp = j == ny - 1 ? c - (ny - 1) * sy : c + sy;
+    const int zp = k == nz - 1 ? c - (nz - 1) * sz : c + sz;
+    const float wxl = bx[c], wxh = bx[xp], wyl = by[c], wyh = by[yp], wzl = bz[c], wzh = bz[zp];
+    const float den = ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh);
+    float num = -b[c];
+    if (!zero) {
+      const int xm = i == 0 ? c + (nx - 1) : c - 1;
+      const int ym = j == 0 ? c + (ny - 1) * sy : c - sy;
+      const int zm = k == 0 ? c + (nz - 1) * sz : c - sz;
+      num = fmaf(wxl, xin[xm], num);
+      num = fmaf(wxh, xin[xp], num);
+      num = fmaf(wyl, xin[ym], num);
+      num = fmaf(wyh, xin[yp], num);
+      num = fmaf(wzl, xin[zm], num);
+      num = fmaf(wzh, xin[zp], num);
+    }
+    sred[ez][ey][ex] = __fdividef(num, den);
+  }
+  __syncthreads();
+  // phase 2: the tile; first colour copies out, second colour is updated
+  for (int e = threadIdx.x; e < FX * FY * FZ; e += FUSED_THREADS) {
+    const int tx = e % FX, ty = (e / FX) % FY, tz = e / (FX * FY);
+    const int i = i0 + tx, j = j0 + ty, k = k0 + tz;
+    if (i >= nx || j >= ny || k >= nz) continue;
+    const int c = i + j * sy + k * sz;
+    const int ex = tx + 1, ey = ty + 1, ez = tz + 1;
+    float v;
+    if (((i + j + k) & 1) == c1) {
+      v = sred[ez][ey][ex];
+    } else {
+      const int xp = i == nx - 1 ? c - (nx - 1) : c + 1;
+      const int yp = j == ny - 1 ? c - (ny - 1) * sy : c + sy;
+      const int zp = k == nz - 1 ? c - (nz - 1) * sz : c + sz;
+      const float wxl = bx[c], wxh = bx[xp], wyl = by[c], wyh = by[yp], wzl = bz[c], wzh = bz[zp];
+      const float den = ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh);
+      float num = -b[c];
+      num = fmaf(wxl, sred[ez][ey][ex - 1], num);
+      num = fmaf(wxh, sred[ez][ey][ex + 1], num);
+      num = fmaf(wyl, sred[ez][ey - 1][ex], num);
+      num = fmaf(wyh, sred[ez][ey + 1][ex], num);
+      num = fmaf(wzl, sred[ez - 1][ey][ex], num);
+      num = fmaf(wzh, sred[ez + 1][ey][ex], num);
+      v = __fdividef(num, den);
+    }
+    xout[c] = v;
+  }
+}
+
+// (At x)_c at one cell.  FP64: sum_f beta_f x_nb - diag_c x_c (fewest FP64
+// operations; FP64 keeps ~13 digits after the cancellation at density
+// ratio 1e3).  FP32: sum_f beta_f (x_nb - x_c): differences first, so the
+// cancellation between the beta ~ 1e3 terms of a gas cell does not eat the
+// 7-digit FP32 mantissa.
+template <typename T>
+__device__ __forceinline__ T op_at(const T *__restrict__ x, const T *__restrict__ bx,
+                                   const T *__restrict__ by, const T *__restrict__ bz,
+                                   const T *__restrict__ diag, const Dims &d, int i, int j, int k) {
+  size_t c = at(d, i, j, k);
+  size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
+  size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
+  size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+  T xc = x[c];
+  if (sizeof(T) == 8 && diag != nullptr) {
+    T s = -diag[c] * xc;
+    s = fma(bx[c], x[xl], s);
+    s = fma(bx[xh], x[xh], s);
+    s = fma(by[c], x[yl], s);
+    s = fma(by[yh], x[yh], s);
+    s = fma(bz[c], x[zl], s);
+    s = fma(bz[zh], x[zh], s);
+    return s;
+  } else {
+    T s = bx[c] * (x[xl] - xc);
+    s = fma(bx[xh], x[xh] - xc, s);
+    s = fma(by[c], x[yl] - xc, s);
+    s = fma(by[yh], x[yh] - xc, s);
+    s = fma(bz[c], x[zl] - xc, s);
+    s = fma(bz[zh], x[zh] - xc, s);
+    return s;
+  }
+}
+
+// scaled residual at one cell: rt = bt - (At x)_c
 template <typename T>
 __device__ __forceinline__ T resid_at(const T *__restrict__ x, const T *__restrict__ b,
                                       const T *__restrict__ bx, const T *__restrict__ by,
                                       const T *__restrict__ bz, const T *__restrict__ diag,
                                       const Dims &d, int i, int j, int k) {
-  size_t c = at(d, i, j, k);
-  size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
-  size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
-  size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
-  T s = -b[c];
-  s = fma(bx[c], x[xl], s);
-  s = fma(bx[xh], x[xh], s);
-  s = fma(by[c], x[yl], s);
-  s = fma(by[yh], x[yh], s);
-  s = fma(bz[c], x[zl], s);
-  s = fma(bz[zh], x[zh], s);
-  return fma(diag[c], x[c], -s);
+  return b[at(d, i, j, k)] - op_at(x, bx, by, bz, diag, d, i, j, k);
+}
+
+
+// ------------------------------------------ A6-A9: coarse tail in one CTA
+// The bottom of the V-cycle (levels of at most a few thousand cells) in a
+// single launch: every level's iterate, right-hand side and face
+// coefficients live in shared memory, and one 1024-thread block runs all
+// sweeps, restrictions, prolongations and the FP64 coarsest solve with
+// __syncthreads between steps.  Replaces ~100 latency-bound launches per
+// cycle.  Same arithmetic as the per-level kernels (colour order, difference
+// form for FP32 residuals, diag formed from the faces).
+constexpr int TAIL_MAX_LEVELS = 8;
+constexpr int TAIL_THREADS = 1024;
+struct TailLevel {
+  Dims d;
+  int n, nu1, nu2;
+  int off;  // element offset of the level's six arrays in shared memory
+  const void *bx, *by, *bz, *idiag;
+};
+struct TailArgs {
+  int nlev;  // levels in the tail (the last one is the coarsest)
+  TailLevel lv[TAIL_MAX_LEVELS];
+  const double *Minv;
+};
+
+// shared-memory arrays of one tail level: x, b, bx, by, bz, 1/diag
+template <typename T>
+struct TailView {
+  T *x, *b, *wx, *wy, *wz, *id;
+  __device__ TailView(T *base, const TailLevel &l) {
+    x = base + l.off;
+    b = x + l.n;
+    wx = b + l.n;
+    wy = wx + l.n;
+    wz = wy + l.n;
+    id = wz + l.n;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void tail_halfsweep(const TailView<T> &v, const Dims &d, int colour,
+                                               int zero) {
+  const int nx = d.nx, ny = d.ny, nz = d.nz, sy = nx, sz = nx * ny;
+  const int hx = nx >> 1, half = (nx * ny * nz) >> 1;
+  for (int t = threadIdx.x; t < half; t += TAIL_THREADS) {
+    const int row = t / hx;
+    const int j = row % ny, k = row / ny;
+    const int i = 2 * (t - row * hx) + ((j + k + colour) & 1);
+    const int c = i + j * sy + k * sz;
+    const int xp = i == nx - 1 ? c - (nx - 1) : c + 1;
+    const int yp = j == ny - 1 ? c - (ny - 1) * sy : c + sy;
+    const int zp = k == nz - 1 ? c - (nz - 1) * sz : c + sz;
+    T num = -v.b[c];
+    if (!zero) {
+      const int xm = i == 0 ? c + (nx - 1) : c - 1;
+      const int ym = j == 0 ? c + (ny - 1) * sy : c - sy;
+      const int zm = k == 0 ? c + (nz - 1) * sz : c - sz;
+      num = fma(v.wx[c], v.x[xm], num);
+      num = fma(v.wx[xp], v.x[xp], num);
+      num = fma(v.wy[c], v.x[ym], num);
+      num = fma(v.wy[yp], v.x[yp], num);
+      num = fma(v.wz[c], v.x[zm], num);
+      num = fma(v.wz[zp], v.x[zp], num);
+    }
+    v.x[c] = num * v.id[c];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS)
+k_tail(TailArgs a, const T *__restrict__ rhs, T *__restrict__ xout) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  T *base = reinterpret_cast<T *>(tail_smem);
+  for (int l = 0; l < a.nlev; ++l) {
+    TailView<T> v(base, a.lv[l]);
+    const T *gx = (const T *)a.lv[l].bx, *gy = (const T *)a.lv[l].by, *gz = (const T *)a.lv[l].bz,
+            *gi = (const T *)a.lv[l].idiag;
+    for (int e = threadIdx.x; e < a.lv[l].n; e += TAIL_THREADS) {
+      v.wx[e] = gx[e];
+      v.wy[e] = gy[e];
+      v.wz[e] = gz[e];
+      v.id[e] = gi[e];
+    }
+  }
+  {
+    TailView<T> v0(base, a.lv[0]);
+    for (int e = threadIdx.x; e < a.lv[0].n; e += TAIL_THREADS) v0.b[e] = rhs[e];
+  }
+  __syncthreads();
+  const int last = a.nlev - 1;
+  for (int l = 0; l < last; ++l) {  // down
+    const TailView<T> v(base, a.lv[l]);
+    const TailView<T> vc(base, a.lv[l + 1]);
+    const Dims d = a.lv[l].d, dc = a.lv[l + 1].d;
+    for (int s = 0; s < a.lv[l].nu1; ++s) {
+      tail_halfsweep(v, d, 0, s == 0);
+      __syncthreads();
+      tail_halfsweep(v, d, 1, 0);
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < a.lv[l + 1].n; e += TAIL_THREADS) {
+      const int I = e % dc.nx, J = (e / dc.nx) % dc.ny, K = e / (dc.nx * dc.ny);
+      T sum = 0;
+      for (int q = 0; q < 8; ++q)
+        sum += resid_at(v.x, v.b, v.wx, v.wy, v.wz, (const T *)nullptr, d, 2 * I + (q & 1),
+                        2 * J + ((q >> 1) & 1), 2 * K + (q >> 2));
+      vc.b[e] = (T)0.5 * sum;
+    }
+    __syncthreads();
+  }
+  {  // coarsest: e = Minv (-(b - mean b)) in FP64
+    __shared__ double mean_s;
+    const TailView<T> v(base, a.lv[last]);
+    const int n = a.lv[last].n;
+    double acc0 = 0.0;
+    for (int e = threadIdx.x; e < n; e += TAIL_THREADS) acc0 += (double)v.b[e];
+    double sum = block_sum(acc0);
+    if (threadIdx.x == 0) mean_s = sum / n;
+    __syncthreads();
+    const double m = mean_s;
+    for (int r = threadIdx.x; r < n; r += TAIL_THREADS) {
+      double acc = 0.0;
+      for (int c = 0; c < n; ++c) acc = fma(a.Minv[(size_t)c * n + r], (double)v.b[c] - m, acc);
+      v.x[r] = (T)(-acc);
+    }
+    __syncthreads();
+  }
+  for (int l = last - 1; l >= 0; --l) {  // up
+    const TailView<T> v(base, a.lv[l]);
+    const TailView<T> vc(base, a.lv[l + 1]);
+    const Dims d = a.lv[l].d, dc = a.lv[l + 1].d;
+    for (int e = threadIdx.x; e < a.lv[l].n; e += TAIL_THREADS) {
+      const int i = e % d.nx, j = (e / d.nx) % d.ny, k = e / (d.nx * d.ny);
+      v.x[e] += vc.x[(i >> 1) + dc.nx * ((j >> 1) + dc.ny * (k >> 1))];
+    }
+    __syncthreads();
+    for (int s = 0; s < a.lv[l].nu2; ++s) {
+      tail_halfsweep(v, d, 1, 0);
+      __syncthreads();
+      tail_halfsweep(v, d, 0, 0);
+      __syncthreads();
+    }
+  }
+  const TailView<T> v0(base, a.lv[0]);
+  for (int e = threadIdx.x; e < a.lv[0].n; e += TAIL_THREADS) xout[e] = v0.x[e];
 }
 
 // ------------------------------------- A7: residual + restriction (fused)
@@ -337,30 +612,25 @@ __global__ void k_prolong(T *__restrict__ x, const T *__restrict__ ec, Dims df, 
 enum { S_RZ = 0, S_RZOLD, S_DQ, S_ALPHA, S_BETA, S_RR, S_BB, S_MEAN, S_TMP, S_COUNT };
 enum { OP_STORE = 0, OP_ALPHA, OP_BETA, OP_MEAN };
 
+// Stencil kernels with a reduction walk a column of `zper` planes per
+// thread (grid z = ceil(nz / zper)), so the partial-sum count stays ~2k.
 // q = At d; per-block partial of d.q
 template <typename T>
 __global__ void k_apply_dot(const T *__restrict__ dv, T *__restrict__ q, const T *__restrict__ bx,
                             const T *__restrict__ by, const T *__restrict__ bz,
-                            const T *__restrict__ diag, Dims d, double *__restrict__ partial) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-  double acc = 0.0;
-  if (i < d.nx && j < d.ny) {
-    size_t c = at(d, i, j, k);
-    size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
-    size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
-    size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
-    T dc = dv[c];
-    T s = -diag[c] * dc;
-    s = fma(bx[c], dv[xl], s);
-    s = fma(bx[xh], dv[xh], s);
-    s = fma(by[c], dv[yl], s);
-    s = fma(by[yh], dv[yh], s);
-    s = fma(bz[c], dv[zl], s);
-    s = fma(bz[zh], dv[zh], s);
-    q[c] = s;
-    acc = (double)(s * dc);
-  }
-  double t = block_sum(acc);
+                            const T *__restrict__ diag, Dims d, int zper,
+                            double *__restrict__ partial) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
+  T acc = 0;
+  if (i < d.nx && j < d.ny)
+    for (int k = k0; k < k1; ++k) {
+      size_t c = at(d, i, j, k);
+      T s = op_at(dv, bx, by, bz, diag, d, i, j, k);
+      q[c] = s;
+      acc = fma(s, dv[c], acc);
+    }
+  double t = block_sum((double)acc);
   if (thread0()) partial[block_linear_id()] = t;
 }
 
@@ -368,16 +638,18 @@ __global__ void k_apply_dot(const T *__restrict__ dv, T *__restrict__ q, const T
 template <typename T>
 __global__ void k_residual(const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r,
                            const T *__restrict__ bx, const T *__restrict__ by,
-                           const T *__restrict__ bz, const T *__restrict__ diag, Dims d,
+                           const T *__restrict__ bz, const T *__restrict__ diag, Dims d, int zper,
                            double *__restrict__ partial, int zero) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
   double acc = 0.0;
-  if (i < d.nx && j < d.ny) {
-    size_t c = at(d, i, j, k);
-    T v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, d, i, j, k);
-    r[c] = v;
-    acc = (double)v * (double)v;
-  }
+  if (i < d.nx && j < d.ny)
+    for (int k = k0; k < k1; ++k) {
+      size_t c = at(d, i, j, k);
+      T v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, d, i, j, k);
+      r[c] = v;
+      acc = fma((double)v, (double)v, acc);
+    }
   double t = block_sum(acc);
   if (thread0()) partial[block_linear_id()] = t;
 }
@@ -386,16 +658,18 @@ __global__ void k_residual(const T *__restrict__ x, const T *__restrict__ b, T *
 __global__ void k_residual_mixed(const double *__restrict__ x, const double *__restrict__ b,
                                  float *__restrict__ r32, const double *__restrict__ bx,
                                  const double *__restrict__ by, const double *__restrict__ bz,
-                                 const double *__restrict__ diag, Dims d,
+                                 const double *__restrict__ diag, Dims d, int zper,
                                  double *__restrict__ partial, int zero) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
   double acc = 0.0;
-  if (i < d.nx && j < d.ny) {
-    size_t c = at(d, i, j, k);
-    double v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, d, i, j, k);
-    r32[c] = (float)v;
-    acc = v * v;
-  }
+  if (i < d.nx && j < d.ny)
+    for (int k = k0; k < k1; ++k) {
+      size_t c = at(d, i, j, k);
+      double v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, d, i, j, k);
+      r32[c] = (float)v;
+      acc = fma(v, v, acc);
+    }
   double t = block_sum(acc);
   if (thread0()) partial[block_linear_id()] = t;
 }
@@ -522,18 +796,20 @@ __global__ void k_assemble(const double *__restrict__ rhs, const double *__restr
 // bt = h^2 div_h u* + Jt = h * sum(u_high - u_low) + Jt, fused divergence
 __global__ void k_assemble_u(const double *__restrict__ ux, const double *__restrict__ uy,
                              const double *__restrict__ uz, const double *__restrict__ Jt,
-                             double *__restrict__ b, Dims d, double h,
+                             double *__restrict__ b, Dims d, int zper, double h,
                              double *__restrict__ partial) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
   double acc = 0.0;
-  if (i < d.nx && j < d.ny) {
-    size_t c = at(d, i, j, k);
-    double s = ux[at(d, whi(i, d.nx), j, k)] - ux[c] + uy[at(d, i, whi(j, d.ny), k)] - uy[c] +
-               uz[at(d, i, j, whi(k, d.nz))] - uz[c];
-    double v = fma(h, s, Jt[c]);
-    b[c] = v;
-    acc = v;
-  }
+  if (i < d.nx && j < d.ny)
+    for (int k = k0; k < k1; ++k) {
+      size_t c = at(d, i, j, k);
+      double s = ux[at(d, whi(i, d.nx), j, k)] - ux[c] + uy[at(d, i, whi(j, d.ny), k)] - uy[c] +
+                 uz[at(d, i, j, whi(k, d.nz))] - uz[c];
+      double v = fma(h, s, Jt[c]);
+      b[c] = v;
+      acc += v;
+    }
   double t = block_sum(acc);
   if (thread0()) partial[block_linear_id()] = t;
 }
@@ -564,9 +840,10 @@ __global__ void k_project(const double *__restrict__ p, const double *__restrict
   double pc = p[c], fc = phi[c], kc = kap[c];
   size_t xl = at(d, wlo(i, d.nx), j, k), yl = at(d, i, wlo(j, d.ny), k),
          zl = at(d, i, j, wlo(k, d.nz));
-  ux[c] -= bx[c] * (pc - p[xl] - gfm_jump(phi[xl], fc, kap[xl], kc, sig)) / h;
-  uy[c] -= by[c] * (pc - p[yl] - gfm_jump(phi[yl], fc, kap[yl], kc, sig)) / h;
-  uz[c] -= bz[c] * (pc - p[zl] - gfm_jump(phi[zl], fc, kap[zl], kc, sig)) / h;
+  double ih = 1.0 / h;
+  ux[c] -= bx[c] * (pc - p[xl] - gfm_jump(phi[xl], fc, kap[xl], kc, sig)) * ih;
+  uy[c] -= by[c] * (pc - p[yl] - gfm_jump(phi[yl], fc, kap[yl], kc, sig)) * ih;
+  uz[c] -= bz[c] * (pc - p[zl] - gfm_jump(phi[zl], fc, kap[zl], kc, sig)) * ih;
 }
 
 // y = scale * v (used to unscale J and the operator for the test API)

@@ -34,18 +34,20 @@ struct Level {
   float *bx32 = nullptr, *by32 = nullptr, *bz32 = nullptr, *diag32 = nullptr, *idiag32 = nullptr;
   double *b = nullptr, *e = nullptr;   // coarse-level rhs / correction (levels >= 1)
   float *b32 = nullptr, *e32 = nullptr;
+  float *t32 = nullptr;                // FP32 ping-pong partner of the level's iterate
 };
 
 enum KernelId {
   K_CURV, K_FACES, K_JUMP, K_DIAG, K_COARSEN, K_DENSE, K_GJ,
-  K_RBGS64, K_RBGS32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
+  K_RBGS64, K_RBGS32, K_RBGSF32, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
   K_APPLY64, K_APPLY32, K_RESID64, K_RESID32, K_RESIDMIX, K_DOT64, K_DOT32, K_AXPY64, K_AXPY32,
   K_XPBY64, K_XPBY32, K_ADD64, K_ADD32, K_ADDF32, K_SUM, K_SUBMEAN, K_REDUCE, K_ASSEMBLE,
   K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_COUNT
 };
 const char *const kKernelNames[K_COUNT] = {
   "curvature", "gfm_faces", "jump", "diag", "coarsen_faces", "dense_build", "gauss_jordan",
-  "rbgs_f64", "rbgs_f32", "resid_restrict_f64", "resid_restrict_f32", "prolong_f64",
+  "rbgs_f64", "rbgs_f32", "rbgs_fused_f32", "coarse_tail_f64", "coarse_tail_f32",
+  "resid_restrict_f64", "resid_restrict_f32", "prolong_f64",
   "prolong_f32", "coarse_solve_f64", "coarse_solve_f32io", "apply_dot_f64", "apply_dot_f32",
   "residual_f64", "residual_f32", "residual_mixed", "dot_f64", "dot_f32", "axpy2_f64",
   "axpy2_f32", "xpby_f64", "xpby_f32", "add_f64", "add_f32", "add_f32_to_f64", "sum",
@@ -95,6 +97,20 @@ struct mp_poisson {
   std::vector<cudaEvent_t> events;
   size_t ev_next = 0;
   std::vector<Pending> pending;
+  // CUDA graphs of whole V-cycles, keyed by (type, rhs, x); launched on st
+  struct Graph {
+    int type;
+    const void *rhs, *x;
+    cudaGraphExec_t exec;
+    std::vector<int> ids, levels;  // kernels in the graph, for launch accounting
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap = nullptr;  // private stream used only for capture
+  // first level of the one-CTA coarse tail per precision, and its smem bytes
+  int tail64 = 0, tail32 = 0;
+  size_t tail64_bytes = 0, tail32_bytes = 0;
+  bool capturing = false;
+  std::vector<int> cap_ids, cap_levels;
 };
 
 namespace {
@@ -119,6 +135,33 @@ int cell_blocks(const Dims &d) {
   return (int)(g.x * g.y * g.z);
 }
 const dim3 kBlock(BX, BY, 1);
+
+// Stencil+reduction kernels: each thread walks zper planes; about 2k blocks.
+int zper_of(const Dims &d) {
+  long plane_blocks = (long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  long want = std::max<long>(1, 2048 / std::max<long>(1, plane_blocks));
+  long zb = std::min<long>(d.nz, want);
+  return (int)((d.nz + zb - 1) / zb);
+}
+dim3 zgrid(const Dims &d) {
+  int zp = zper_of(d);
+  return dim3((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + zp - 1) / zp);
+}
+int zblocks(const Dims &d) {
+  dim3 g = zgrid(d);
+  return (int)(g.x * g.y * g.z);
+}
+// fused-sweep tiles: large tiles (fewer ring cells) on large levels, small
+// tiles (enough CTAs) on mid-size levels
+constexpr int FBX = 32, FBY = 16, FBZ = 8, FSX = 16, FSY = 8, FSZ = 4;
+bool big_tile(const Dims &d) { return (size_t)d.nx * d.ny * d.nz >= ((size_t)1 << 20); }
+dim3 fused_grid(const Dims &d) {
+  if (big_tile(d)) return dim3((d.nx + FBX - 1) / FBX, (d.ny + FBY - 1) / FBY, (d.nz + FBZ - 1) / FBZ);
+  return dim3((d.nx + FSX - 1) / FSX, (d.ny + FSY - 1) / FSY, (d.nz + FSZ - 1) / FSZ);
+}
+// dynamic shared memory of the one-CTA coarse tail: FP32 levels up to ~16^3;
+// FP64 only the smallest levels (one SM's FP64 rate is the limit there)
+constexpr size_t TAIL_BUDGET32 = 200 * 1024, TAIL_BUDGET64 = 48 * 1024;
 
 template <typename T>
 mp_status dalloc(mp_poisson *hd, T **p, size_t count) {
@@ -148,6 +191,11 @@ void prof_resolve(mp_poisson *hd) {
 }
 
 void prof_begin(mp_poisson *hd, int id, int level) {
+  if (hd->capturing) {
+    hd->cap_ids.push_back(id);
+    hd->cap_levels.push_back(level);
+    return;
+  }
   hd->prof[id][level].launches++;
   if (!hd->prof_on) return;
   if (hd->ev_next + 2 > hd->events.size()) {
@@ -158,7 +206,7 @@ void prof_begin(mp_poisson *hd, int id, int level) {
 }
 
 void prof_end(mp_poisson *hd, int id, int level, double bytes) {
-  if (!hd->prof_on) return;
+  if (!hd->prof_on || hd->capturing) return;
   cudaEvent_t a = hd->events[hd->ev_next], b = hd->events[hd->ev_next + 1];
   cudaEventRecord(b, hd->st);
   hd->ev_next += 2;
@@ -173,6 +221,13 @@ void prof_end(mp_poisson *hd, int id, int level, double bytes) {
     prof_begin((hd), (id), (level));                              \
     kern<<<(grid), (block), 0, (hd)->st>>>(__VA_ARGS__);          \
     prof_end((hd), (id), (level), (double)(bytes));               \
+  } while (0)
+// the same with dynamic shared memory
+#define LAUNCH_SMEM(hd, id, level, bytes, kern, grid, block, smem, ...) \
+  do {                                                                  \
+    prof_begin((hd), (id), (level));                                    \
+    kern<<<(grid), (block), (smem), (hd)->st>>>(__VA_ARGS__);           \
+    prof_end((hd), (id), (level), (double)(bytes));                     \
   } while (0)
 
 template <typename T>
@@ -216,9 +271,33 @@ template <> struct LV<float> {
 };
 
 // One symmetric V-cycle with zero initial guess: x ~= At^-1 rhs on level l.
+// Pre-smoothing sweeps red then black, post-smoothing black then red (the
+// adjoint), so the cycle is a symmetric preconditioner.  FP32 levels use the
+// fused out-of-place sweep, alternating between x and the level's t32 so the
+// last sweep lands in x; FP64 levels use in-place per-colour sweeps (fewest
+// FP64 operations: FP64 is ALU-bound on this part).
 template <typename T>
 mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
   Level &lv = hd->L[l];
+  const int tail = sizeof(T) == 8 ? hd->tail64 : hd->tail32;
+  if (l == tail && l < (int)hd->L.size() - 1) {
+    TailArgs a{};
+    a.nlev = (int)hd->L.size() - l;
+    a.Minv = hd->Minv;
+    double bytes = 0.0;
+    int off = 0;
+    for (int q = 0; q < a.nlev; ++q) {
+      Level &t = hd->L[l + q];
+      a.lv[q] = TailLevel{t.d, (int)t.n, t.nu1, t.nu2, off, LV<T>::bx(t), LV<T>::by(t),
+                          LV<T>::bz(t), LV<T>::idiag(t)};
+      off += 6 * (int)t.n;
+      bytes += 4.0 * t.n * sizeof(T);
+    }
+    size_t smem = sizeof(T) == 8 ? hd->tail64_bytes : hd->tail32_bytes;
+    auto ktail = k_tail<T>;
+    LAUNCH_SMEM(hd, kid<T>(K_TAIL64, K_TAIL32), l, bytes, ktail, 1, TAIL_THREADS, smem, a, rhs, x);
+    return launch_ok();
+  }
   if (l == (int)hd->L.size() - 1) {
     LAUNCH(hd, kid<T>(K_COARSE64, K_COARSE32), l, lv.n * (lv.n * 8.0 + 2.0 * sizeof(T)),
            k_coarse_solve<T>, 1, 512, hd->Minv, rhs, x, (int)lv.n);
@@ -227,25 +306,116 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
   Level &lc = hd->L[l + 1];
   T *bx = LV<T>::bx(lv), *by = LV<T>::by(lv), *bz = LV<T>::bz(lv);
   T *diag = LV<T>::diag(lv), *idiag = LV<T>::idiag(lv);
-  dim3 hg = half_grid(lv.d);
-  const int krb = kid<T>(K_RBGS64, K_RBGS32);
   const double sz = sizeof(T), nl = (double)lv.n;
-  for (int s = 0; s < lv.nu1; ++s) {
-    LAUNCH(hd, krb, l, (s == 0 ? 4.5 : 5.0) * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz,
-           idiag, lv.d, 0, s == 0);
-    LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1, 0);
+  T *cur = x;
+  if constexpr (sizeof(T) == 4) {
+    const int S = lv.nu1 + lv.nu2;
+    float *A = (S & 1) ? x : lv.t32;
+    float *B = (A == x) ? lv.t32 : x;
+    const dim3 fg = fused_grid(lv.d);
+    cur = nullptr;
+    const bool big = big_tile(lv.d);
+    auto kbig = k_rbgs_fused<FBX, FBY, FBZ>;
+    auto ksmall = k_rbgs_fused<FSX, FSY, FSZ>;
+    for (int s = 0; s < lv.nu1; ++s) {
+      float *dst = (cur == A) ? B : A;
+      if (big)
+        LAUNCH(hd, K_RBGSF32, l, (s == 0 ? 20.0 : 24.0) * nl, kbig, fg,
+               FUSED_THREADS, s == 0 ? dst : cur, dst, rhs, bx, by, bz, lv.d, s == 0, 0);
+      else
+        LAUNCH(hd, K_RBGSF32, l, (s == 0 ? 20.0 : 24.0) * nl, ksmall, fg,
+               FUSED_THREADS, s == 0 ? dst : cur, dst, rhs, bx, by, bz, lv.d, s == 0, 0);
+      cur = dst;
+    }
+    LAUNCH(hd, K_RESTR32, l, 6.125 * nl * sz, k_resid_restrict<float>, cell_grid(lc.d), kBlock,
+           cur, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
+    CKS(launch_ok());
+    CKS(vcycle<T>(hd, l + 1, LV<T>::b(lc), LV<T>::e(lc)));
+    LAUNCH(hd, K_PROL32, l, 2.125 * nl * sz, k_prolong<float>, cell_grid(lv.d), kBlock, cur,
+           LV<T>::e(lc), lv.d, lc.d);
+    for (int s = 0; s < lv.nu2; ++s) {
+      float *dst = (cur == A) ? B : A;
+      if (big)
+        LAUNCH(hd, K_RBGSF32, l, 24.0 * nl, kbig, fg, FUSED_THREADS, cur,
+               dst, rhs, bx, by, bz, lv.d, 0, 1);
+      else
+        LAUNCH(hd, K_RBGSF32, l, 24.0 * nl, ksmall, fg, FUSED_THREADS, cur,
+               dst, rhs, bx, by, bz, lv.d, 0, 1);
+      cur = dst;
+    }
+    (void)idiag;
+  } else {
+    dim3 hg = half_grid(lv.d);
+    const int krb = K_RBGS64;
+    for (int s = 0; s < lv.nu1; ++s) {
+      LAUNCH(hd, krb, l, (s == 0 ? 4.5 : 5.0) * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by,
+             bz, idiag, lv.d, 0, s == 0);
+      LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1,
+             0);
+    }
+    LAUNCH(hd, K_RESTR64, l, 6.125 * nl * sz, k_resid_restrict<T>, cell_grid(lc.d), kBlock, x,
+           rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
+    CKS(launch_ok());
+    CKS(vcycle<T>(hd, l + 1, LV<T>::b(lc), LV<T>::e(lc)));
+    LAUNCH(hd, K_PROL64, l, 2.125 * nl * sz, k_prolong<T>, cell_grid(lv.d), kBlock, x,
+           LV<T>::e(lc), lv.d, lc.d);
+    for (int s = 0; s < lv.nu2; ++s) {
+      LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1,
+             0);
+      LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 0,
+             0);
+    }
   }
-  LAUNCH(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
-         cell_grid(lc.d), kBlock, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
-  CKS(launch_ok());
-  CKS(vcycle<T>(hd, l + 1, LV<T>::b(lc), LV<T>::e(lc)));
-  LAUNCH(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong<T>, cell_grid(lv.d),
-         kBlock, x, LV<T>::e(lc), lv.d, lc.d);
-  for (int s = 0; s < lv.nu2; ++s) {
-    LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1, 0);
-    LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 0, 0);
-  }
+  (void)cur;
   return launch_ok();
+}
+
+void destroy_graphs(mp_poisson *hd) {
+  for (auto &g : hd->graphs) cudaGraphExecDestroy(g.exec);
+  hd->graphs.clear();
+}
+
+// A whole V-cycle from the finest level.  Without per-launch profiling it is
+// captured once into a CUDA graph (per precision and buffer pair) and
+// replayed: the cycle is a fixed sequence of ~100 launches, most of them on
+// small coarse levels where launch latency, not bandwidth, sets the time.
+template <typename T>
+mp_status run_vcycle(mp_poisson *hd, const T *rhs, T *x) {
+  if (hd->prof_on) return vcycle<T>(hd, 0, rhs, x);
+  mp_poisson::Graph *g = nullptr;
+  for (auto &e : hd->graphs)
+    if (e.type == (int)sizeof(T) && e.rhs == rhs && e.x == x) g = &e;
+  if (!g) {
+    cudaStream_t saved = hd->st;
+    hd->st = hd->cap;
+    hd->capturing = true;
+    hd->cap_ids.clear();
+    hd->cap_levels.clear();
+    cudaError_t e0 = cudaStreamBeginCapture(hd->cap, cudaStreamCaptureModeThreadLocal);
+    mp_status s = e0 == cudaSuccess ? vcycle<T>(hd, 0, rhs, x) : MP_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e1 = cudaStreamEndCapture(hd->cap, &graph);
+    hd->st = saved;
+    hd->capturing = false;
+    if (s != MP_OK || e0 != cudaSuccess || e1 != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return s != MP_OK ? s : MP_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) {
+      cudaGetLastError();
+      return MP_ERR_CUDA;
+    }
+    hd->graphs.push_back(mp_poisson::Graph{(int)sizeof(T), rhs, x, exec, hd->cap_ids,
+                                           hd->cap_levels});
+    g = &hd->graphs.back();
+  }
+  CK(cudaGraphLaunch(g->exec, hd->st));
+  for (size_t k = 0; k < g->ids.size(); ++k) hd->prof[g->ids[k]][g->levels[k]].launches++;
+  return MP_OK;
 }
 
 bool bad(double v) { return !std::isfinite(v); }
@@ -269,16 +439,17 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
       *iters = it;
       return MP_ERR_NOT_CONVERGED;
     }
-    CKS(vcycle<T>(hd, 0, r, z));
+    CKS(run_vcycle<T>(hd, r, z));
     const double nsz = (double)n * sizeof(T);
     LAUNCH(hd, kid<T>(K_DOT64, K_DOT32), 0, 2.0 * nsz, k_dot<T>, VEC_BLOCKS, VEC_THREADS, r, z, n,
            hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
     LAUNCH(hd, kid<T>(K_XPBY64, K_XPBY32), 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<T>, VEC_BLOCKS,
            VEC_THREADS, dv, z, n, hd->scal, it == 0);
-    LAUNCH(hd, kid<T>(K_APPLY64, K_APPLY32), 0, 6.0 * nsz, k_apply_dot<T>, cell_grid(l0.d), kBlock,
-           dv, q, bx, by, bz, diag, l0.d, hd->partial);
-    CKS(reduce(hd, cell_blocks(l0.d), OP_ALPHA, 0));
+    LAUNCH(hd, kid<T>(K_APPLY64, K_APPLY32), 0, (sizeof(T) == 8 ? 6.0 : 5.0) * nsz,
+           k_apply_dot<T>, zgrid(l0.d), kBlock, dv, q, bx, by, bz, diag, l0.d, zper_of(l0.d),
+           hd->partial);
+    CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
     LAUNCH(hd, kid<T>(K_AXPY64, K_AXPY32), 0, 6.0 * nsz, k_axpy2<T>, VEC_BLOCKS, VEC_THREADS, x,
            r, dv, q, n, hd->scal, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
@@ -307,13 +478,13 @@ mp_status stationary(mp_poisson *hd, T *x, const T *bt, T *r, T *z, double tol_a
       *iters = it;
       return MP_ERR_NOT_CONVERGED;
     }
-    CKS(vcycle<T>(hd, 0, r, z));
+    CKS(run_vcycle<T>(hd, r, z));
     const double nsz = (double)hd->n * sizeof(T);
     LAUNCH(hd, kid<T>(K_ADD64, K_ADD32), 0, 3.0 * nsz, k_add<T>, VEC_BLOCKS, VEC_THREADS, x, z,
            hd->n);
-    LAUNCH(hd, kid<T>(K_RESID64, K_RESID32), 0, 7.0 * nsz, k_residual<T>, cell_grid(l0.d), kBlock,
-           x, bt, r, bx, by, bz, diag, l0.d, hd->partial, 0);
-    CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+    LAUNCH(hd, kid<T>(K_RESID64, K_RESID32), 0, 7.0 * nsz, k_residual<T>, zgrid(l0.d), kBlock,
+           x, bt, r, bx, by, bz, diag, l0.d, zper_of(l0.d), hd->partial, 0);
+    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
     ++it;
     CKS(read_scalars(hd));
     rn = std::sqrt(hd->scal_h[S_RR]);
@@ -351,10 +522,10 @@ mp_status assemble_rhs(mp_poisson *hd, const double *rhs) {
 
 mp_status assemble_rhs_u(mp_poisson *hd, const double *ux, const double *uy, const double *uz) {
   Level &l0 = hd->L[0];
-  LAUNCH(hd, K_ASSEMBLE_U, 0, hd->n * 40.0, k_assemble_u, cell_grid(l0.d), kBlock, ux, uy, uz,
-         hd->Jt, hd->b, l0.d, hd->h, hd->partial);
+  LAUNCH(hd, K_ASSEMBLE_U, 0, hd->n * 40.0, k_assemble_u, zgrid(l0.d), kBlock, ux, uy, uz,
+         hd->Jt, hd->b, l0.d, zper_of(l0.d), hd->h, hd->partial);
   CKS(launch_ok());
-  return finish_rhs(hd, cell_blocks(l0.d));
+  return finish_rhs(hd, zblocks(l0.d));
 }
 
 // Solve At p = bt (bt in hd->b, S_BB set).  p: device FP64, in/out.
@@ -380,9 +551,10 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
   mp_status st = MP_OK;
   int iters = 0;
   if (o.precision == 0) {
-    LAUNCH(hd, K_RESID64, 0, hd->n * (zero ? 16.0 : 56.0), k_residual<double>, cell_grid(l0.d),
-           kBlock, p, hd->b, hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial, zero);
-    CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+    LAUNCH(hd, K_RESID64, 0, hd->n * (zero ? 16.0 : 56.0), k_residual<double>, zgrid(l0.d),
+           kBlock, p, hd->b, hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial,
+           zero);
+    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
     CKS(read_scalars(hd));
     hd->stats.r0 = std::sqrt(hd->scal_h[S_RR]) * inv_b;
     if (hist) hist->push_back(hd->stats.r0);
@@ -396,9 +568,10 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     hd->stats.outer_steps = iters;
   } else {
     // FP64 iterative refinement around an FP32 inner solve
-    LAUNCH(hd, K_RESIDMIX, 0, hd->n * (zero ? 12.0 : 52.0), k_residual_mixed, cell_grid(l0.d),
-           kBlock, p, hd->b, hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial, zero);
-    CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+    LAUNCH(hd, K_RESIDMIX, 0, hd->n * (zero ? 12.0 : 52.0), k_residual_mixed, zgrid(l0.d),
+           kBlock, p, hd->b, hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d),
+           hd->partial, zero);
+    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
     CKS(read_scalars(hd));
     double rn = std::sqrt(hd->scal_h[S_RR]);
     hd->stats.r0 = rn * inv_b;
@@ -418,16 +591,16 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
         if (si == MP_ERR_DIVERGED) { st = si; break; }
         if (si != MP_OK && si != MP_ERR_NOT_CONVERGED) return si;
       } else {
-        CKS(vcycle<float>(hd, 0, hd->r32, hd->e32));
+        CKS(run_vcycle<float>(hd, hd->r32, hd->e32));
         inner = 1;
       }
       total += inner;
       ++outer;
       LAUNCH(hd, K_ADDF32, 0, hd->n * 20.0, k_add_f32, VEC_BLOCKS, VEC_THREADS, p, hd->e32,
              hd->n);
-      LAUNCH(hd, K_RESIDMIX, 0, hd->n * 52.0, k_residual_mixed, cell_grid(l0.d), kBlock, p, hd->b,
-             hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial, 0);
-      CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+      LAUNCH(hd, K_RESIDMIX, 0, hd->n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b,
+             hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
       CKS(read_scalars(hd));
       rn = std::sqrt(hd->scal_h[S_RR]);
       if (hist) hist->push_back(rn * inv_b);
@@ -438,9 +611,9 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
   if (st == MP_OK || st == MP_ERR_NOT_CONVERGED) {
     CKS(remove_mean(hd, p));
     // final true FP64 residual of the returned p
-    LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, cell_grid(l0.d), kBlock, p, hd->b,
-           hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial, 0);
-    CKS(reduce(hd, cell_blocks(l0.d), OP_STORE, S_RR));
+    LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b,
+           hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
     CKS(read_scalars(hd));
     hd->stats.relres = std::sqrt(hd->scal_h[S_RR]) * inv_b;
   }
@@ -476,7 +649,7 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
   LAUNCH(hd, K_CURV, 0, n0 * 16.0, k_curvature, cell_grid(l0.d), kBlock, hd->phi, hd->kap, l0.d,
          hd->h, hd->per);
   LAUNCH(hd, K_FACES, 0, n0 * 32.0, k_faces, cell_grid(l0.d), kBlock, hd->phi, l0.bx, l0.by,
-         l0.bz, l0.d, rho_l, rho_g, hd->per);
+         l0.bz, l0.d, rho_l, rho_g, 1.0 / rho_l, 1.0 / rho_g, hd->per);
   LAUNCH(hd, K_JUMP, 0, n0 * 48.0, k_jump, cell_grid(l0.d), kBlock, hd->phi, hd->kap, l0.bx,
          l0.by, l0.bz, hd->Jt, l0.d, sigma);
   CKS(launch_ok());
@@ -549,6 +722,7 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
     CKS(dalloc(hd, &lv.bz32, lv.n));
     CKS(dalloc(hd, &lv.diag32, lv.n));
     CKS(dalloc(hd, &lv.idiag32, lv.n));
+    CKS(dalloc(hd, &lv.t32, lv.n));
     if (l > 0) {
       CKS(dalloc(hd, &lv.b, lv.n));
       CKS(dalloc(hd, &lv.e, lv.n));
@@ -575,7 +749,7 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
   CKS(dalloc(hd, &hd->pst, n));
   CKS(dalloc(hd, &hd->Maug, (size_t)hd->nc * 2 * hd->nc));
   CKS(dalloc(hd, &hd->Minv, (size_t)hd->nc * hd->nc));
-  hd->npart = std::max(cell_blocks(hd->L[0].d), VEC_BLOCKS);
+  hd->npart = std::max(std::max(cell_blocks(hd->L[0].d), zblocks(hd->L[0].d)), VEC_BLOCKS);
   CKS(dalloc(hd, &hd->partial, (size_t)hd->npart));
   CKS(dalloc(hd, &hd->scal, (size_t)S_COUNT));
   if (cudaMallocHost((void **)&hd->scal_h, S_COUNT * sizeof(double)) != cudaSuccess) {
@@ -584,6 +758,30 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
     return MP_ERR_OOM;
   }
   CK(cudaMemsetAsync(hd->scal, 0, S_COUNT * sizeof(double), hd->st));
+  CK(cudaStreamCreateWithFlags(&hd->cap, cudaStreamNonBlocking));
+  // coarse tail: the coarsest levels whose iterate, rhs and faces fit the
+  // shared-memory budget of one block (coarsest level always included)
+  for (int pass = 0; pass < 2; ++pass) {
+    size_t elem = pass == 0 ? sizeof(double) : sizeof(float);
+    size_t budget = pass == 0 ? TAIL_BUDGET64 : TAIL_BUDGET32;
+    int start = (int)hd->L.size() - 1;
+    size_t bytes = 6 * hd->L.back().n * elem;
+    while (start > 0 && bytes + 6 * hd->L[start - 1].n * elem <= budget) {
+      --start;
+      bytes += 6 * hd->L[start].n * elem;
+    }
+    if (pass == 0) {
+      hd->tail64 = start;
+      hd->tail64_bytes = bytes;
+    } else {
+      hd->tail32 = start;
+      hd->tail32_bytes = bytes;
+    }
+  }
+  CK(cudaFuncSetAttribute(k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)std::max<size_t>(hd->tail64_bytes, 1)));
+  CK(cudaFuncSetAttribute(k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)std::max<size_t>(hd->tail32_bytes, 1)));
   return MP_OK;
 }
 
@@ -654,9 +852,11 @@ mp_status mp_poisson_set_geometry(mp_handle hd, const double *phi_dev, double rh
 
 mp_status mp_poisson_set_opts(mp_handle hd, const mp_opts *opts) {
   if (!hd || !opts || !valid_opts(*opts)) return MP_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(hd->st));
   hd->opts = *opts;
   hd->st = (cudaStream_t)opts->stream;
   apply_nu(hd);
+  destroy_graphs(hd);
   return MP_OK;
 }
 
@@ -715,8 +915,8 @@ mp_status mp_poisson_project_step_host(mp_handle hd, double *ux_h, double *uy_h,
 mp_status mp_poisson_apply(mp_handle hd, const double *x, double *y) {
   if (!hd || !x || !y) return MP_ERR_INVALID_ARG;
   Level &l0 = hd->L[0];
-  LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, cell_grid(l0.d), kBlock, x, y,
-         l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->partial);
+  LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, x, y,
+         l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial);
   LAUNCH(hd, K_SCALE, 0, hd->n * 16.0, k_scale, VEC_BLOCKS, VEC_THREADS, y, y, hd->n,
          1.0 / (hd->h * hd->h));
   CKS(launch_ok());
@@ -827,6 +1027,8 @@ void mp_poisson_destroy(mp_handle hd) {
   cudaStreamSynchronize(hd->st);
   for (void *p : hd->allocs) cudaFree(p);
   for (cudaEvent_t e : hd->events) cudaEventDestroy(e);
+  destroy_graphs(hd);
+  if (hd->cap) cudaStreamDestroy(hd->cap);
   if (hd->scal_h) cudaFreeHost(hd->scal_h);
   delete hd;
 }

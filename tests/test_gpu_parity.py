@@ -36,6 +36,24 @@ def owned(f):
     return f.fx[:, :, :-1], f.fy[:, :-1, :], f.fz[:-1, :, :]
 
 
+def band(phi, bc):
+    """Cells with a face neighbour of the other fluid (periodic axes wrap;
+    across a wall there is no neighbour)."""
+    gas = phi > 0
+    out = np.zeros_like(gas)
+    for axis, kind in enumerate(bc):
+        ax = 2 - axis
+        for shift in (1, -1):
+            nb = np.roll(gas, shift, axis=ax)
+            diff = nb != gas
+            if kind == N:
+                edge = [slice(None)] * 3
+                edge[ax] = 0 if shift == 1 else -1
+                diff[tuple(edge)] = False
+            out |= diff
+    return out
+
+
 def rel_max(a, b):
     return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
 
@@ -87,7 +105,12 @@ def test_setup_fields_match_oracle(name):
     kap = oracle.curvature(phi, h, bc)
     f = oracle.faces(phi, prm["rho_l"], prm["rho_g"], bc)
     J = oracle.jump(phi, kap, f, h, prm["sigma"], bc)
-    assert rel_max(got["kappa"], kap) < 1e-12
+    # curvature is evaluated in the interface band (the only cells the jump
+    # reads) and is zero elsewhere
+    bnd = band(phi, bc)
+    assert bnd.any()
+    assert rel_max(got["kappa"][bnd], kap[bnd]) < 1e-12
+    assert np.all(got["kappa"][~bnd] == 0.0)
     for g, o in zip((got["bx"], got["by"], got["bz"]), owned(f)):
         assert rel_max(g, o) < 1e-13
     assert rel_max(got["J"], J) < 1e-11
@@ -121,13 +144,17 @@ def test_solve_matches_oracle(name, precision, method):
     ref = oracle.solve(phi, rhs, h, prm["rho_l"], prm["rho_g"], prm["sigma"], bc, tol=REF_TOL)
     assert ref["iters"] >= 0
     s = make(phi, prm, precision=precision, method=method, max_iters=400)
-    p, it, hist = s.solve(dev(rhs), tol=TOL)
+    # The stationary V-cycle leaves its error in smooth modes, which the
+    # residual underweights: on the all-wall grid it needs 2e-11 to stay
+    # within the 1e-8 parity bar (at 1e-10 it measured 1.3e-8).
+    tol = TOL if method == 0 else 2e-11
+    p, it, hist = s.solve(dev(rhs), tol=tol)
     st = s.stats()
     pg = host(p)
     assert abs(pg.mean()) < 1e-12 * np.abs(pg).max()
-    assert st["relres"] <= TOL
+    assert st["relres"] <= tol
     assert hist[0] == pytest.approx(st["r0"])
-    assert hist[-1] <= TOL
+    assert hist[-1] <= tol
     # residual of the GPU pressure evaluated by the oracle's own operator
     _, rn = oracle.residual(ref["faces"], ref["b"], pg, h, bc)
     assert rn / np.linalg.norm(ref["b"]) <= 1.5 * TOL
@@ -268,7 +295,10 @@ def test_full_size_256_properties(precision):
     assert rn / np.linalg.norm(b) <= 1.5 * TOL
     g = s.fields()
     idx = np.random.Generator(np.random.PCG64(3)).integers(0, phi.size, 4096)
-    for key, ref in (("kappa", kap), ("bx", owned(f)[0]), ("bz", owned(f)[2]), ("J", J)):
-        got = host(g[key]).ravel()[idx]
-        assert np.max(np.abs(got - ref.ravel()[idx])) <= 1e-11 * max(np.abs(ref).max(), 1e-300)
+    bidx = np.flatnonzero(band(phi, bc).ravel())
+    bidx = bidx[np.random.Generator(np.random.PCG64(4)).integers(0, bidx.size, 4096)]
+    for key, ref, ix in (("kappa", kap, bidx), ("bx", owned(f)[0], idx), ("bz", owned(f)[2], idx),
+                         ("J", J, idx), ("J", J, bidx)):
+        got = host(g[key]).ravel()[ix]
+        assert np.max(np.abs(got - ref.ravel()[ix])) <= 1e-11 * max(np.abs(ref).max(), 1e-300)
     s.close()
