@@ -83,6 +83,7 @@ typedef struct {
   double relres;       /* final ||b - A p|| / ||b||, FP64, true residual */
   double r0;           /* initial ||b - A p0|| / ||b|| */
   int used_net;        /* 1 if the learned guess was kept, 0 if not requested or rejected */
+  double net_relres;   /* ||b - A p_net|| / ||b|| of the learned guess (0 if not requested) */
   int levels;          /* multigrid levels */
   int coarse_n;        /* unknowns of the coarsest (direct) level */
 } mp_stats;

@@ -133,21 +133,27 @@ def init_params(rng):
     return p
 
 
-def unet_forward(p, x):
-    """Returns (output (nz, ny, nx), cache of every activation)."""
+def unet_forward(p, x, rnd=None):
+    """Returns (output (nz, ny, nx), cache of every activation).
+
+    rnd (optional) is applied to every stored activation (convolution
+    outputs after ReLU and pooled tensors): a test can pass a rounding to
+    the kernels' storage format to compare on identically rounded operands.
+    """
+    rnd = (lambda a: a) if rnd is None else rnd
     cache = {"in": x}
 
     def cr(name, inp):
         z = conv3d(inp, p[name + ".w"], p[name + ".b"])
-        y = relu(z)
+        y = rnd(relu(z))
         cache[name + ".in"] = inp
         cache[name + ".out"] = y
         return y
 
     e0 = cr("e0b", cr("e0a", x))
-    e1 = cr("e1b", cr("e1a", avgpool2(e0)))
-    e2 = cr("e2b", cr("e2a", avgpool2(e1)))
-    e3 = cr("e3b", cr("e3a", avgpool2(e2)))
+    e1 = cr("e1b", cr("e1a", rnd(avgpool2(e0))))
+    e2 = cr("e2b", cr("e2a", rnd(avgpool2(e1))))
+    e3 = cr("e3b", cr("e3a", rnd(avgpool2(e2))))
     d2 = cr("d2b", cr("d2a", np.concatenate([upsample2(e3), e2], axis=-1)))
     d1 = cr("d1b", cr("d1a", np.concatenate([upsample2(d2), e1], axis=-1)))
     d0 = cr("d0b", cr("d0a", np.concatenate([upsample2(d1), e0], axis=-1)))
@@ -156,38 +162,45 @@ def unet_forward(p, x):
     return out[..., 0], cache
 
 
-def unet_backward(p, cache, gout):
-    """Gradients of sum(out * gout) w.r.t. every parameter."""
+def unet_backward(p, cache, gout, rnd=None):
+    """Gradients of sum(out * gout) w.r.t. every parameter (and the input).
+
+    rnd (optional) is applied where activation gradients are stored (the
+    head's output gradient, every input gradient, the upsampling adjoint and
+    the merged skip + pooling gradient), to compare with kernels that keep
+    those tensors in a narrower format.
+    """
+    rnd = (lambda a: a) if rnd is None else rnd
     g = {}
     d0 = cache["d0"]
     gout = np.asarray(gout, dtype=np.float64)[..., None]
     g["head.w"] = (gout.reshape(-1, 1).T @ d0.reshape(-1, d0.shape[-1]))
     g["head.b"] = gout.reshape(-1, 1).sum(axis=0)
-    gd0 = gout @ p["head.w"]
+    gd0 = rnd(gout @ p["head.w"])
 
     def back(name, gy):
         y = cache[name + ".out"]
         gz = gy * (y > 0)
         g[name + ".w"] = conv3d_wgrad(cache[name + ".in"], gz)
         g[name + ".b"] = bias_grad(gz)
-        return conv3d_dgrad(gz, p[name + ".w"])
+        return rnd(conv3d_dgrad(gz, p[name + ".w"]))
 
     c0, c1, c2, c3 = CH
     gcat0 = back("d0a", back("d0b", gd0))
-    gd1 = upsample2_adjoint(gcat0[..., :c1])
+    gd1 = rnd(upsample2_adjoint(gcat0[..., :c1]))
     ge0 = gcat0[..., c1:]
     gcat1 = back("d1a", back("d1b", gd1))
-    gd2 = upsample2_adjoint(gcat1[..., :c2])
+    gd2 = rnd(upsample2_adjoint(gcat1[..., :c2]))
     ge1 = gcat1[..., c2:]
     gcat2 = back("d2a", back("d2b", gd2))
-    ge3 = upsample2_adjoint(gcat2[..., :c3])
+    ge3 = rnd(upsample2_adjoint(gcat2[..., :c3]))
     ge2 = gcat2[..., c3:]
     gp2 = back("e3a", back("e3b", ge3))
-    ge2 = ge2 + avgpool2_adjoint(gp2)
+    ge2 = rnd(ge2 + avgpool2_adjoint(gp2))
     gp1 = back("e2a", back("e2b", ge2))
-    ge1 = ge1 + avgpool2_adjoint(gp1)
+    ge1 = rnd(ge1 + avgpool2_adjoint(gp1))
     gp0 = back("e1a", back("e1b", ge1))
-    ge0 = ge0 + avgpool2_adjoint(gp0)
+    ge0 = rnd(ge0 + avgpool2_adjoint(gp0))
     gin = back("e0a", back("e0b", ge0))
     return g, gin
 

@@ -27,3 +27,4 @@ from .poisson import (  # noqa: F401
     mp_poisson_solve,
     mp_status_str,
 )
+from .net import Net, mp_conv3d_fwd, mp_conv3d_wgrad, mp_poisson_set_net  # noqa: F401

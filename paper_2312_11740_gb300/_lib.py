@@ -52,6 +52,7 @@ class mp_stats(ctypes.Structure):
         ("relres", ctypes.c_double),
         ("r0", ctypes.c_double),
         ("used_net", ctypes.c_int),
+        ("net_relres", ctypes.c_double),
         ("levels", ctypes.c_int),
         ("coarse_n", ctypes.c_int),
     ]
@@ -95,6 +96,25 @@ SIGNATURES = {
     "mp_poisson_get_profile": (_I, [_P, ctypes.POINTER(mp_kernel_prof), _I, _IP]),
     "mp_poisson_rhs_noalloc": (_I, [ctypes.c_longlong, _P, _P, _P, _P]),
     "mp_poisson_destroy": (None, [_P]),
+    "mp_poisson_set_net": (_I, [_P, _P]),
+    "mp_conv3d_fwd": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _P, _I, _I, _P, _P, _P]),
+    "mp_conv3d_wgrad": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P, _P]),
+    "mp_net_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _P]),
+    "mp_net_dims": (_I, [_P, _IP, _IP, _IP]),
+    "mp_net_param_count": (ctypes.c_size_t, [_P]),
+    "mp_net_set_params": (_I, [_P, _P]),
+    "mp_net_get_params": (_I, [_P, _P]),
+    "mp_net_features": (_I, [_P, _P, _P, _D, _D, _DP]),
+    "mp_net_get_input2": (_I, [_P, _P]),
+    "mp_net_set_input2": (_I, [_P, _P]),
+    "mp_net_forward": (_I, [_P, _P]),
+    "mp_net_train_step": (_I, [_P, _P, ctypes.c_float, _I, _DP]),
+    "mp_net_set_input": (_I, [_P, _P]),
+    "mp_net_backward": (_I, [_P, _P, _P]),
+    "mp_net_pressure": (_I, [_P, _D, _P]),
+    "mp_net_set_stream": (_I, [_P, _P]),
+    "mp_net_make_target": (_I, [_P, _P, _P]),
+    "mp_net_destroy": (None, [_P]),
 }
 
 _lib = None

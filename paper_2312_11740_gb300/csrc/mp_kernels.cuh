@@ -276,8 +276,9 @@ __global__ void k_coarse_solve(const double *__restrict__ Minv, const T *__restr
 }
 
 // ------------------------------------------------- A6: red-black smoother
-// One colour ((i+j+k) & 1 == colour): x_c = (sum_f beta_f x_nb - bt_c) / diag_c.
-// zero != 0 treats x as zero before the update (first sweep of a cycle).
+// One colour ((i+j+k) & 1 == colour): x_c = (sum_f beta_f x_nb - bt_c) / diag_c,
+// in place (a colour's update reads only the other colour).  zero != 0
+// treats x as zero before the update (first sweep of a cycle).
 template <typename T>
 __global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__restrict__ bx,
                        const T *__restrict__ by, const T *__restrict__ bz,
@@ -286,109 +287,23 @@ __global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__re
   if (t >= (d.nx >> 1) || j >= d.ny) return;
   int i = 2 * t + ((j + k + colour) & 1);
   size_t c = at(d, i, j, k);
+  size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
+  size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
+  size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+  const T wxl = bx[c], wxh = bx[xh], wyl = by[c], wyh = by[yh], wzl = bz[c], wzh = bz[zh];
   T s = -b[c];
   if (!zero) {
-    size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
-    size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
-    size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
-    s = fma(bx[c], x[xl], s);
-    s = fma(bx[xh], x[xh], s);
-    s = fma(by[c], x[yl], s);
-    s = fma(by[yh], x[yh], s);
-    s = fma(bz[c], x[zl], s);
-    s = fma(bz[zh], x[zh], s);
+    s = fma(wxl, x[xl], s);
+    s = fma(wxh, x[xh], s);
+    s = fma(wyl, x[yl], s);
+    s = fma(wyh, x[yh], s);
+    s = fma(wzl, x[zl], s);
+    s = fma(wzh, x[zh], s);
   }
-  x[c] = s * idiag[c];
-}
-
-// ------------------------------------ A6: fused red-black sweep (FP32)
-// One full sweep per launch (colour c1 first, then the other; red = even
-// i+j+k), out of place (xin -> xout) so that no CTA reads a value another CTA
-// has already updated.  A CTA owns an FX x FY x FZ tile: it first computes
-// the new first-colour values on the tile plus a one-cell ring (wrapped)
-// into shared memory, then the second colour of the tile from them, and
-// writes both colours.  1/diag is formed from the six
-// face coefficients on the fly.  DRAM traffic per sweep is one read of x, b
-// and the three face arrays and one write of x (24 B/cell); the ring reads
-// come from L2.  zero != 0: xin is taken as 0 (first sweep of a cycle).
-constexpr int FUSED_THREADS = 256;
-
-__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
-template <int FX, int FY, int FZ>
-__global__ void __launch_bounds__(FUSED_THREADS)
-k_rbgs_fused(const float *__restrict__ xin, float *__restrict__ xout, const float *__restrict__ b,
-             const float *__restrict__ bx, const float *__restrict__ by,
-             const float *__restrict__ bz, Dims d, int zero, int c1) {
-  constexpr int EX = FX + 2, EY = FY + 2, EZ = FZ + 2, HALF = EX / 2;
-  static_assert(FX % 2 == 0, "first-colour cells alternate along x");
-  __shared__ float sred[EZ][EY][EX];
-  const int nx = d.nx, ny = d.ny, nz = d.nz, sy = nx, sz = nx * ny;
-  const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY, k0 = blockIdx.z * FZ;
-  // phase 1: first-colour cells of the tile and its one-cell ring (wrapped).
-  // Ring cells past the last valid cell of a ragged tile are skipped.
-  for (int e = threadIdx.x; e < EY * EZ * HALF; e += FUSED_THREADS) {
-    const int row = e / HALF, t = e - row * HALF;
-    const int ey = row % EY, ez = row / EY;
-    int j = j0 + ey - 1, k = k0 + ez - 1;
-    if (j > ny || k > nz) continue;
-    j += j < 0 ? ny : 0;
-    j -= j >= ny ? ny : 0;
-    k += k < 0 ? nz : 0;
-    k -= k >= nz ? nz : 0;
-    // parity of unwrapped and wrapped indices agree: smoothed axes are even
-    const int ex = 2 * t + ((i0 - 1 + j + k + c1) & 1);
-    int i = i0 - 1 + ex;
-    if (i > nx) continue;
-    i += i < 0 ? nx : 0;
-    i -= i >= nx ? nx : 0;
-    const int c = i + j * sy + k * sz;
-    const int xp = i == nx - 1 ? c - (nx - 1) : c + 1;
-    const int yp = j == ny - 1 ? c - (ny - 1) * sy : c + sy;
-    const int zp = k == nz - 1 ? c - (nz - 1) * sz : c + sz;
-    const float wxl = bx[c], wxh = bx[xp], wyl = by[c], wyh = by[yp], wzl = bz[c], wzh = bz[zp];
-    const float den = ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh);
-    float num = -b[c];
-    if (!zero) {
-      const int xm = i == 0 ? c + (nx - 1) : c - 1;
-      const int ym = j == 0 ? c + (ny - 1) * sy : c - sy;
-      const int zm = k == 0 ? c + (nz - 1) * sz : c - sz;
-      num = fmaf(wxl, xin[xm], num);
-      num = fmaf(wxh, xin[xp], num);
-      num = fmaf(wyl, xin[ym], num);
-      num = fmaf(wyh, xin[yp], num);
-      num = fmaf(wzl, xin[zm], num);
-      num = fmaf(wzh, xin[zp], num);
-    }
-    sred[ez][ey][ex] = __fdividef(num, den);
-  }
-  __syncthreads();
-  // phase 2: the tile; first colour copies out, second colour is updated
-  for (int e = threadIdx.x; e < FX * FY * FZ; e += FUSED_THREADS) {
-    const int tx = e % FX, ty = (e / FX) % FY, tz = e / (FX * FY);
-    const int i = i0 + tx, j = j0 + ty, k = k0 + tz;
-    if (i >= nx || j >= ny || k >= nz) continue;
-    const int c = i + j * sy + k * sz;
-    const int ex = tx + 1, ey = ty + 1, ez = tz + 1;
-    float v;
-    if (((i + j + k) & 1) == c1) {
-      v = sred[ez][ey][ex];
-    } else {
-      const int xp = i == nx - 1 ? c - (nx - 1) : c + 1;
-      const int yp = j == ny - 1 ? c - (ny - 1) * sy : c + sy;
-      const int zp = k == nz - 1 ? c - (nz - 1) * sz : c + sz;
-      const float wxl = bx[c], wxh = bx[xp], wyl = by[c], wyh = by[yp], wzl = bz[c], wzh = bz[zp];
-      const float den = ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh);
-      float num = -b[c];
-      num = fmaf(wxl, sred[ez][ey][ex - 1], num);
-      num = fmaf(wxh, sred[ez][ey][ex + 1], num);
-      num = fmaf(wyl, sred[ez][ey - 1][ex], num);
-      num = fmaf(wyh, sred[ez][ey + 1][ex], num);
-      num = fmaf(wzl, sred[ez - 1][ey][ex], num);
-      num = fmaf(wzh, sred[ez + 1][ey][ex], num);
-      v = __fdividef(num, den);
-    }
-    xout[c] = v;
+  if (sizeof(T) == 8) {
+    x[c] = s * idiag[c];  // stored 1/diag: no FP64 division
+  } else {
+    x[c] = __fdividef((float)s, (float)(((wxl + wxh) + (wyl + wyh)) + (wzl + wzh)));
   }
 }
 

@@ -1,0 +1,1252 @@
+// Learned warm start: BF16 implicit-GEMM 3x3x3 convolutions on the 5th-generation
+// tensor cores (tcgen05.mma, operands in shared memory, FP32 accumulator in
+// tensor memory), and the U-Net built from them.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mp_net.h"
+
+namespace mpnet {
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------- tcgen05 helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// Shared-memory matrix descriptor, no swizzle: start address, leading- and
+// stride-dimension byte offsets (all >> 4), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B,
+// majorness of A/B (0 = K-major), N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n, int amaj, int bmaj) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)amaj << 15) | ((uint32_t)bmaj << 16) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(mbar)));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+}
+// Bounded wait for the phase of the given parity to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < (1L << 24) && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity));
+  }
+  return done != 0;
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *out) {
+  uint32_t v[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) out[q] = __uint_as_float(v[q]);
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// ------------------------------------------------------------ conv forward
+// D[128 voxels][COUT] = A[128][K] B[COUT][K]^T with K = 27 taps x Cin (tap
+// major).  A row = the input channels of one voxel's neighbour for a tap,
+// gathered from up to two tensors (the first optionally at half resolution,
+// read through nearest-neighbour upsampling: the decoder's up+concat fused
+// into the gather).  Smem tiles use the no-swizzle K-major core-matrix
+// layout: element (r, k) of an R x 64 stage tile at
+// (k/8)*(R/8)*128 + (r/8)*128 + (r%8)*16 + (k%8)*2 bytes.
+struct ConvGeom {
+  int nx, ny, nz;   // output (and full-resolution input) grid
+  int ca, cb;       // channels of the two inputs (cb = 0: single input)
+  int up_a;         // 1: input a is stored at half resolution
+  int cin;          // ca + cb (multiple of 16)
+};
+
+constexpr int CONV_THREADS = 128;
+constexpr int NSTAGE = 3;
+constexpr int STAGE_K = 64;                  // K elements per stage (4 MMAs of K = 16)
+constexpr int A_STAGE_BYTES = 128 * STAGE_K * 2;
+
+// tcgen05.alloc takes a power-of-two column count of at least 32
+template <int COUT>
+__host__ __device__ constexpr int tmem_cols() {
+  return COUT <= 32 ? 32 : (COUT <= 64 ? 64 : (COUT <= 128 ? 128 : 256));
+}
+template <int COUT>
+__host__ __device__ constexpr int b_stage_bytes() {
+  return COUT * STAGE_K * 2;
+}
+template <int COUT>
+__host__ __device__ constexpr int conv_smem_bytes() {
+  return NSTAGE * (A_STAGE_BYTES + b_stage_bytes<COUT>()) + 1024;
+}
+
+// 16 input channels [ci0, ci0+16) of the voxel (x, y, z) (zero outside)
+__device__ __forceinline__ void gather16(const bf16 *__restrict__ xa, const bf16 *__restrict__ xb,
+                                         const ConvGeom &g, int x, int y, int z, int ci0,
+                                         uint4 &lo, uint4 &hi) {
+  lo = make_uint4(0, 0, 0, 0);
+  hi = lo;
+  if (x < 0 || y < 0 || z < 0 || x >= g.nx || y >= g.ny || z >= g.nz) return;
+  const uint4 *src;
+  if (ci0 < g.ca) {
+    int ax = x, ay = y, az = z, anx = g.nx, any = g.ny;
+    if (g.up_a) {
+      ax >>= 1;
+      ay >>= 1;
+      az >>= 1;
+      anx >>= 1;
+      any >>= 1;
+    }
+    src = reinterpret_cast<const uint4 *>(
+        xa + (((size_t)az * any + ay) * anx + ax) * g.ca + ci0);
+  } else {
+    src = reinterpret_cast<const uint4 *>(
+        xb + (((size_t)z * g.ny + y) * g.nx + x) * g.cb + (ci0 - g.ca));
+  }
+  lo = __ldg(src);
+  hi = __ldg(src + 1);
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(CONV_THREADS)
+k_conv3d_fwd(const bf16 *__restrict__ xa, const bf16 *__restrict__ xb,
+             const bf16 *__restrict__ w, const float *__restrict__ bias, bf16 *__restrict__ y,
+             float *__restrict__ y32, ConvGeom g, int relu, int *__restrict__ err) {
+  constexpr int TM = tmem_cols<COUT>();  // TMEM allocation: a power of two >= 32
+  constexpr int BST = b_stage_bytes<COUT>();
+  extern __shared__ __align__(1024) uint8_t conv_smem[];
+  uint8_t *sm = conv_smem + ((1024 - (smem_u32(conv_smem) & 1023)) & 1023);
+  uint8_t *sA = sm;
+  uint8_t *sB = sm + NSTAGE * A_STAGE_BYTES;
+  __shared__ __align__(8) uint64_t mbar[NSTAGE];
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // this thread's voxel: brick of 8 x 4 x 4 voxels
+  const int vx = blockIdx.x * 8 + (tid & 7), vy = blockIdx.y * 4 + ((tid >> 3) & 3),
+            vz = blockIdx.z * 4 + (tid >> 5);
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(&mbar[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 0) tmem_alloc(&tslot, TM);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = tslot;
+
+  const int cpt = g.cin >> 4;          // 16-channel chunks per tap
+  const int ksteps = 27 * cpt;
+  const int nst = (ksteps + 3) >> 2;
+  const size_t wrow = (size_t)27 * g.cin;  // weights per output channel
+  constexpr uint32_t IDESC = idesc_bf16(128, COUT, 0, 0);
+  bool ok = true;
+  for (int s = 0; s < nst && ok; ++s) {
+    const int buf = s % NSTAGE;
+    if (s >= NSTAGE) {
+      bool done = mbar_wait(&mbar[buf], (uint32_t)((s / NSTAGE - 1) & 1));
+      if (!done) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) {
+        ok = false;
+        break;
+      }
+    }
+    uint8_t *a_st = sA + buf * A_STAGE_BYTES;
+    uint8_t *b_st = sB + buf * BST;
+    const int kq = min(4, ksteps - 4 * s);
+    // A: this thread's voxel, 4 K-steps x 16 channels
+    for (int q = 0; q < kq; ++q) {
+      const int j = 4 * s + q, t = j / cpt, ci0 = (j - t * cpt) << 4;
+      const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+      uint4 lo, hi;
+      gather16(xa, xb, g, vx + dx, vy + dy, vz + dz, ci0, lo, hi);
+      const uint32_t rowoff = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
+      *reinterpret_cast<uint4 *>(a_st + (2 * q) * 2048 + rowoff) = lo;
+      *reinterpret_cast<uint4 *>(a_st + (2 * q + 1) * 2048 + rowoff) = hi;
+    }
+    // B: COUT rows x kq K-steps x 2 halves of 8 channels
+    for (int e = tid; e < COUT * kq * 2; e += CONV_THREADS) {
+      const int co = e % COUT, qh = e / COUT, q = qh >> 1, h = qh & 1;
+      const int j = 4 * s + q, t = j / cpt, ci0 = (j - t * cpt) << 4;
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(w + co * wrow + (size_t)t * g.cin +
+                                                            ci0 + 8 * h));
+      *reinterpret_cast<uint4 *>(b_st + (2 * q + h) * (COUT / 8) * 128 + (co >> 3) * 128 +
+                                 (co & 7) * 16) = v;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(a_st), b0 = smem_u32(b_st);
+      for (int q = 0; q < kq; ++q) {
+        const uint64_t da = sdesc(a0 + 2 * q * 2048, 2048, 128);
+        const uint64_t db = sdesc(b0 + 2 * q * (COUT / 8) * 128, (COUT / 8) * 128, 128);
+        mma_bf16(taddr, da, db, IDESC, (s > 0 || q > 0) ? 1u : 0u);
+      }
+      mma_commit(&mbar[buf]);
+    }
+  }
+  // wait for the last stage's MMAs (the commit tracks all earlier ones too)
+  if (ok) {
+    const int last = nst - 1;
+    bool done = mbar_wait(&mbar[last % NSTAGE], (uint32_t)((last / NSTAGE) & 1));
+    if (!done) abort_flag = 1;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (abort_flag) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    const bool inside = vx < g.nx && vy < g.ny && vz < g.nz;
+    const size_t vox = ((size_t)vz * g.ny + vy) * g.nx + vx;
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      float acc[16];
+      tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + c0, acc);
+      if (inside) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          float v = acc[q] + (bias ? bias[c0 + q] : 0.f);
+          acc[q] = relu ? fmaxf(v, 0.f) : v;
+        }
+        if (y32) {
+          float4 *o = reinterpret_cast<float4 *>(y32 + vox * COUT + c0);
+          for (int q = 0; q < 4; ++q) o[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        } else {
+          __align__(16) bf16 hv[16];
+          for (int q = 0; q < 16; ++q) hv[q] = __float2bfloat16_rn(acc[q]);
+          uint4 *o = reinterpret_cast<uint4 *>(y + vox * COUT + c0);
+          o[0] = *reinterpret_cast<uint4 *>(&hv[0]);
+          o[1] = *reinterpret_cast<uint4 *>(&hv[8]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(taddr, TM);
+}
+
+
+// --------------------------------------------------------- conv weight grad
+// D[128 rows (t, ci)][COUT] = sum over a chunk of voxels v of
+// X[v + off_t][ci] * G[v][co]: rows are (tap, input channel) pairs, K runs
+// over voxels.  Each CTA reduces one chunk of WG_VOX voxels into FP32
+// partials; k_wgrad_reduce sums the chunks in a fixed order (split-K,
+// deterministic).  Operands are stored K-major: a 16-byte load of 8
+// channels of one voxel is written as 8 two-byte elements of one smem
+// column.
+constexpr int WG_VOX = 2048;  // voxels per CTA (32 stages of 64)
+
+__device__ __forceinline__ void gather8(const bf16 *__restrict__ xa, const bf16 *__restrict__ xb,
+                                        const ConvGeom &g, int x, int y, int z, int ci0,
+                                        uint4 &v) {
+  v = make_uint4(0, 0, 0, 0);
+  if (x < 0 || y < 0 || z < 0 || x >= g.nx || y >= g.ny || z >= g.nz) return;
+  if (ci0 < g.ca) {
+    int ax = x, ay = y, az = z, anx = g.nx, any = g.ny;
+    if (g.up_a) {
+      ax >>= 1;
+      ay >>= 1;
+      az >>= 1;
+      anx >>= 1;
+      any >>= 1;
+    }
+    v = __ldg(reinterpret_cast<const uint4 *>(xa + (((size_t)az * any + ay) * anx + ax) * g.ca + ci0));
+  } else {
+    v = __ldg(reinterpret_cast<const uint4 *>(xb + (((size_t)z * g.ny + y) * g.nx + x) * g.cb +
+                                              (ci0 - g.ca)));
+  }
+}
+
+__device__ __forceinline__ void scatter8(uint8_t *tile, int r8, int k, const uint4 &v) {
+  // 8 rows r8*8 .. r8*8+7 at K column k of a K-major 128-row tile
+  const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+  uint8_t *base = tile + (k >> 3) * 2048 + r8 * 128 + (k & 7) * 2;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) *reinterpret_cast<bf16 *>(base + q * 16) = e[q];
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(CONV_THREADS)
+k_conv3d_wgrad(const bf16 *__restrict__ xa, const bf16 *__restrict__ xb,
+               const bf16 *__restrict__ gr, ConvGeom g, float *__restrict__ partial,
+               int *__restrict__ err) {
+  constexpr int TM = tmem_cols<COUT>();
+  constexpr int BST = b_stage_bytes<COUT>();
+  extern __shared__ __align__(1024) uint8_t conv_smem[];
+  uint8_t *sm = conv_smem + ((1024 - (smem_u32(conv_smem) & 1023)) & 1023);
+  uint8_t *sA = sm;
+  uint8_t *sB = sm + NSTAGE * A_STAGE_BYTES;
+  __shared__ __align__(8) uint64_t mbar[NSTAGE];
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rows = 27 * g.cin, m0 = blockIdx.x * 128;
+  const long nvox = (long)g.nx * g.ny * g.nz;
+  const long v0 = (long)blockIdx.y * WG_VOX;
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(&mbar[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 0) tmem_alloc(&tslot, TM);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = tslot;
+  constexpr uint32_t IDESC = idesc_bf16(128, COUT, 0, 0);
+  const int nst = WG_VOX / STAGE_K;
+  bool ok = true;
+  for (int s = 0; s < nst && ok; ++s) {
+    const int buf = s % NSTAGE;
+    if (s >= NSTAGE) {
+      bool done = mbar_wait(&mbar[buf], (uint32_t)((s / NSTAGE - 1) & 1));
+      if (!done) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) {
+        ok = false;
+        break;
+      }
+    }
+    uint8_t *a_st = sA + buf * A_STAGE_BYTES;
+    uint8_t *b_st = sB + buf * BST;
+    // A: 16 row groups of 8 (tap, channel) pairs x 64 voxels
+    for (int e = tid; e < 16 * STAGE_K; e += CONV_THREADS) {
+      const int k = e % STAGE_K, r8 = e / STAGE_K;
+      const long v = v0 + (long)s * STAGE_K + k;
+      const int m = m0 + r8 * 8;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (m < rows && v < nvox) {
+        const int t = m / g.cin, ci0 = m - t * g.cin;
+        const int x = (int)(v % g.nx), y = (int)((v / g.nx) % g.ny), z = (int)(v / ((long)g.nx * g.ny));
+        gather8(xa, xb, g, x + t % 3 - 1, y + (t / 3) % 3 - 1, z + t / 9 - 1, ci0, val);
+      }
+      scatter8(a_st, r8, k, val);
+    }
+    // B: COUT/8 row groups x 64 voxels of the output gradient
+    for (int e = tid; e < (COUT / 8) * STAGE_K; e += CONV_THREADS) {
+      const int k = e % STAGE_K, r8 = e / STAGE_K;
+      const long v = v0 + (long)s * STAGE_K + k;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (v < nvox) val = __ldg(reinterpret_cast<const uint4 *>(gr + v * COUT + r8 * 8));
+      const bf16 *ev = reinterpret_cast<const bf16 *>(&val);
+      uint8_t *base = b_st + (k >> 3) * (COUT / 8) * 128 + r8 * 128 + (k & 7) * 2;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) *reinterpret_cast<bf16 *>(base + q * 16) = ev[q];
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(a_st), b0 = smem_u32(b_st);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t da = sdesc(a0 + 2 * q * 2048, 2048, 128);
+        const uint64_t db = sdesc(b0 + 2 * q * (COUT / 8) * 128, (COUT / 8) * 128, 128);
+        mma_bf16(taddr, da, db, IDESC, (s > 0 || q > 0) ? 1u : 0u);
+      }
+      mma_commit(&mbar[buf]);
+    }
+  }
+  if (ok) {
+    const int last = nst - 1;
+    bool done = mbar_wait(&mbar[last % NSTAGE], (uint32_t)((last / NSTAGE) & 1));
+    if (!done) abort_flag = 1;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (abort_flag) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    const int m = m0 + warp * 32 + lane;
+    float *dst = partial + ((size_t)blockIdx.y * rows + m) * COUT;
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      float acc[16];
+      tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + c0, acc);
+      if (m < rows)
+        for (int q = 0; q < 16; ++q) dst[c0 + q] = acc[q];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(taddr, TM);
+}
+
+// dw[co][t][ci] = sum over chunks (fixed order) of partial[chunk][t*cin + ci][co]
+__global__ void k_wgrad_reduce(const float *__restrict__ partial, int chunks, int rows, int cout,
+                               float *__restrict__ dw) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cout) return;
+  const int co = e / rows, row = e - co * rows;
+  float acc = 0.f;
+  for (int c = 0; c < chunks; ++c) acc += partial[((size_t)c * rows + row) * cout + co];
+  dw[(size_t)co * rows + row] = acc;
+}
+
+
+// ------------------------------------------------------------ small kernels
+constexpr int RED_BLOCKS = 1024, RED_THREADS = 256;
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sumd(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// fixed-order block sum (result in thread 0); blockDim.x == RED_THREADS
+__device__ __forceinline__ double block_sumd(double v) {
+  __shared__ double red[RED_THREADS / 32];
+  v = warp_sumd(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < RED_THREADS / 32 ? red[threadIdx.x] : 0.0;
+    s = warp_sumd(s);
+  }
+  return s;
+}
+
+// per-block partial sums of f(i) over a fixed grid; mode 0: x, 1: x^2
+template <typename T>
+__global__ void k_psum(const T *__restrict__ x, size_t n, int mode, double *__restrict__ part) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * RED_THREADS) {
+    double v = (double)x[i];
+    acc += mode ? v * v : v;
+  }
+  double t = block_sumd(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+__global__ void k_pfinal(const double *__restrict__ part, int np, double *__restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += RED_THREADS) acc += part[i];
+  double t = block_sumd(acc);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// network input: channel 0 = clip(phi / (4h), -1, 1), channel 1 = bt / s, rest 0
+__global__ void k_features(const double *__restrict__ phi, const double *__restrict__ bt,
+                           size_t n, double inv4h, double inv_s, bf16 *__restrict__ out) {
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n;
+       v += (size_t)gridDim.x * blockDim.x) {
+    double f0 = phi[v] * inv4h;
+    f0 = f0 > 1.0 ? 1.0 : (f0 < -1.0 ? -1.0 : f0);
+    __align__(16) bf16 h[16];
+    h[0] = __float2bfloat16_rn((float)f0);
+    h[1] = __float2bfloat16_rn((float)(bt[v] * inv_s));
+#pragma unroll
+    for (int q = 2; q < 16; ++q) h[q] = __float2bfloat16_rn(0.f);
+    uint4 *o = reinterpret_cast<uint4 *>(out + v * 16);
+    o[0] = *reinterpret_cast<uint4 *>(&h[0]);
+    o[1] = *reinterpret_cast<uint4 *>(&h[8]);
+  }
+}
+
+// 2x2x2 average pooling (fine nx, ny, nz; C channels)
+__global__ void k_pool2(const bf16 *__restrict__ in, bf16 *__restrict__ out, int nx, int ny, int nz,
+                        int C) {
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const size_t total = (size_t)cx * cy * cz * C;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % C);
+    const size_t vc = e / C;
+    const int X = (int)(vc % cx), Y = (int)((vc / cx) % cy), Z = (int)(vc / ((size_t)cx * cy));
+    float acc = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const int x = 2 * X + (q & 1), y = 2 * Y + ((q >> 1) & 1), z = 2 * Z + (q >> 2);
+      acc += __bfloat162float(in[(((size_t)z * ny + y) * nx + x) * C + c]);
+    }
+    out[e] = __float2bfloat16_rn(acc * 0.125f);
+  }
+}
+
+// 1x1x1 head: q[v] = sum_c d[v][c] w[c] + b
+__global__ void k_head_fwd(const bf16 *__restrict__ d, const float *__restrict__ w,
+                           const float *__restrict__ b, size_t n, int C, float *__restrict__ q) {
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n;
+       v += (size_t)gridDim.x * blockDim.x) {
+    float acc = b[0];
+    for (int c = 0; c < C; ++c) acc = fmaf(__bfloat162float(d[v * C + c]), w[c], acc);
+    q[v] = acc;
+  }
+}
+
+// gradient through ReLU: gz = gy where y > 0
+__global__ void k_relu_mask(const bf16 *__restrict__ gy, const bf16 *__restrict__ y, size_t n,
+                            bf16 *__restrict__ gz) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    gz[e] = __bfloat162float(y[e]) > 0.f ? gy[e] : __float2bfloat16_rn(0.f);
+}
+
+// per-channel partial sums of g (nvox x C) over voxel chunks, fixed order
+__global__ void k_chan_psum(const bf16 *__restrict__ g, size_t nvox, int C, int chunk,
+                            float *__restrict__ part) {
+  const int c = threadIdx.x;  // blockDim.x == C
+  const size_t v0 = (size_t)blockIdx.x * chunk;
+  float acc = 0.f;
+  for (size_t v = v0; v < v0 + chunk && v < nvox; ++v) acc += __bfloat162float(g[v * C + c]);
+  part[(size_t)blockIdx.x * C + c] = acc;
+}
+__global__ void k_chan_final(const float *__restrict__ part, int chunks, int C,
+                             float *__restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float acc = 0.f;
+  for (int k = 0; k < chunks; ++k) acc += part[(size_t)k * C + c];
+  out[c] = acc;
+}
+
+// head backward: gd[v][c] = gq[v] w[c]; partials of gq[v] d[v][c] (dw) and gq (db)
+__global__ void k_head_bwd(const float *__restrict__ gq, const bf16 *__restrict__ d,
+                           const float *__restrict__ w, size_t nvox, int C, int chunk,
+                           bf16 *__restrict__ gd, float *__restrict__ part) {
+  const int c = threadIdx.x;  // blockDim.x == C + 1 (last lane: bias)
+  const size_t v0 = (size_t)blockIdx.x * chunk;
+  float acc = 0.f;
+  for (size_t v = v0; v < v0 + chunk && v < nvox; ++v) {
+    const float g = gq[v];
+    if (c < C) {
+      gd[v * C + c] = __float2bfloat16_rn(g * w[c]);
+      acc = fmaf(g, __bfloat162float(d[v * C + c]), acc);
+    } else {
+      acc += g;
+    }
+  }
+  part[(size_t)blockIdx.x * (C + 1) + c] = acc;
+}
+
+// split the gradient of a concatenated input [up(a) (ca) | b (cb)] at full
+// resolution: the a-part goes back through nearest upsampling (a parent
+// sums its 8 children) into ga (bf16, half resolution); the b-part is
+// stored in FP32 (to be added to the pooling path's contribution)
+__global__ void k_split_up(const bf16 *__restrict__ gx, int nx, int ny, int nz, int ca, int cb,
+                           bf16 *__restrict__ ga, float *__restrict__ gb32) {
+  const int cin = ca + cb;
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const size_t ncoarse = (size_t)cx * cy * cz;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ncoarse * cin;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % cin);
+    const size_t vc = e / cin;
+    const int X = (int)(vc % cx), Y = (int)((vc / cx) % cy), Z = (int)(vc / ((size_t)cx * cy));
+    if (c < ca) {
+      float acc = 0.f;
+      for (int q = 0; q < 8; ++q) {
+        const int x = 2 * X + (q & 1), y = 2 * Y + ((q >> 1) & 1), z = 2 * Z + (q >> 2);
+        acc += __bfloat162float(gx[(((size_t)z * ny + y) * nx + x) * cin + c]);
+      }
+      ga[vc * ca + c] = __float2bfloat16_rn(acc);
+    } else {
+      for (int q = 0; q < 8; ++q) {
+        const int x = 2 * X + (q & 1), y = 2 * Y + ((q >> 1) & 1), z = 2 * Z + (q >> 2);
+        const size_t v = ((size_t)z * ny + y) * nx + x;
+        gb32[v * cb + (c - ca)] = __bfloat162float(gx[v * cin + c]);
+      }
+    }
+  }
+}
+
+// gradient of an encoder output used by both the skip connection (gskip32,
+// full resolution, may be null) and 2x2x2 average pooling (gpool, half
+// resolution): g = gskip + gpool[parent] / 8
+__global__ void k_pool_adjoint_add(const float *__restrict__ gskip32,
+                                   const bf16 *__restrict__ gpool, int nx, int ny, int nz, int C,
+                                   bf16 *__restrict__ g) {
+  const size_t total = (size_t)nx * ny * nz * C;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % C);
+    const size_t v = e / C;
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((size_t)nx * ny));
+    const size_t vp = (((size_t)(z >> 1) * (ny >> 1) + (y >> 1)) * (nx >> 1) + (x >> 1));
+    float acc = 0.125f * __bfloat162float(gpool[vp * C + c]);
+    if (gskip32) acc += gskip32[e];
+    g[e] = __float2bfloat16_rn(acc);
+  }
+}
+
+// gauge-free MSE: e = (q - mean q) - (t - mean t); per-block partial of e^2
+// and gradient gq = 2 e / n; means in mq_mt[0], mq_mt[1]
+__global__ void k_loss(const float *__restrict__ q, const float *__restrict__ t, size_t n,
+                       const double *__restrict__ mq_mt, float *__restrict__ gq,
+                       double *__restrict__ part) {
+  const double mq = mq_mt[0] / n, mt = mq_mt[1] / n;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * RED_THREADS) {
+    const double e = ((double)q[i] - mq) - ((double)t[i] - mt);
+    gq[i] = (float)(2.0 * e / n);
+    acc += e * e;
+  }
+  double s = block_sumd(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Adam, bias-corrected (step >= 1)
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, size_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// BF16 copies of one layer's weights: forward [co][t][ci] and the flipped,
+// transposed set that turns the input gradient into a forward convolution:
+// wd[ci][t][co] = w[co][26 - t][ci]
+__global__ void k_pack(const float *__restrict__ w, int cout, int cin, bf16 *__restrict__ wf,
+                       bf16 *__restrict__ wd) {
+  const int total = cout * 27 * cin;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int ci = e % cin, t = (e / cin) % 27, co = e / (27 * cin);
+    const bf16 b = __float2bfloat16_rn(w[e]);
+    wf[e] = b;
+    if (wd) wd[((size_t)ci * 27 + (26 - t)) * cout + co] = b;
+  }
+}
+
+// training target q = (p - mean) / rms(p - mean): sums of p and p^2 in sums
+__global__ void k_make_target(const double *__restrict__ p, size_t n,
+                              const double *__restrict__ sums, float *__restrict__ q) {
+  const double m = sums[0] / n;
+  const double var = sums[1] / n - m * m;
+  const double inv = var > 0.0 ? 1.0 / sqrt(var) : 1.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    q[i] = (float)((p[i] - m) * inv);
+}
+
+// p0 = scale * (q - mean q) in FP64 (mean from sum_q)
+__global__ void k_to_pressure(const float *__restrict__ q, size_t n, const double *__restrict__ sum_q,
+                              double scale, double *__restrict__ p0) {
+  const double m = *sum_q / n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    p0[i] = scale * ((double)q[i] - m);
+}
+
+}  // namespace mpnet
+
+// =================================================================== host side
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace mpnet;
+
+namespace {
+
+#define NCK(call)                                  \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return MP_ERR_CUDA;     \
+  } while (0)
+#define NCKS(call)                  \
+  do {                              \
+    mp_status s_ = (call);          \
+    if (s_ != MP_OK) return s_;     \
+  } while (0)
+
+constexpr int NLAYER = 14;
+constexpr int CH[4] = {16, 32, 64, 64};
+
+struct Layer {
+  int cout, cin, level;  // level: 0 = finest
+  int ca, cb, up_a;      // input composition
+  size_t woff, boff;     // offsets of weights and bias in the parameter vector
+  bf16 *wf = nullptr, *wd = nullptr;
+  bf16 *y = nullptr;     // output activation
+  bf16 *gy = nullptr;    // gradient w.r.t. the output
+};
+
+}  // namespace
+
+struct mp_net {
+  int nx[4], ny[4], nz[4];
+  size_t nv[4];
+  cudaStream_t st = nullptr;
+  Layer L[NLAYER];
+  size_t nparam = 0, head_w = 0, head_b = 0;
+  float *param = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  bf16 *in16 = nullptr;           // network input (16 channels, level 0)
+  bf16 *pool[3] = {};             // pooled encoder outputs (levels 1..3)
+  float *gskip32[3] = {};         // FP32 skip-path gradients of the encoder outputs, levels 0..2
+  bf16 *gz = nullptr;             // ReLU-masked gradient (largest size)
+  bf16 *gx = nullptr;             // input gradient of a layer (largest size)
+  float *q = nullptr, *gq = nullptr;
+  float *wpart = nullptr;         // weight-gradient split-K partials
+  size_t wpart_n = 0;
+  float *cpart = nullptr;         // per-channel partial sums
+  double *dpart = nullptr, *dscal = nullptr, *hscal = nullptr;
+  int *err = nullptr;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+template <typename T>
+mp_status nalloc(mp_net *net, T **p, size_t count) {
+  void *v = nullptr;
+  if (cudaMalloc(&v, count * sizeof(T) + 64) != cudaSuccess) {
+    cudaGetLastError();
+    return MP_ERR_OOM;
+  }
+  net->allocs.push_back(v);
+  *p = (T *)v;
+  return MP_OK;
+}
+
+bool cout_ok(int c) { return c == 16 || c == 32 || c == 48 || c == 64 || c == 96 || c == 128; }
+
+template <int COUT>
+mp_status launch_fwd(const ConvGeom &g, const bf16 *xa, const bf16 *xb, const bf16 *w,
+                     const float *bias, bf16 *y, float *y32, int relu, int *err, cudaStream_t st) {
+  const int smem = conv_smem_bytes<COUT>();
+  static bool attr = false;
+  if (!attr) {
+    NCK(cudaFuncSetAttribute(k_conv3d_fwd<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  dim3 grid((g.nx + 7) / 8, (g.ny + 3) / 4, (g.nz + 3) / 4);
+  k_conv3d_fwd<COUT><<<grid, CONV_THREADS, smem, st>>>(xa, xb, w, bias, y, y32, g, relu, err);
+  NCK(cudaGetLastError());
+  return MP_OK;
+}
+
+mp_status conv_fwd(const ConvGeom &g, const bf16 *xa, const bf16 *xb, const bf16 *w,
+                   const float *bias, int cout, bf16 *y, float *y32, int relu, int *err,
+                   cudaStream_t st) {
+  switch (cout) {
+    case 16: return launch_fwd<16>(g, xa, xb, w, bias, y, y32, relu, err, st);
+    case 32: return launch_fwd<32>(g, xa, xb, w, bias, y, y32, relu, err, st);
+    case 48: return launch_fwd<48>(g, xa, xb, w, bias, y, y32, relu, err, st);
+    case 64: return launch_fwd<64>(g, xa, xb, w, bias, y, y32, relu, err, st);
+    case 96: return launch_fwd<96>(g, xa, xb, w, bias, y, y32, relu, err, st);
+    case 128: return launch_fwd<128>(g, xa, xb, w, bias, y, y32, relu, err, st);
+  }
+  return MP_ERR_INVALID_ARG;
+}
+
+size_t wgrad_chunks(const ConvGeom &g) {
+  const size_t nv = (size_t)g.nx * g.ny * g.nz;
+  return (nv + WG_VOX - 1) / WG_VOX;
+}
+size_t wgrad_partial_floats(const ConvGeom &g, int cout) {
+  return wgrad_chunks(g) * 27 * (size_t)g.cin * cout;
+}
+
+template <int COUT>
+mp_status launch_wgrad(const ConvGeom &g, const bf16 *xa, const bf16 *xb, const bf16 *gr,
+                       float *part, float *dw, int *err, cudaStream_t st) {
+  const int smem = conv_smem_bytes<COUT>();
+  static bool attr = false;
+  if (!attr) {
+    NCK(cudaFuncSetAttribute(k_conv3d_wgrad<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem));
+    attr = true;
+  }
+  const int rows = 27 * g.cin;
+  const int chunks = (int)wgrad_chunks(g);
+  dim3 grid((rows + 127) / 128, chunks);
+  k_conv3d_wgrad<COUT><<<grid, CONV_THREADS, smem, st>>>(xa, xb, gr, g, part, err);
+  k_wgrad_reduce<<<(rows * COUT + 255) / 256, 256, 0, st>>>(part, chunks, rows, COUT, dw);
+  NCK(cudaGetLastError());
+  return MP_OK;
+}
+
+mp_status conv_wgrad(const ConvGeom &g, const bf16 *xa, const bf16 *xb, const bf16 *gr, int cout,
+                     float *part, float *dw, int *err, cudaStream_t st) {
+  switch (cout) {
+    case 16: return launch_wgrad<16>(g, xa, xb, gr, part, dw, err, st);
+    case 32: return launch_wgrad<32>(g, xa, xb, gr, part, dw, err, st);
+    case 64: return launch_wgrad<64>(g, xa, xb, gr, part, dw, err, st);
+  }
+  return MP_ERR_INVALID_ARG;
+}
+
+mp_status check_err(mp_net *net) {
+  int h = 0;
+  NCK(cudaMemcpyAsync(&h, net->err, sizeof(int), cudaMemcpyDeviceToHost, net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  return h ? MP_ERR_TIMEOUT : MP_OK;
+}
+
+int grid_for(size_t n, int threads = 256) {
+  size_t b = (n + threads - 1) / threads;
+  return (int)std::min<size_t>(b, 152 * 32);
+}
+
+ConvGeom geom(const mp_net *net, const Layer &l) {
+  ConvGeom g;
+  g.nx = net->nx[l.level];
+  g.ny = net->ny[l.level];
+  g.nz = net->nz[l.level];
+  g.ca = l.ca;
+  g.cb = l.cb;
+  g.up_a = l.up_a;
+  g.cin = l.cin;
+  return g;
+}
+
+// inputs (a, b) of layer i
+void layer_inputs(const mp_net *net, int i, const bf16 **a, const bf16 **b) {
+  const Layer *L = net->L;
+  *b = nullptr;
+  switch (i) {
+    case 0: *a = net->in16; break;
+    case 2: *a = net->pool[0]; break;
+    case 4: *a = net->pool[1]; break;
+    case 6: *a = net->pool[2]; break;
+    case 8: *a = L[7].y; *b = L[5].y; break;   // up(e3) | e2
+    case 10: *a = L[9].y; *b = L[3].y; break;  // up(d2) | e1
+    case 12: *a = L[11].y; *b = L[1].y; break; // up(d1) | e0
+    default: *a = L[i - 1].y; break;
+  }
+}
+
+mp_status pack_all(mp_net *net) {
+  for (int i = 0; i < NLAYER; ++i) {
+    Layer &l = net->L[i];
+    k_pack<<<grid_for((size_t)l.cout * 27 * l.cin), 256, 0, net->st>>>(
+        net->param + l.woff, l.cout, l.cin, l.wf, i == 0 ? nullptr : l.wd);
+  }
+  NCK(cudaGetLastError());
+  return MP_OK;
+}
+
+mp_status forward(mp_net *net) {
+  NCK(cudaMemsetAsync(net->err, 0, sizeof(int), net->st));
+  for (int i = 0; i < NLAYER; ++i) {
+    Layer &l = net->L[i];
+    if (i == 2 || i == 4 || i == 6) {  // pool the previous level's encoder output
+      const int lv = l.level - 1;
+      k_pool2<<<grid_for(net->nv[l.level] * l.ca), 256, 0, net->st>>>(
+          net->L[i - 1].y, net->pool[l.level - 1], net->nx[lv], net->ny[lv], net->nz[lv], l.ca);
+    }
+    const bf16 *a, *b;
+    layer_inputs(net, i, &a, &b);
+    NCKS(conv_fwd(geom(net, l), a, b, l.wf, net->param + l.boff, l.cout, l.y, nullptr, 1,
+                  net->err, net->st));
+  }
+  k_head_fwd<<<grid_for(net->nv[0]), 256, 0, net->st>>>(
+      net->L[13].y, net->param + net->head_w, net->param + net->head_b, net->nv[0], CH[0],
+      net->q);
+  NCK(cudaGetLastError());
+  return MP_OK;
+}
+
+// gradients of sum(q * gq) into net->grad (gq in net->gq)
+mp_status backward(mp_net *net) {
+  const size_t n0 = net->nv[0];
+  // head
+  {
+    const int chunk = 4096;
+    const int chunks = (int)((n0 + chunk - 1) / chunk);
+    k_head_bwd<<<chunks, CH[0] + 1, 0, net->st>>>(net->gq, net->L[13].y,
+                                                  net->param + net->head_w, n0, CH[0], chunk,
+                                                  net->L[13].gy, net->cpart);
+    k_chan_final<<<1, 32, 0, net->st>>>(net->cpart, chunks, CH[0] + 1, net->grad + net->head_w);
+  }
+  for (int i = NLAYER - 1; i >= 0; --i) {
+    Layer &l = net->L[i];
+    const ConvGeom g = geom(net, l);
+    const size_t nv = net->nv[l.level];
+    k_relu_mask<<<grid_for(nv * l.cout), 256, 0, net->st>>>(l.gy, l.y, nv * l.cout, net->gz);
+    {
+      const int chunk = 1024;
+      const int chunks = (int)((nv + chunk - 1) / chunk);
+      k_chan_psum<<<chunks, l.cout, 0, net->st>>>(net->gz, nv, l.cout, chunk, net->cpart);
+      k_chan_final<<<1, 128, 0, net->st>>>(net->cpart, chunks, l.cout, net->grad + l.boff);
+    }
+    const bf16 *a, *b;
+    layer_inputs(net, i, &a, &b);
+    NCKS(conv_wgrad(g, a, b, net->gz, l.cout, net->wpart, net->grad + l.woff, net->err,
+                    net->st));
+    if (i == 0) break;
+    // input gradient: forward convolution of gz with the flipped, transposed weights
+    ConvGeom gd = g;
+    gd.ca = l.cout;
+    gd.cb = 0;
+    gd.up_a = 0;
+    gd.cin = l.cout;
+    const bool plain = !(i == 2 || i == 4 || i == 6 || i == 8 || i == 10 || i == 12);
+    bf16 *dst = plain ? net->L[i - 1].gy : net->gx;
+    NCKS(conv_fwd(gd, net->gz, nullptr, l.wd, nullptr, l.cin, dst, nullptr, 0, net->err,
+                  net->st));
+    const int lv = l.level;
+    if (i == 12 || i == 10 || i == 8) {  // decoder input: [up(coarse) | skip]
+      const int coarse = i == 12 ? 11 : (i == 10 ? 9 : 7);
+      k_split_up<<<grid_for(net->nv[lv + 1] * l.cin), 256, 0, net->st>>>(
+          net->gx, net->nx[lv], net->ny[lv], net->nz[lv], l.ca, l.cb, net->L[coarse].gy,
+          net->gskip32[lv]);
+    } else if (i == 6 || i == 4 || i == 2) {  // encoder input = pooled finer output
+      const int fine = i - 1, flv = lv - 1;
+      k_pool_adjoint_add<<<grid_for(net->nv[flv] * l.cin), 256, 0, net->st>>>(
+          net->gskip32[flv], net->gx, net->nx[flv], net->ny[flv], net->nz[flv], l.cin,
+          net->L[fine].gy);
+    }
+  }
+  NCK(cudaGetLastError());
+  return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mp_status mp_conv3d_fwd(int nx, int ny, int nz, const void *xa, int ca, int up_a, const void *xb,
+                        int cb, const void *w, const float *bias, int cout, int relu, void *y,
+                        float *y32, void *stream) {
+  if (nx <= 0 || ny <= 0 || nz <= 0 || nx % 8 || ny % 4 || nz % 4 || !xa || ca <= 0 || ca % 16 ||
+      cb < 0 || cb % 16 || (cb > 0 && !xb) || !w || !cout_ok(cout) || (!y && !y32) ||
+      (up_a && (nx % 2 || ny % 2 || nz % 2)))
+    return MP_ERR_INVALID_ARG;
+  int *err = nullptr;
+  NCK(cudaMallocAsync((void **)&err, sizeof(int), (cudaStream_t)stream));
+  NCK(cudaMemsetAsync(err, 0, sizeof(int), (cudaStream_t)stream));
+  ConvGeom g{nx, ny, nz, ca, cb, up_a ? 1 : 0, ca + cb};
+  mp_status s = conv_fwd(g, (const bf16 *)xa, (const bf16 *)xb, (const bf16 *)w, bias, cout,
+                         (bf16 *)y, y32, relu, err, (cudaStream_t)stream);
+  int h = 0;
+  if (s == MP_OK) {
+    NCK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  }
+  NCK(cudaFreeAsync(err, (cudaStream_t)stream));
+  NCK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (s != MP_OK) return s;
+  return h ? MP_ERR_TIMEOUT : MP_OK;
+}
+
+mp_status mp_conv3d_wgrad(int nx, int ny, int nz, const void *xa, int ca, int up_a,
+                          const void *xb, int cb, const void *g, int cout, float *dw,
+                          void *stream) {
+  if (nx <= 0 || ny <= 0 || nz <= 0 || !xa || ca <= 0 || ca % 16 || cb < 0 || cb % 16 ||
+      (cb > 0 && !xb) || !g || !dw || !(cout == 16 || cout == 32 || cout == 64) ||
+      (up_a && (nx % 2 || ny % 2 || nz % 2)))
+    return MP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ConvGeom geo{nx, ny, nz, ca, cb, up_a ? 1 : 0, ca + cb};
+  int *err = nullptr;
+  float *part = nullptr;
+  NCK(cudaMallocAsync((void **)&err, sizeof(int), st));
+  NCK(cudaMallocAsync((void **)&part, wgrad_partial_floats(geo, cout) * sizeof(float), st));
+  NCK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  mp_status s = conv_wgrad(geo, (const bf16 *)xa, (const bf16 *)xb, (const bf16 *)g, cout, part,
+                           dw, err, st);
+  int h = 0;
+  if (s == MP_OK) NCK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NCK(cudaFreeAsync(part, st));
+  NCK(cudaFreeAsync(err, st));
+  NCK(cudaStreamSynchronize(st));
+  if (s != MP_OK) return s;
+  return h ? MP_ERR_TIMEOUT : MP_OK;
+}
+
+mp_status mp_net_create(mp_net_handle *out, int nx, int ny, int nz, void *stream) {
+  if (!out || nx <= 0 || ny <= 0 || nz <= 0 || nx % 32 || ny % 32 || nz % 32)
+    return MP_ERR_INVALID_ARG;
+  *out = nullptr;
+  mp_net *net = new (std::nothrow) mp_net();
+  if (!net) return MP_ERR_OOM;
+  net->st = (cudaStream_t)stream;
+  for (int l = 0; l < 4; ++l) {
+    net->nx[l] = nx >> l;
+    net->ny[l] = ny >> l;
+    net->nz[l] = nz >> l;
+    net->nv[l] = (size_t)net->nx[l] * net->ny[l] * net->nz[l];
+  }
+  // layers in forward order: (cout, cin, level, ca, cb, up_a)
+  const int spec[NLAYER][6] = {
+      {CH[0], 16, 0, 16, 0, 0},          {CH[0], CH[0], 0, CH[0], 0, 0},
+      {CH[1], CH[0], 1, CH[0], 0, 0},    {CH[1], CH[1], 1, CH[1], 0, 0},
+      {CH[2], CH[1], 2, CH[1], 0, 0},    {CH[2], CH[2], 2, CH[2], 0, 0},
+      {CH[3], CH[2], 3, CH[2], 0, 0},    {CH[3], CH[3], 3, CH[3], 0, 0},
+      {CH[2], CH[3] + CH[2], 2, CH[3], CH[2], 1}, {CH[2], CH[2], 2, CH[2], 0, 0},
+      {CH[1], CH[2] + CH[1], 1, CH[2], CH[1], 1}, {CH[1], CH[1], 1, CH[1], 0, 0},
+      {CH[0], CH[1] + CH[0], 0, CH[1], CH[0], 1}, {CH[0], CH[0], 0, CH[0], 0, 0}};
+  size_t off = 0, wpart = 0, maxact = 0;
+  mp_status s = MP_OK;
+  for (int i = 0; i < NLAYER && s == MP_OK; ++i) {
+    Layer &l = net->L[i];
+    l.cout = spec[i][0];
+    l.cin = spec[i][1];
+    l.level = spec[i][2];
+    l.ca = spec[i][3];
+    l.cb = spec[i][4];
+    l.up_a = spec[i][5];
+    l.woff = off;
+    off += (size_t)l.cout * 27 * l.cin;
+    l.boff = off;
+    off += l.cout;
+    const size_t nv = net->nv[l.level];
+    wpart = std::max(wpart, wgrad_partial_floats(geom(net, l), l.cout));
+    maxact = std::max(maxact, nv * (size_t)std::max(l.cin, l.cout));
+    if ((s = nalloc(net, &l.wf, (size_t)l.cout * 27 * l.cin)) != MP_OK) break;
+    if ((s = nalloc(net, &l.wd, (size_t)l.cout * 27 * l.cin)) != MP_OK) break;
+    if ((s = nalloc(net, &l.y, nv * l.cout)) != MP_OK) break;
+    s = nalloc(net, &l.gy, nv * l.cout);
+  }
+  net->head_w = off;
+  off += CH[0];
+  net->head_b = off;
+  off += 1;
+  net->nparam = off;
+  net->wpart_n = wpart;
+  if (s == MP_OK) s = nalloc(net, &net->param, off);
+  if (s == MP_OK) s = nalloc(net, &net->grad, off);
+  if (s == MP_OK) s = nalloc(net, &net->adam_m, off);
+  if (s == MP_OK) s = nalloc(net, &net->adam_v, off);
+  if (s == MP_OK) s = nalloc(net, &net->in16, net->nv[0] * 16);
+  for (int l = 0; l < 3 && s == MP_OK; ++l) s = nalloc(net, &net->pool[l], net->nv[l + 1] * CH[l]);
+  for (int l = 0; l < 3 && s == MP_OK; ++l) s = nalloc(net, &net->gskip32[l], net->nv[l] * CH[l]);
+  if (s == MP_OK) s = nalloc(net, &net->gz, maxact);
+  if (s == MP_OK) s = nalloc(net, &net->gx, maxact);
+  if (s == MP_OK) s = nalloc(net, &net->q, net->nv[0]);
+  if (s == MP_OK) s = nalloc(net, &net->gq, net->nv[0]);
+  if (s == MP_OK) s = nalloc(net, &net->wpart, wpart);
+  if (s == MP_OK) s = nalloc(net, &net->cpart, (net->nv[0] / 1024 + 64) * 130);
+  if (s == MP_OK) s = nalloc(net, &net->dpart, RED_BLOCKS + 8);
+  if (s == MP_OK) s = nalloc(net, &net->dscal, 8);
+  if (s == MP_OK) s = nalloc(net, &net->err, 4);
+  if (s == MP_OK && cudaMallocHost((void **)&net->hscal, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    net->hscal = nullptr;
+    s = MP_ERR_OOM;
+  }
+  if (s == MP_OK) {
+    if (cudaMemsetAsync(net->param, 0, off * sizeof(float), net->st) != cudaSuccess ||
+        cudaMemsetAsync(net->adam_m, 0, off * sizeof(float), net->st) != cudaSuccess ||
+        cudaMemsetAsync(net->adam_v, 0, off * sizeof(float), net->st) != cudaSuccess ||
+        cudaMemsetAsync(net->in16, 0, net->nv[0] * 16 * sizeof(bf16), net->st) != cudaSuccess)
+      s = MP_ERR_CUDA;
+  }
+  if (s == MP_OK) s = pack_all(net);
+  if (s == MP_OK && cudaStreamSynchronize(net->st) != cudaSuccess) s = MP_ERR_CUDA;
+  if (s != MP_OK) {
+    mp_net_destroy(net);
+    return s;
+  }
+  *out = net;
+  return MP_OK;
+}
+
+size_t mp_net_param_count(mp_net_handle net) { return net ? net->nparam : 0; }
+
+mp_status mp_net_dims(mp_net_handle net, int *nx, int *ny, int *nz) {
+  if (!net) return MP_ERR_INVALID_ARG;
+  if (nx) *nx = net->nx[0];
+  if (ny) *ny = net->ny[0];
+  if (nz) *nz = net->nz[0];
+  return MP_OK;
+}
+
+mp_status mp_net_set_params(mp_net_handle net, const float *p) {
+  if (!net || !p) return MP_ERR_INVALID_ARG;
+  NCK(cudaMemcpyAsync(net->param, p, net->nparam * sizeof(float), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCK(cudaMemsetAsync(net->adam_m, 0, net->nparam * sizeof(float), net->st));
+  NCK(cudaMemsetAsync(net->adam_v, 0, net->nparam * sizeof(float), net->st));
+  NCKS(pack_all(net));
+  NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_get_params(mp_net_handle net, float *p) {
+  if (!net || !p) return MP_ERR_INVALID_ARG;
+  NCK(cudaMemcpyAsync(p, net->param, net->nparam * sizeof(float), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_set_stream(mp_net_handle net, void *stream) {
+  if (!net) return MP_ERR_INVALID_ARG;
+  net->st = (cudaStream_t)stream;
+  return MP_OK;
+}
+
+mp_status mp_net_set_input(mp_net_handle net, const void *x16) {
+  if (!net || !x16) return MP_ERR_INVALID_ARG;
+  // (a full 16-channel input: channels 2..15 are whatever the caller passes)
+  NCK(cudaMemcpyAsync(net->in16, x16, net->nv[0] * 16 * sizeof(bf16), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_features(mp_net_handle net, const double *phi, const double *b, double h,
+                          double b_scale, double *s_out) {
+  if (!net || !phi || !b || !(h > 0.0) || !(b_scale > 0.0)) return MP_ERR_INVALID_ARG;
+  const size_t n = net->nv[0];
+  k_psum<double><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(b, n, 1, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
+  NCK(cudaMemcpyAsync(net->hscal, net->dscal, sizeof(double), cudaMemcpyDeviceToHost, net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  double rb = std::sqrt(net->hscal[0] / (double)n);  // rms(b); f1 = b / rms(b) = bt / s
+  if (!(rb > 0.0) || !std::isfinite(rb)) rb = 1.0;
+  k_features<<<grid_for(n), 256, 0, net->st>>>(phi, b, n, 0.25 / h, 1.0 / rb, net->in16);
+  NCK(cudaGetLastError());
+  NCK(cudaStreamSynchronize(net->st));
+  if (s_out) *s_out = b_scale * rb;
+  return MP_OK;
+}
+
+mp_status mp_net_get_input2(mp_net_handle net, void *x2) {
+  if (!net || !x2) return MP_ERR_INVALID_ARG;
+  NCK(cudaMemcpy2DAsync(x2, 2 * sizeof(bf16), net->in16, 16 * sizeof(bf16), 2 * sizeof(bf16),
+                        net->nv[0], cudaMemcpyDeviceToDevice, net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_set_input2(mp_net_handle net, const void *x2) {
+  if (!net || !x2) return MP_ERR_INVALID_ARG;
+  // the other 14 channels stay zero (set at creation, never written)
+  NCK(cudaMemcpy2DAsync(net->in16, 16 * sizeof(bf16), x2, 2 * sizeof(bf16), 2 * sizeof(bf16),
+                        net->nv[0], cudaMemcpyDeviceToDevice, net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_forward(mp_net_handle net, float *q_dev) {
+  if (!net) return MP_ERR_INVALID_ARG;
+  NCKS(forward(net));
+  if (q_dev)
+    NCK(cudaMemcpyAsync(q_dev, net->q, net->nv[0] * sizeof(float), cudaMemcpyDeviceToDevice,
+                        net->st));
+  return check_err(net);
+}
+
+mp_status mp_net_pressure(mp_net_handle net, double s, double *p_dev) {
+  if (!net || !p_dev) return MP_ERR_INVALID_ARG;
+  const size_t n = net->nv[0];
+  k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, n, 0, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
+  k_to_pressure<<<grid_for(n), 256, 0, net->st>>>(net->q, n, net->dscal, s, p_dev);
+  NCK(cudaGetLastError());
+  NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_make_target(mp_net_handle net, const double *p, float *q) {
+  if (!net || !p || !q) return MP_ERR_INVALID_ARG;
+  const size_t n = net->nv[0];
+  k_psum<double><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(p, n, 0, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 4);
+  k_psum<double><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(p, n, 1, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 5);
+  k_make_target<<<grid_for(n), 256, 0, net->st>>>(p, n, net->dscal + 4, q);
+  NCK(cudaGetLastError());
+  NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_backward(mp_net_handle net, const float *gq, float *grad_dev) {
+  if (!net || !gq) return MP_ERR_INVALID_ARG;
+  NCKS(forward(net));
+  NCK(cudaMemcpyAsync(net->gq, gq, net->nv[0] * sizeof(float), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCKS(backward(net));
+  if (grad_dev)
+    NCK(cudaMemcpyAsync(grad_dev, net->grad, net->nparam * sizeof(float),
+                        cudaMemcpyDeviceToDevice, net->st));
+  return check_err(net);
+}
+
+mp_status mp_net_train_step(mp_net_handle net, const float *target, float lr, int step,
+                            double *loss_out) {
+  if (!net || !target || step < 1 || !(lr > 0.f)) return MP_ERR_INVALID_ARG;
+  const size_t n = net->nv[0];
+  NCKS(forward(net));
+  // means of prediction and target, then loss and its gradient
+  k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, n, 0, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
+  k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(target, n, 0, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 1);
+  k_loss<<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, target, n, net->dscal, net->gq,
+                                                 net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 2);
+  NCKS(backward(net));
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);
+  k_adam<<<grid_for(net->nparam), 256, 0, net->st>>>(net->param, net->grad, net->adam_m,
+                                                     net->adam_v, net->nparam, lr, b1, b2, 1e-8f,
+                                                     c1, c2);
+  NCKS(pack_all(net));
+  NCK(cudaMemcpyAsync(net->hscal, net->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                      net->st));
+  NCKS(check_err(net));
+  if (loss_out) *loss_out = net->hscal[0] / (double)n;
+  return MP_OK;
+}
+
+void mp_net_destroy(mp_net_handle net) {
+  if (!net) return;
+  cudaStreamSynchronize(net->st);
+  for (void *p : net->allocs) cudaFree(p);
+  if (net->hscal) cudaFreeHost(net->hscal);
+  delete net;
+}
+
+}  // extern "C"

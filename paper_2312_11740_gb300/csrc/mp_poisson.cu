@@ -16,6 +16,7 @@
 #include <new>
 #include <vector>
 
+#include "../../include/mp_net.h"
 #include "../../include/mp_poisson.h"
 #include "mp_kernels.cuh"
 
@@ -34,19 +35,18 @@ struct Level {
   float *bx32 = nullptr, *by32 = nullptr, *bz32 = nullptr, *diag32 = nullptr, *idiag32 = nullptr;
   double *b = nullptr, *e = nullptr;   // coarse-level rhs / correction (levels >= 1)
   float *b32 = nullptr, *e32 = nullptr;
-  float *t32 = nullptr;                // FP32 ping-pong partner of the level's iterate
 };
 
 enum KernelId {
   K_CURV, K_FACES, K_JUMP, K_DIAG, K_COARSEN, K_DENSE, K_GJ,
-  K_RBGS64, K_RBGS32, K_RBGSF32, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
+  K_RBGS64, K_RBGS32, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
   K_APPLY64, K_APPLY32, K_RESID64, K_RESID32, K_RESIDMIX, K_DOT64, K_DOT32, K_AXPY64, K_AXPY32,
   K_XPBY64, K_XPBY32, K_ADD64, K_ADD32, K_ADDF32, K_SUM, K_SUBMEAN, K_REDUCE, K_ASSEMBLE,
   K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_COUNT
 };
 const char *const kKernelNames[K_COUNT] = {
   "curvature", "gfm_faces", "jump", "diag", "coarsen_faces", "dense_build", "gauss_jordan",
-  "rbgs_f64", "rbgs_f32", "rbgs_fused_f32", "coarse_tail_f64", "coarse_tail_f32",
+  "rbgs_f64", "rbgs_f32", "coarse_tail_f64", "coarse_tail_f32",
   "resid_restrict_f64", "resid_restrict_f32", "prolong_f64",
   "prolong_f32", "coarse_solve_f64", "coarse_solve_f32io", "apply_dot_f64", "apply_dot_f32",
   "residual_f64", "residual_f32", "residual_mixed", "dot_f64", "dot_f32", "axpy2_f64",
@@ -90,6 +90,7 @@ struct mp_poisson {
   int npart = 0;
   double bnorm = 0.0;
   mp_stats stats{};
+  mp_net_handle net = nullptr;  // learned initial guess (initial_guess = 2)
   std::vector<void *> allocs;
   // launch accounting / CUDA-event profiling
   ProfEntry prof[K_COUNT][MAX_LEVELS];
@@ -150,14 +151,6 @@ dim3 zgrid(const Dims &d) {
 int zblocks(const Dims &d) {
   dim3 g = zgrid(d);
   return (int)(g.x * g.y * g.z);
-}
-// fused-sweep tiles: large tiles (fewer ring cells) on large levels, small
-// tiles (enough CTAs) on mid-size levels
-constexpr int FBX = 32, FBY = 16, FBZ = 8, FSX = 16, FSY = 8, FSZ = 4;
-bool big_tile(const Dims &d) { return (size_t)d.nx * d.ny * d.nz >= ((size_t)1 << 20); }
-dim3 fused_grid(const Dims &d) {
-  if (big_tile(d)) return dim3((d.nx + FBX - 1) / FBX, (d.ny + FBY - 1) / FBY, (d.nz + FBZ - 1) / FBZ);
-  return dim3((d.nx + FSX - 1) / FSX, (d.ny + FSY - 1) / FSY, (d.nz + FSZ - 1) / FSZ);
 }
 // dynamic shared memory of the one-CTA coarse tail: FP32 levels up to ~16^3;
 // FP64 only the smallest levels (one SM's FP64 rate is the limit there)
@@ -272,10 +265,9 @@ template <> struct LV<float> {
 
 // One symmetric V-cycle with zero initial guess: x ~= At^-1 rhs on level l.
 // Pre-smoothing sweeps red then black, post-smoothing black then red (the
-// adjoint), so the cycle is a symmetric preconditioner.  FP32 levels use the
-// fused out-of-place sweep, alternating between x and the level's t32 so the
-// last sweep lands in x; FP64 levels use in-place per-colour sweeps (fewest
-// FP64 operations: FP64 is ALU-bound on this part).
+// adjoint), so the cycle is a symmetric preconditioner.  Each colour is one
+// in-place launch (a colour reads only the other colour).  The levels at
+// the bottom run inside one CTA (k_tail).
 template <typename T>
 mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
   Level &lv = hd->L[l];
@@ -307,66 +299,31 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
   T *bx = LV<T>::bx(lv), *by = LV<T>::by(lv), *bz = LV<T>::bz(lv);
   T *diag = LV<T>::diag(lv), *idiag = LV<T>::idiag(lv);
   const double sz = sizeof(T), nl = (double)lv.n;
-  T *cur = x;
-  if constexpr (sizeof(T) == 4) {
-    const int S = lv.nu1 + lv.nu2;
-    float *A = (S & 1) ? x : lv.t32;
-    float *B = (A == x) ? lv.t32 : x;
-    const dim3 fg = fused_grid(lv.d);
-    cur = nullptr;
-    const bool big = big_tile(lv.d);
-    auto kbig = k_rbgs_fused<FBX, FBY, FBZ>;
-    auto ksmall = k_rbgs_fused<FSX, FSY, FSZ>;
-    for (int s = 0; s < lv.nu1; ++s) {
-      float *dst = (cur == A) ? B : A;
-      if (big)
-        LAUNCH(hd, K_RBGSF32, l, (s == 0 ? 20.0 : 24.0) * nl, kbig, fg,
-               FUSED_THREADS, s == 0 ? dst : cur, dst, rhs, bx, by, bz, lv.d, s == 0, 0);
-      else
-        LAUNCH(hd, K_RBGSF32, l, (s == 0 ? 20.0 : 24.0) * nl, ksmall, fg,
-               FUSED_THREADS, s == 0 ? dst : cur, dst, rhs, bx, by, bz, lv.d, s == 0, 0);
-      cur = dst;
-    }
-    LAUNCH(hd, K_RESTR32, l, 6.125 * nl * sz, k_resid_restrict<float>, cell_grid(lc.d), kBlock,
-           cur, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
-    CKS(launch_ok());
-    CKS(vcycle<T>(hd, l + 1, LV<T>::b(lc), LV<T>::e(lc)));
-    LAUNCH(hd, K_PROL32, l, 2.125 * nl * sz, k_prolong<float>, cell_grid(lv.d), kBlock, cur,
-           LV<T>::e(lc), lv.d, lc.d);
-    for (int s = 0; s < lv.nu2; ++s) {
-      float *dst = (cur == A) ? B : A;
-      if (big)
-        LAUNCH(hd, K_RBGSF32, l, 24.0 * nl, kbig, fg, FUSED_THREADS, cur,
-               dst, rhs, bx, by, bz, lv.d, 0, 1);
-      else
-        LAUNCH(hd, K_RBGSF32, l, 24.0 * nl, ksmall, fg, FUSED_THREADS, cur,
-               dst, rhs, bx, by, bz, lv.d, 0, 1);
-      cur = dst;
-    }
-    (void)idiag;
-  } else {
+  {
     dim3 hg = half_grid(lv.d);
-    const int krb = K_RBGS64;
+    const int krb = kid<T>(K_RBGS64, K_RBGS32);
+    // FP32 forms 1/diag from the faces (no idiag read); FP64 reads the
+    // stored 1/diag (FP64 division is costly on this part)
+    const double per = sizeof(T) == 8 ? 5.0 : 4.5;
     for (int s = 0; s < lv.nu1; ++s) {
-      LAUNCH(hd, krb, l, (s == 0 ? 4.5 : 5.0) * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by,
-             bz, idiag, lv.d, 0, s == 0);
-      LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1,
+      LAUNCH(hd, krb, l, (s == 0 ? per - 0.5 : per) * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx,
+             by, bz, idiag, lv.d, 0, s == 0);
+      LAUNCH(hd, krb, l, per * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1,
              0);
     }
-    LAUNCH(hd, K_RESTR64, l, 6.125 * nl * sz, k_resid_restrict<T>, cell_grid(lc.d), kBlock, x,
-           rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
+    LAUNCH(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
+           cell_grid(lc.d), kBlock, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
     CKS(launch_ok());
     CKS(vcycle<T>(hd, l + 1, LV<T>::b(lc), LV<T>::e(lc)));
-    LAUNCH(hd, K_PROL64, l, 2.125 * nl * sz, k_prolong<T>, cell_grid(lv.d), kBlock, x,
-           LV<T>::e(lc), lv.d, lc.d);
+    LAUNCH(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong<T>, cell_grid(lv.d),
+           kBlock, x, LV<T>::e(lc), lv.d, lc.d);
     for (int s = 0; s < lv.nu2; ++s) {
-      LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1,
+      LAUNCH(hd, krb, l, per * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1,
              0);
-      LAUNCH(hd, krb, l, 5.0 * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 0,
+      LAUNCH(hd, krb, l, per * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 0,
              0);
     }
   }
-  (void)cur;
   return launch_ok();
 }
 
@@ -537,7 +494,7 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
   hd->stats = mp_stats{};
   hd->stats.levels = (int)hd->L.size();
   hd->stats.coarse_n = hd->nc;
-  if (o.initial_guess == 2) return MP_ERR_NO_NET;
+  if (o.initial_guess == 2 && !hd->net) return MP_ERR_NO_NET;
   int zero = o.initial_guess == 0;
   if (zero) CK(cudaMemsetAsync(p, 0, hd->n * sizeof(double), hd->st));
   if (hd->bnorm == 0.0) {
@@ -545,6 +502,40 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     CK(cudaStreamSynchronize(hd->st));
     if (hist) hist->push_back(0.0);
     return MP_OK;
+  }
+  if (o.initial_guess == 2) {
+    // learned guess: features from phi and the assembled rhs, network,
+    // p0 = s c (q - mean q); kept only if its FP64 residual is below ||b||
+    // the network gives the shape q; its scale is the energy-optimal
+    // alpha = (q . bt) / (q . At q) (minimises the A-norm error of alpha q)
+    double s = 1.0;
+    CK(cudaStreamSynchronize(hd->st));
+    CKS(mp_net_set_stream(hd->net, hd->st));
+    CKS(mp_net_features(hd->net, hd->phi, hd->b, hd->h, 1.0, &s));
+    CKS(mp_net_forward(hd->net, nullptr));
+    CKS(mp_net_pressure(hd->net, 1.0, p));
+    LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, p, hd->q,
+           l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial);
+    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_TMP));
+    LAUNCH(hd, K_DOT64, 0, hd->n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, p, hd->b, hd->n,
+           hd->partial);
+    CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RZ));
+    CKS(read_scalars(hd));
+    double alpha = hd->scal_h[S_RZ] / hd->scal_h[S_TMP];
+    if (!std::isfinite(alpha)) alpha = 0.0;
+    LAUNCH(hd, K_SCALE, 0, hd->n * 16.0, k_scale, VEC_BLOCKS, VEC_THREADS, p, p, hd->n, alpha);
+    LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b,
+           hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
+    CKS(read_scalars(hd));
+    const double rnet = std::sqrt(hd->scal_h[S_RR]);
+    hd->stats.net_relres = rnet / hd->bnorm;
+    if (rnet < hd->bnorm) {
+      hd->stats.used_net = 1;
+    } else {
+      CK(cudaMemsetAsync(p, 0, hd->n * sizeof(double), hd->st));
+      zero = 1;
+    }
   }
   double inv_b = 1.0 / hd->bnorm;
   double tol_abs = tol * hd->bnorm;
@@ -722,7 +713,6 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
     CKS(dalloc(hd, &lv.bz32, lv.n));
     CKS(dalloc(hd, &lv.diag32, lv.n));
     CKS(dalloc(hd, &lv.idiag32, lv.n));
-    CKS(dalloc(hd, &lv.t32, lv.n));
     if (l > 0) {
       CKS(dalloc(hd, &lv.b, lv.n));
       CKS(dalloc(hd, &lv.e, lv.n));
@@ -1013,6 +1003,17 @@ mp_status mp_poisson_get_profile(mp_handle hd, mp_kernel_prof *out, int cap, int
       ++m;
     }
   if (count) *count = m;
+  return MP_OK;
+}
+
+mp_status mp_poisson_set_net(mp_handle hd, mp_net_handle net) {
+  if (!hd) return MP_ERR_INVALID_ARG;
+  if (net) {
+    int nx = 0, ny = 0, nz = 0;
+    CKS(mp_net_dims(net, &nx, &ny, &nz));
+    if (nx != hd->g.nx || ny != hd->g.ny || nz != hd->g.nz) return MP_ERR_INVALID_ARG;
+  }
+  hd->net = net;
   return MP_OK;
 }
 

@@ -1,0 +1,215 @@
+"""Training and evaluation of the learned initial guess (the warm start).
+
+Data: seeded bubble configurations (1-16 gas bubbles, radii 0.03-0.12,
+density ratio 1000, sigma 0.07, periodic x,y / wall z) with seeded smooth
+u*; each sample's pressure comes from the plain FP64 multigrid solve to
+relative residual 1e-10.  Stored on the GPU: the network's two input
+channels (BF16) and the target q = p / rms(p) (FP32, mean-free): the
+network learns the shape, the solver fits the scale.
+
+Training: Adam on the gauge-free MSE, one sample per step, every forward
+and backward operation in the library's tcgen05 kernels.
+
+Evaluation on held-out seeds: the number of solver iterations to 1e-10 from
+the zero guess and from the learned guess (with its residual check and
+zero-guess fallback), hence the iterations saved and the fallback rate.
+
+    python -m paper_2312_11740_gb300.learn --n 128 --train 2000 --epochs 3 \\
+        --eval 200 --out net128.npz
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+from . import Net, Poisson, mp_poisson_set_net
+from .poisson import NEUMANN, PERIODIC
+
+RHO_L, RHO_G, SIGMA = 1.0, 1e-3, 0.07
+BC = (PERIODIC, PERIODIC, NEUMANN)
+
+
+def _synth():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import synth
+    return synth
+
+
+def geometry(seed, n, device):
+    """Seeded 1-16 bubbles, radii U[0.03, 0.12]: (phi, u*) on the device."""
+    synth = _synth()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    count = int(rng.integers(1, 17))
+    bubbles = synth.random_bubbles(seed, count, 0.03, 0.12, n)
+    h = 1.0 / n
+    phi = synth.level_set((n, n, n), h, bubbles, device=device)
+    u = synth.velocity(seed, (n, n, n), h, device=device)
+    return phi, u, bubbles
+
+
+def make_dataset(seeds, n, stream=None, log=print):
+    """Solve each seeded problem with the plain FP64 solver; returns the
+    network inputs (BF16, (count, n, n, n, 2)), targets (FP32) and solver
+    iteration counts."""
+    dev = torch.device("cuda")
+    h = 1.0 / n
+    count = len(seeds)
+    X = torch.empty((count, n, n, n, 2), dtype=torch.bfloat16, device=dev)
+    Q = torch.empty((count, n, n, n), dtype=torch.float32, device=dev)
+    its = []
+    net = Net(n, n, n, stream=stream)
+    solver = None
+    t0 = time.time()
+    for k, seed in enumerate(seeds):
+        phi, u, _ = geometry(seed, n, dev)
+        if solver is None:
+            solver = Poisson(phi, h, BC, RHO_L, RHO_G, SIGMA, precision=0, stream=stream)
+        else:
+            solver.set_geometry(phi, RHO_L, RHO_G, SIGMA)
+        rhs = solver.divergence(*u)
+        p, it, _ = solver.solve(rhs, tol=1e-10)
+        b = solver.rhs(rhs)
+        net.features(phi, b, h, h * h)
+        X[k] = net.get_input2()
+        Q[k] = net.make_target(p)
+        its.append(it)
+        if log and (k + 1) % max(1, count // 10) == 0:
+            log("  data %d/%d  %.1fs" % (k + 1, count, time.time() - t0))
+    net.close()
+    solver.close()
+    return X, Q, its
+
+
+def init_params(net, seed):
+    """He-normal weights, small biases, drawn on the host (PCG64(seed))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shapes = [(16, 16, 2), (16, 16, 16), (32, 16, 16), (32, 32, 32), (64, 32, 32), (64, 64, 64),
+              (64, 64, 64), (64, 64, 64), (64, 128, 128), (64, 64, 64), (32, 96, 96),
+              (32, 32, 32), (16, 48, 48), (16, 16, 16)]
+    parts = []
+    for cout, cin, fan in shapes:
+        parts.append(rng.standard_normal(cout * 27 * cin) * np.sqrt(2.0 / (27 * fan)))
+        parts.append(np.zeros(cout))
+    parts.append(rng.standard_normal(16) * 0.25)
+    parts.append(np.zeros(1))
+    vec = np.concatenate(parts).astype(np.float32)
+    assert vec.size == net.param_count(), (vec.size, net.param_count())
+    return torch.from_numpy(vec).cuda()
+
+
+def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None):
+    """Adam over shuffled samples; returns the loss history (one per step)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    count = X.shape[0]
+    losses = []
+    step = 0
+    total = epochs * count
+    t0 = time.time()
+    for ep in range(epochs):
+        order = rng.permutation(count)
+        for k in order:
+            step += 1
+            cur = lr if lr_final is None else lr * (lr_final / lr) ** (step / total)
+            net.set_input2(X[k])
+            losses.append(net.train_step(Q[k], cur, step))
+        if log:
+            log("  epoch %d  mean loss %.4e  %.1fs" % (ep + 1, float(np.mean(losses[-count:])),
+                                                       time.time() - t0))
+    return losses
+
+
+def evaluate(net, seeds, n, precision=0, stream=None, log=print):
+    """Iterations to 1e-10 from the zero guess and from the learned guess,
+    and the learned guess's relative error against the converged pressure."""
+    dev = torch.device("cuda")
+    h = 1.0 / n
+    rows = []
+    solver = None
+    for seed in seeds:
+        phi, u, _ = geometry(seed, n, dev)
+        if solver is None:
+            solver = Poisson(phi, h, BC, RHO_L, RHO_G, SIGMA, precision=precision, stream=stream)
+            mp_poisson_set_net(solver.handle, net)
+        else:
+            solver.set_geometry(phi, RHO_L, RHO_G, SIGMA)
+        rhs = solver.divergence(*u)
+        solver.set_opts(initial_guess=0)
+        p0, it0, _ = solver.solve(rhs, tol=1e-10)
+        solver.set_opts(initial_guess=2, max_iters=0)
+        pg, _, _ = solver.solve(rhs, tol=1e-10, allow_not_converged=True)  # the guess itself
+        guess_err = float(torch.linalg.norm(pg - p0) / torch.linalg.norm(p0))
+        solver.set_opts(initial_guess=2, max_iters=200)
+        p1, it1, _ = solver.solve(rhs, tol=1e-10)
+        st = solver.stats()
+        err = float(torch.linalg.norm(p1 - p0) / torch.linalg.norm(p0))
+        rows.append(dict(seed=seed, zero_iters=it0, net_iters=it1, used_net=st["used_net"],
+                         net_relres=st["net_relres"], guess_rel_err=guess_err,
+                         diff_vs_zero_guess=err))
+    mp_poisson_set_net(solver.handle, None)
+    solver.close()
+    zero = np.array([r["zero_iters"] for r in rows])
+    lrn = np.array([r["net_iters"] for r in rows])
+    used = np.array([r["used_net"] for r in rows])
+    summary = dict(samples=len(rows), mean_zero_iters=float(zero.mean()),
+                   mean_net_iters=float(lrn.mean()), iterations_saved=float((zero - lrn).mean()),
+                   fallback_rate=float(1.0 - used.mean()),
+                   median_net_relres=float(np.median([r["net_relres"] for r in rows])),
+                   median_guess_rel_err=float(np.median([r["guess_rel_err"] for r in rows])))
+    if log:
+        log("  eval: " + json.dumps(summary))
+    return summary, rows
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--train-seed0", type=int, default=10000)
+    ap.add_argument("--eval", type=int, default=200)
+    ap.add_argument("--eval-seed0", type=int, default=20000)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=1e-4)
+    ap.add_argument("--init-seed", type=int, default=7)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--report", default=None)
+    a = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    n = a.n
+    t0 = time.time()
+    print("data: %d training samples at %d^3" % (a.train, n), flush=True)
+    X, Q, its = make_dataset(list(range(a.train_seed0, a.train_seed0 + a.train)), n)
+    t_data = time.time() - t0
+    net = Net(n, n, n)
+    net.set_params(init_params(net, a.init_seed))
+    print("train: %d epochs" % a.epochs, flush=True)
+    t1 = time.time()
+    losses = train(net, X, Q, a.epochs, a.lr, a.init_seed, lr_final=a.lr_final)
+    t_train = time.time() - t1
+    del X, Q
+    torch.cuda.empty_cache()
+    summary, rows = evaluate(net, list(range(a.eval_seed0, a.eval_seed0 + a.eval)), n)
+    report = dict(n=n, train_samples=a.train, epochs=a.epochs, lr=a.lr, lr_final=a.lr_final,
+                  data_seconds=t_data, train_seconds=t_train,
+                  steps=len(losses), loss_first=float(np.mean(losses[:50])),
+                  loss_last=float(np.mean(losses[-50:])), train_solver_iters=float(np.mean(its)),
+                  eval=summary)
+    print(json.dumps(report), flush=True)
+    if a.out:
+        np.savez(a.out, params=net.get_params().cpu().numpy(), n=n, losses=np.array(losses))
+    if a.report:
+        with open(a.report, "w") as f:
+            json.dump(dict(report=report, rows=rows), f, indent=1)
+    net.close()
+
+
+if __name__ == "__main__":
+    main()

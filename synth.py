@@ -47,13 +47,16 @@ def _min_image(d: np.ndarray, length: float, periodic: bool) -> np.ndarray:
     return d - length * np.round(d / length)
 
 
-def level_set(shape, h, bubbles, pool_z0=None, bc=(PERIODIC, PERIODIC, NEUMANN)):
+def level_set(shape, h, bubbles, pool_z0=None, bc=(PERIODIC, PERIODIC, NEUMANN), device=None):
     """Gas-positive signed distance of a union of spherical bubbles and an
     optional gas layer above a liquid pool (gas for z > pool_z0).
 
     phi = max(z - pool_z0, max_b (R_b - |x - c_b|)), distances taken with the
-    minimum-image convention along periodic axes.  Returns (nz, ny, nx) f64.
+    minimum-image convention along periodic axes.  Returns (nz, ny, nx) f64
+    (a torch tensor on `device` when given; same formula).
     """
+    if device is not None:
+        return _level_set_torch(shape, h, bubbles, pool_z0, bc, device)
     nz, ny, nx = shape
     x = cell_centres(nx, h)[None, None, :]
     y = cell_centres(ny, h)[None, :, None]
@@ -68,6 +71,29 @@ def level_set(shape, h, bubbles, pool_z0=None, bc=(PERIODIC, PERIODIC, NEUMANN))
         dz = _min_image(z - cz, lz, bc[2] == PERIODIC)
         phi = np.maximum(phi, r - np.sqrt(dx * dx + dy * dy + dz * dz))
     return np.ascontiguousarray(phi)
+
+
+def _level_set_torch(shape, h, bubbles, pool_z0, bc, device):
+    import torch
+    nz, ny, nx = shape
+    f64 = torch.float64
+    x = ((torch.arange(nx, dtype=f64, device=device) + 0.5) * h)[None, None, :]
+    y = ((torch.arange(ny, dtype=f64, device=device) + 0.5) * h)[None, :, None]
+    z = ((torch.arange(nz, dtype=f64, device=device) + 0.5) * h)[:, None, None]
+    lx, ly, lz = nx * h, ny * h, nz * h
+    phi = torch.full(shape, -float("inf"), dtype=f64, device=device)
+    if pool_z0 is not None:
+        phi = torch.maximum(phi, (z - pool_z0).expand(shape))
+
+    def mi(d, length, periodic):
+        return d - length * torch.round(d / length) if periodic else d
+
+    for (cx, cy, cz), r in bubbles:
+        dx = mi(x - cx, lx, bc[0] == PERIODIC)
+        dy = mi(y - cy, ly, bc[1] == PERIODIC)
+        dz = mi(z - cz, lz, bc[2] == PERIODIC)
+        phi = torch.maximum(phi, r - torch.sqrt(dx * dx + dy * dy + dz * dz))
+    return phi.contiguous()
 
 
 def random_bubbles(seed, count, rmin, rmax, n, h=None, pool_z0=None, max_tries=200000):

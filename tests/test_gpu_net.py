@@ -1,0 +1,219 @@
+"""Learned warm start on the GPU vs the FP64 conv-net oracle.
+
+Single kernels (forward, input gradient through the flipped/transposed
+weights, weight gradient) are compared on identical BF16-rounded operands
+with FP32-accumulation tolerances; the whole U-Net forward with BF16
+rounding emulated in the oracle; the U-Net parameter gradient against the
+oracle's FP64 backward (loose: the GPU keeps activation gradients in BF16).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import conv
+from paper_2312_11740_gb300 import Net, mp_conv3d_fwd, mp_conv3d_wgrad
+
+pytestmark = pytest.mark.gpu
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def bf16_round(x):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    b = x.view(np.uint32).astype(np.uint64)
+    b = ((b + (((b >> 16) & 1) + 0x7FFF)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def to_bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).cuda()
+
+
+def to_f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def rel_max(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("ca,cout", [(16, 16), (32, 64), (64, 32), (16, 48), (32, 96), (64, 128)])
+def test_conv_forward_matches_oracle(ca, cout):
+    g = rng(ca * 1000 + cout)
+    shape = (8, 8, 16)
+    x = bf16_round(g.standard_normal(shape + (ca,)))
+    w = bf16_round(g.standard_normal((cout, 3, 3, 3, ca)) / np.sqrt(27 * ca))
+    b = g.standard_normal(cout).astype(np.float32).astype(np.float64)
+    y = mp_conv3d_fwd(to_bf16(x), to_bf16(w.reshape(cout, 27, ca)), cout, bias=to_f32(b),
+                      out32=True).cpu().numpy()
+    ref = conv.conv3d(x, w, b)
+    assert rel_max(y, ref) < 1e-5
+    # BF16 output with ReLU: rounding of the FP32 result
+    yb = mp_conv3d_fwd(to_bf16(x), to_bf16(w.reshape(cout, 27, ca)), cout, bias=to_f32(b),
+                       relu=True).float().cpu().numpy()
+    r = np.maximum(ref, 0.0)
+    assert np.all(np.abs(yb - r) <= 2.0 ** -8 * np.abs(r) + 1e-5 * np.abs(r).max())
+
+
+def test_conv_forward_upsampled_concat_matches_oracle():
+    g = rng(7)
+    xa = bf16_round(g.standard_normal((4, 4, 8, 32)))    # half resolution
+    xb = bf16_round(g.standard_normal((8, 8, 16, 16)))
+    cout = 48
+    w = bf16_round(g.standard_normal((cout, 3, 3, 3, 48)) / np.sqrt(27 * 48))
+    y = mp_conv3d_fwd(to_bf16(xa), to_bf16(w.reshape(cout, 27, 48)), cout, xb=to_bf16(xb),
+                      up_a=True, out32=True).cpu().numpy()
+    ref = conv.conv3d(np.concatenate([conv.upsample2(xa), xb], axis=-1), w)
+    assert rel_max(y, ref) < 1e-5
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (64, 16), (96, 32)])
+def test_input_gradient_through_flipped_weights(cin, cout):
+    g = rng(cin + 7 * cout)
+    w = bf16_round(g.standard_normal((cout, 3, 3, 3, cin)) / np.sqrt(27 * cin))
+    gy = bf16_round(g.standard_normal((8, 8, 16, cout)))
+    # wd[ci][t][co] = w[co][26 - t][ci]
+    wd = w.reshape(cout, 27, cin)[:, ::-1, :].transpose(2, 1, 0).copy()
+    dx = mp_conv3d_fwd(to_bf16(gy), to_bf16(wd), cin, out32=True).cpu().numpy()
+    assert rel_max(dx, conv.conv3d_dgrad(gy, w)) < 1e-5
+
+
+@pytest.mark.parametrize("ca,cb,up,cout", [(16, 0, False, 32), (64, 0, False, 16),
+                                           (32, 16, True, 16), (64, 32, True, 64)])
+def test_weight_gradient_matches_oracle(ca, cb, up, cout):
+    g = rng(ca + 3 * cb + 11 * cout)
+    full = (8, 8, 16)
+    xa = bf16_round(g.standard_normal(((4, 4, 8) if up else full) + (ca,)))
+    xb = bf16_round(g.standard_normal(full + (cb,))) if cb else None
+    gy = bf16_round(g.standard_normal(full + (cout,)))
+    dw = mp_conv3d_wgrad(to_bf16(xa), to_bf16(gy), xb=None if xb is None else to_bf16(xb),
+                         up_a=up).cpu().numpy()
+    xin = conv.upsample2(xa) if up else xa
+    if cb:
+        xin = np.concatenate([xin, xb], axis=-1)
+    ref = conv.conv3d_wgrad(xin, gy).reshape(cout, 27, ca + cb)
+    assert rel_max(dw, ref) < 1e-5
+
+
+def oracle_params_from_vector(vec):
+    """GPU parameter vector -> oracle dict (first layer keeps its 2 used inputs)."""
+    p, off = {}, 0
+    for name, co, ci in conv.layer_shapes():
+        ci_gpu = 16 if name == "e0a" else ci
+        w = vec[off:off + co * 27 * ci_gpu].reshape(co, 27, ci_gpu)
+        off += co * 27 * ci_gpu
+        p[name + ".w"] = w[:, :, :ci].reshape(co, 3, 3, 3, ci)
+        p[name + ".b"] = vec[off:off + co]
+        off += co
+    p["head.w"] = vec[off:off + conv.CH[0]].reshape(1, -1)
+    off += conv.CH[0]
+    p["head.b"] = vec[off:off + 1]
+    return p
+
+
+def random_param_vector(net, seed):
+    g = rng(seed)
+    parts = []
+    for name, co, ci in conv.layer_shapes():
+        ci_gpu = 16 if name == "e0a" else ci
+        parts.append(g.standard_normal(co * 27 * ci_gpu) * np.sqrt(2.0 / (27 * ci)))
+        parts.append(0.05 * g.standard_normal(co))
+    parts.append(g.standard_normal(conv.CH[0]) / 4.0)
+    parts.append(np.array([0.1]))
+    vec = np.concatenate(parts)
+    assert vec.size == net.param_count()
+    return bf16_round(vec).astype(np.float32).astype(np.float64)
+
+
+def make_input(seed, shape):
+    g = rng(seed)
+    x = np.zeros(shape + (16,))
+    x[..., 0] = np.clip(g.standard_normal(shape), -1, 1)
+    x[..., 1] = g.standard_normal(shape)
+    return bf16_round(x)
+
+
+def test_unet_forward_matches_oracle():
+    shape = (32, 32, 32)
+    net = Net(32, 32, 32)
+    vec = random_param_vector(net, 1)
+    net.set_params(to_f32(vec))
+    x = make_input(2, shape)
+    net.set_input(to_bf16(x))
+    q = net.forward().cpu().numpy()
+    ref, _ = conv.unet_forward(oracle_params_from_vector(vec), x[..., :2], rnd=bf16_round)
+    assert np.linalg.norm(q - ref) / np.linalg.norm(ref) < 2e-2
+    net.close()
+
+
+def test_unet_backward_matches_oracle():
+    shape = (32, 32, 32)
+    net = Net(32, 32, 32)
+    vec = random_param_vector(net, 3)
+    net.set_params(to_f32(vec))
+    x = make_input(4, shape)
+    net.set_input(to_bf16(x))
+    gq = rng(5).standard_normal(shape)
+    grad = net.backward(to_f32(gq)).cpu().numpy()
+    p = oracle_params_from_vector(vec)
+    _, cache = conv.unet_forward(p, x[..., :2], rnd=bf16_round)
+    gref, _ = conv.unet_backward(p, cache, gq, rnd=bf16_round)
+    # GPU gradient vector laid out like the parameters (first layer: 16 inputs)
+    off = 0
+    for name, co, ci in conv.layer_shapes():
+        ci_gpu = 16 if name == "e0a" else ci
+        gw = grad[off:off + co * 27 * ci_gpu].reshape(co, 27, ci_gpu)[:, :, :ci]
+        off += co * 27 * ci_gpu
+        gb = grad[off:off + co]
+        off += co
+        rw = gref[name + ".w"].reshape(co, 27, ci)
+        cos = (gw * rw).sum() / (np.linalg.norm(gw) * np.linalg.norm(rw))
+        # BF16 storage of activation gradients compounds along the backward
+        # chain: the oracle rounds at the same places, but its FP64 values
+        # before rounding differ from the kernels' FP32 sums, so near-tie
+        # roundings differ and the difference grows toward the first
+        # layers (e0a, e0b: the longest chain, ~6% measured, cos 0.998)
+        assert cos > 0.995, (name, cos)
+        err = np.linalg.norm(gw - rw) / np.linalg.norm(rw)
+        assert err < (1e-1 if name in ("e0a", "e0b") else 5e-2), (name, err)
+        assert np.linalg.norm(gb - gref[name + ".b"]) <= 3e-2 * np.linalg.norm(gref[name + ".b"]) + 1e-6
+    gh = grad[off:off + conv.CH[0]]
+    assert np.linalg.norm(gh - gref["head.w"].ravel()) / np.linalg.norm(gref["head.w"]) < 2e-2
+    net.close()
+
+
+def test_train_step_is_adam_on_the_oracle_gradient():
+    """One training step = forward, gauge-free MSE, backward, Adam.  At
+    step 1 Adam moves every parameter by -lr * g / (|g| + eps), i.e. by
+    -lr * sign(g): the update's sign must match the oracle's gradient of the
+    same loss wherever that gradient is not tiny."""
+    shape = (32, 32, 32)
+    net = Net(32, 32, 32)
+    vec = random_param_vector(net, 6)
+    net.set_params(to_f32(vec))
+    x = make_input(7, shape)
+    net.set_input(to_bf16(x))
+    target = rng(8).standard_normal(shape)
+    lr = 1e-3
+    loss = net.train_step(to_f32(target), lr, 1)
+    delta = net.get_params().cpu().numpy().astype(np.float64) - vec
+    p = oracle_params_from_vector(vec)
+    out, cache = conv.unet_forward(p, x[..., :2], rnd=bf16_round)
+    L, gout = conv.gauge_mse(out, target)
+    assert loss == pytest.approx(L, rel=2e-2)
+    gref, _ = conv.unet_backward(p, cache, gout, rnd=bf16_round)
+    off, agree, total = 0, 0, 0
+    for name, co, ci in conv.layer_shapes():
+        ci_gpu = 16 if name == "e0a" else ci
+        dw = delta[off:off + co * 27 * ci_gpu].reshape(co, 27, ci_gpu)[:, :, :ci].ravel()
+        off += co * 27 * ci_gpu + co
+        gw = gref[name + ".w"].ravel()
+        big = np.abs(gw) > 1e-2 * np.abs(gw).max()
+        agree += np.sum(np.sign(dw[big]) == -np.sign(gw[big]))
+        total += big.sum()
+        assert np.max(np.abs(dw)) <= lr * 1.001
+    assert agree / total > 0.99
+    net.close()
