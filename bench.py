@@ -17,6 +17,7 @@ not shard: one grid per GPU); value = steps of all ranks / max time.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -53,7 +54,7 @@ def peaks():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -66,9 +67,17 @@ class ClockSampler:
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(index)], stdout=self.out, stderr=subprocess.DEVNULL)
+                 "-lms", "50", "-i", str(index)], stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        self.t0 = self.t1 = None
+        time.sleep(0.5)  # let the sampler start before the timed region
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
@@ -82,14 +91,21 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append(dict(sm=float(parts[1]), max=float(parts[2]), power=float(parts[3]),
-                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append(dict(ts=ts, sm=float(parts[2]), max=float(parts[3]),
+                                 power=float(parts[4]), hw=parts[6], hwt=parts[7], swt=parts[8],
+                                 pcap=parts[9]))
             except ValueError:
                 continue
         os.unlink(self.path)
+        # samples taken inside the timed region (all of them if none fell inside)
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if self.t0 <= r["ts"] <= self.t1]
+            if inside:
+                rows = inside
         if not rows:
             return None
         reasons = set()
@@ -240,6 +256,8 @@ def run_mine(args, rank, world, local_rank):
         sampler = ClockSampler(local_rank) if name == "mixed" else None
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if sampler:
+            sampler.mark_start()
         e0.record(stream)
         its, relres = [], []
         for k in range(args.warmup, args.warmup + args.steps):
@@ -250,6 +268,8 @@ def run_mine(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        if sampler:
+            sampler.mark_end()
         clocks = sampler.stop() if sampler else None
         ms = e0.elapsed_time(e1)
         if world > 1:
@@ -361,7 +381,7 @@ def run_mine(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--n", type=int, default=256, help="grid cells per axis (default 256)")

@@ -99,6 +99,20 @@ mp_status mp_net_forward(mp_net_handle net, float *q_dev);
 mp_status mp_net_train_step(mp_net_handle net, const float *q_target_dev, float lr, int step,
                             double *loss_out);
 
+/*
+ * Loss of mp_net_train_step.  kind 0: gauge-free mean squared error against
+ * the target (default).  kind 1: energy norm,
+ *   L = 1 - (q.A t)^2 / ((q.A q)(t.A t)),
+ * the squared relative A-norm error of the best multiple of q, i.e. of the
+ * guess the solver forms with its energy-optimal scale.  A is the
+ * (positive semidefinite) variable-coefficient Laplacian whose ghost-fluid
+ * face coefficients come from the phi channel of the current input
+ * (f0 = phi / 4h is unclipped wherever a face crosses the interface), with
+ * densities rho_l, rho_g and boundary conditions bc (as mp_poisson_setup).
+ */
+mp_status mp_net_set_loss(mp_net_handle net, int kind, double rho_l, double rho_g,
+                          const mp_bc bc[3]);
+
 /* Set the 16-channel BF16 input directly (device pointer, N*16 bf16). */
 mp_status mp_net_set_input(mp_net_handle net, const void *x16_dev);
 
@@ -122,7 +136,8 @@ void mp_net_destroy(mp_net_handle net);
 /* Use `net` (or NULL to detach) for initial_guess = 2 in mp_poisson_solve:
  * the solve builds the features from phi and b, runs the network, takes
  * p0 = alpha (q - mean q) with the energy-optimal alpha = (q.bt)/(q.A q),
- * and keeps it only if ||b - A p0|| < ||b|| (mp_stats.used_net); otherwise
+ * and keeps it according to mp_opts.net_check (default: only if
+ * ||b - A p0|| < ||b||; mp_stats.used_net, mp_stats.net_relres); otherwise
  * it starts from zero.  The grid must match. */
 mp_status mp_poisson_set_net(mp_handle hd, mp_net_handle net);
 

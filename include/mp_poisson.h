@@ -69,17 +69,24 @@ typedef struct {
   int max_iters;     /* outer iterations (FP64) or total inner iterations (mixed). Default 200. */
   int nu1, nu2;      /* pre/post red-black Gauss–Seidel sweeps on the finest level. Default 2, 2. */
   int nu_growth;     /* sweeps multiply by this per coarser level. Default 2. */
-  int nu_max;        /* cap on sweeps per level. Default 16. */
-  double inner_rtol; /* mixed: inner FP32 solve reduces its residual by this factor per
-                        outer refinement step. Default 1e-4. */
-  int inner_max;     /* mixed: cap on inner iterations per outer step. Default 12. */
+  int nu_max;        /* cap on sweeps per level. Default 8. */
+  double inner_rtol; /* mixed: the FP32 recurrence residual must fall by this factor below the
+                        last true residual before the FP32 correction is folded into the FP64
+                        solution and the residual replaced by the true FP64 one (reliable
+                        update; the CG direction is kept).  Default 1e-4. */
+  int inner_max;     /* mixed: at most this many FP32 iterations between true residuals.
+                        Default 12. */
+  int net_check;     /* learned guess p0 = alpha q (alpha energy-optimal) is kept when
+                        0: its residual ||b - A p0|| is below ||b|| (default);
+                        1: alpha is finite and nonzero, i.e. whenever the A-norm error of p0
+                           is below that of the zero guess (always true for that alpha). */
   void *stream;      /* cudaStream_t; NULL = legacy default stream. */
 } mp_opts;
 
 /* Statistics of the last mp_poisson_solve / mp_poisson_project_step. */
 typedef struct {
   int iterations;      /* V-cycle applications (preconditioner or stationary steps) */
-  int outer_steps;     /* mixed: FP64 refinement steps; FP64 mode: equals iterations */
+  int outer_steps;     /* mixed: true FP64 residuals formed after the first; FP64: = iterations */
   double relres;       /* final ||b - A p|| / ||b||, FP64, true residual */
   double r0;           /* initial ||b - A p0|| / ||b|| */
   int used_net;        /* 1 if the learned guess was kept, 0 if not requested or rejected */
@@ -123,8 +130,10 @@ mp_status mp_poisson_set_opts(mp_handle hd, const mp_opts *opts);
  * rhs_dev: device, N f64 (e.g. div u*).  p_dev: device, N f64, in/out
  * (read only if initial_guess = 1), mean-free on exit.  iterations (may be
  * NULL) gets mp_stats.iterations.  res_hist (host, may be NULL) gets up to
- * res_hist_cap relative residuals: [0] is the initial one, then one per
- * outer iteration; res_hist_len (may be NULL) gets the count written.
+ * res_hist_cap true relative residuals: [0] is the initial one, then one
+ * per FP64 iteration (FP64 mode) or per reliable update (mixed mode, where
+ * the FP32 iterations in between carry only a recurrence estimate);
+ * res_hist_len (may be NULL) gets the count written.
  * Returns MP_OK, MP_ERR_NOT_CONVERGED (p holds the last iterate) or an error.
  */
 mp_status mp_poisson_solve(mp_handle hd, const double *rhs_dev, double *p_dev, double tol,

@@ -41,6 +41,7 @@ class mp_opts(ctypes.Structure):
         ("nu_max", ctypes.c_int),
         ("inner_rtol", ctypes.c_double),
         ("inner_max", ctypes.c_int),
+        ("net_check", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -113,6 +114,7 @@ SIGNATURES = {
     "mp_net_backward": (_I, [_P, _P, _P]),
     "mp_net_pressure": (_I, [_P, _D, _P]),
     "mp_net_set_stream": (_I, [_P, _P]),
+    "mp_net_set_loss": (_I, [_P, _I, _D, _D, _IP]),
     "mp_net_make_target": (_I, [_P, _P, _P]),
     "mp_net_destroy": (None, [_P]),
 }

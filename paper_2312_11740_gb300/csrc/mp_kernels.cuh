@@ -62,6 +62,10 @@ __device__ __forceinline__ bool thread0() {
   return threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
 }
 
+// phi > 0 (gas) tested on the bit pattern: an integer comparison instead of
+// an FP64 one (FP64 instructions are the scarce resource of the setup kernels)
+__device__ __forceinline__ bool gas(double v) { return __double_as_longlong(v) > 0; }
+
 // ------------------------------------------------------------ A1: curvature
 // kappa = -div(grad phi/|grad phi|) by central differences at cell centres,
 // |grad phi| floored at 1e-12, |kappa| clamped to 1/h.  Gas-positive phi
@@ -81,9 +85,9 @@ __global__ void k_curvature(const double *__restrict__ phi, double *__restrict__
   double xm = phi[at(d, im, j, k)], xp = phi[at(d, ip, j, k)];
   double ym = phi[at(d, i, jm, k)], yp = phi[at(d, i, jp, k)];
   double zm = phi[at(d, i, j, km)], zp = phi[at(d, i, j, kp)];
-  bool gc = c > 0.0;
-  bool band = ((xm > 0.0) != gc) || ((xp > 0.0) != gc) || ((ym > 0.0) != gc) ||
-              ((yp > 0.0) != gc) || ((zm > 0.0) != gc) || ((zp > 0.0) != gc);
+  bool gc = gas(c);
+  bool band = (gas(xm) != gc) || (gas(xp) != gc) || (gas(ym) != gc) || (gas(yp) != gc) ||
+              (gas(zm) != gc) || (gas(zp) != gc);
   if (!band) {
     kap[at(d, i, j, k)] = 0.0;
     return;
@@ -116,7 +120,7 @@ __global__ void k_curvature(const double *__restrict__ phi, double *__restrict__
 // as computing 1/rho here), so single-fluid faces cost no division.
 __device__ __forceinline__ double gfm_beta(double pa, double pb, double rl, double rg, double irl,
                                            double irg) {
-  bool ga = pa > 0.0, gb = pb > 0.0;
+  bool ga = gas(pa), gb = gas(pb);
   if (ga == gb) return ga ? irg : irl;
   double ra = ga ? rg : rl, rb = gb ? rg : rl;
   double th = fabs(pa) / (fabs(pa) + fabs(pb));
@@ -126,7 +130,7 @@ __device__ __forceinline__ double gfm_beta(double pa, double pb, double rl, doub
 // Pressure jump [p]_{a->b} = p(b side) - p(a side) = +-sigma kappa_G,
 // kappa_G linearly interpolated to the interface; 0 off the interface.
 __device__ __forceinline__ double gfm_jump(double pa, double pb, double ka, double kb, double sig) {
-  bool ga = pa > 0.0, gb = pb > 0.0;
+  bool ga = gas(pa), gb = gas(pb);
   if (ga == gb) return 0.0;
   double aa = fabs(pa), ab = fabs(pb);
   double kg = (ab * ka + aa * kb) / (aa + ab);
@@ -159,10 +163,17 @@ __global__ void k_jump(const double *__restrict__ phi, const double *__restrict_
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
-  double pc = phi[c], kc = kap[c];
+  double pc = phi[c];
   size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
   size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
   size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+  const bool g = gas(pc);
+  if (gas(phi[xl]) == g && gas(phi[xh]) == g && gas(phi[yl]) == g && gas(phi[yh]) == g &&
+      gas(phi[zl]) == g && gas(phi[zh]) == g) {
+    Jt[c] = 0.0;  // no interface on any face of the cell
+    return;
+  }
+  double kc = kap[c];
   double s = 0.0;
   s += bx[xh] * gfm_jump(pc, phi[xh], kc, kap[xh], sig) - bx[c] * gfm_jump(phi[xl], pc, kap[xl], kc, sig);
   s += by[yh] * gfm_jump(pc, phi[yh], kc, kap[yh], sig) - by[c] * gfm_jump(phi[yl], pc, kap[yl], kc, sig);
@@ -181,7 +192,10 @@ __global__ void k_diag(const double *__restrict__ bx, const double *__restrict__
   size_t c = at(d, i, j, k);
   double s = bx[c] + bx[at(d, whi(i, d.nx), j, k)] + by[c] + by[at(d, i, whi(j, d.ny), k)] + bz[c] +
              bz[at(d, i, j, whi(k, d.nz))];
-  double is = 1.0 / s;
+  // 1/s: FP32 reciprocal refined by one Newton step in FP64 (relative error
+  // ~1e-14, two FP64 operations instead of a full FP64 division)
+  double is = (double)(1.0f / (float)s);
+  is = is * fma(-s, is, 2.0);
   diag[c] = s;
   idiag[c] = is;
   bx32[c] = (float)bx[c];
@@ -639,11 +653,13 @@ __global__ void k_add(T *__restrict__ x, const T *__restrict__ y, size_t n) {
     x[e] += y[e];
 }
 
-// x64 += e32 (refinement step accumulation in FP64)
-__global__ void k_add_f32(double *__restrict__ x, const float *__restrict__ e, size_t n) {
+// x64 += e32, then e32 = 0 (accumulation of an FP32 correction in FP64)
+__global__ void k_add_f32(double *__restrict__ x, float *__restrict__ e, size_t n) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
-       k += (size_t)gridDim.x * blockDim.x)
+       k += (size_t)gridDim.x * blockDim.x) {
     x[k] += (double)e[k];
+    e[k] = 0.f;
+  }
 }
 
 template <typename T>
@@ -748,17 +764,21 @@ __global__ void k_project(const double *__restrict__ p, const double *__restrict
                           const double *__restrict__ kap, const double *__restrict__ bx,
                           const double *__restrict__ by, const double *__restrict__ bz,
                           double *__restrict__ ux, double *__restrict__ uy,
-                          double *__restrict__ uz, Dims d, double sig, double h) {
+                          double *__restrict__ uz, Dims d, double sig, double ih) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
   double pc = p[c], fc = phi[c], kc = kap[c];
   size_t xl = at(d, wlo(i, d.nx), j, k), yl = at(d, i, wlo(j, d.ny), k),
          zl = at(d, i, j, wlo(k, d.nz));
-  double ih = 1.0 / h;
-  ux[c] -= bx[c] * (pc - p[xl] - gfm_jump(phi[xl], fc, kap[xl], kc, sig)) * ih;
-  uy[c] -= by[c] * (pc - p[yl] - gfm_jump(phi[yl], fc, kap[yl], kc, sig)) * ih;
-  uz[c] -= bz[c] * (pc - p[zl] - gfm_jump(phi[zl], fc, kap[zl], kc, sig)) * ih;
+  const bool g = gas(fc);
+  double dx = pc - p[xl], dy = pc - p[yl], dz = pc - p[zl];
+  if (gas(phi[xl]) != g) dx -= gfm_jump(phi[xl], fc, kap[xl], kc, sig);
+  if (gas(phi[yl]) != g) dy -= gfm_jump(phi[yl], fc, kap[yl], kc, sig);
+  if (gas(phi[zl]) != g) dz -= gfm_jump(phi[zl], fc, kap[zl], kc, sig);
+  ux[c] = fma(-bx[c] * ih, dx, ux[c]);
+  uy[c] = fma(-by[c] * ih, dy, uy[c]);
+  uz[c] = fma(-bz[c] * ih, dz, uz[c]);
 }
 
 // y = scale * v (used to unscale J and the operator for the test API)

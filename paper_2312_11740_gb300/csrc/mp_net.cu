@@ -1,6 +1,7 @@
 // Learned warm start: BF16 implicit-GEMM 3x3x3 convolutions on the 5th-generation
 // tensor cores (tcgen05.mma, operands in shared memory, FP32 accumulator in
 // tensor memory), and the U-Net built from them.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -86,14 +87,11 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// ------------------------------------------------------------ conv forward
-// D[128 voxels][COUT] = A[128][K] B[COUT][K]^T with K = 27 taps x Cin (tap
-// major).  A row = the input channels of one voxel's neighbour for a tap,
-// gathered from up to two tensors (the first optionally at half resolution,
-// read through nearest-neighbour upsampling: the decoder's up+concat fused
-// into the gather).  Smem tiles use the no-swizzle K-major core-matrix
-// layout: element (r, k) of an R x 64 stage tile at
-// (k/8)*(R/8)*128 + (r/8)*128 + (r%8)*16 + (k%8)*2 bytes.
+// ------------------------------------------------------------ convolutions
+// Geometry of one 3x3x3 convolution whose input is the channel concatenation
+// of xa (optionally at half resolution, read through nearest upsampling)
+// and xb.  Smem operand tiles use the no-swizzle K-major core-matrix layout:
+// a core matrix is 8 rows x 16 bytes (8 BF16 of K) stored contiguously.
 struct ConvGeom {
   int nx, ny, nz;   // output (and full-resolution input) grid
   int ca, cb;       // channels of the two inputs (cb = 0: single input)
@@ -120,54 +118,110 @@ __host__ __device__ constexpr int conv_smem_bytes() {
   return NSTAGE * (A_STAGE_BYTES + b_stage_bytes<COUT>()) + 1024;
 }
 
-// 16 input channels [ci0, ci0+16) of the voxel (x, y, z) (zero outside)
-__device__ __forceinline__ void gather16(const bf16 *__restrict__ xa, const bf16 *__restrict__ xb,
-                                         const ConvGeom &g, int x, int y, int z, int ci0,
-                                         uint4 &lo, uint4 &hi) {
-  lo = make_uint4(0, 0, 0, 0);
-  hi = lo;
-  if (x < 0 || y < 0 || z < 0 || x >= g.nx || y >= g.ny || z >= g.nz) return;
-  const uint4 *src;
-  if (ci0 < g.ca) {
-    int ax = x, ay = y, az = z, anx = g.nx, any = g.ny;
-    if (g.up_a) {
-      ax >>= 1;
-      ay >>= 1;
-      az >>= 1;
-      anx >>= 1;
-      any >>= 1;
-    }
-    src = reinterpret_cast<const uint4 *>(
-        xa + (((size_t)az * any + ay) * anx + ax) * g.ca + ci0);
-  } else {
-    src = reinterpret_cast<const uint4 *>(
-        xb + (((size_t)z * g.ny + y) * g.nx + x) * g.cb + (ci0 - g.ca));
-  }
-  lo = __ldg(src);
-  hi = __ldg(src + 1);
+// ------------------------------------------------ conv forward, halo-tiled
+// CTA tile: 8 (x) x 16 (y) x HT_Z (z) output voxels and NC output channels,
+// one M = 128 accumulator per z-plane (row r = voxel (r % 8, r / 8) of the
+// plane).  For each 16-channel chunk of the input the tile's halo
+// (10 x 18 x (HT_Z + 2) voxels) is staged ONCE in shared memory, as two
+// 8-channel planes laid out [z][y][x][8 ch] (the box order of a 4D TMA
+// load, whose out-of-range fill supplies the zero padding).  Each of the 27
+// taps is then one MMA per plane whose A descriptor starts at the tap's
+// shifted voxel: a core matrix (8 rows x 16 bytes) is 8 x-consecutive
+// voxels, the next core matrix along M is the next y row (stride 10 x 16
+// bytes), the next along K the other 8-channel plane.  The weights of the
+// chunk arrive as one bulk copy of a pre-packed image [t][k/8][co/8][co%8][8].
+// A persistent CTA walks its tiles chunk by chunk through an NS-deep ring of
+// stages (TMA -> mbarrier -> MMA issued by one thread -> commit -> refill),
+// with two TMEM accumulator sets so that the epilogue of one tile overlaps
+// the MMAs of the next.  Inputs read through nearest upsampling (the
+// decoder's up + concat) are gathered by all threads instead of the TMA.
+constexpr int HT_Z = 4;
+constexpr int HX = 10, HY = 18, HZ = HT_Z + 2;
+constexpr int HVOX = HX * HY * HZ;      // halo voxels per tile
+constexpr int HPLANE = HVOX * 16;       // bytes of one 8-channel halo plane
+constexpr int HALO_BYTES = 2 * HPLANE;  // a 16-channel chunk
+
+template <int NC>
+__host__ __device__ constexpr int himg_bytes() {
+  return 27 * NC * 32;  // weights of one 16-channel chunk for NC outputs
+}
+template <int NC>
+__host__ __device__ constexpr int h_nstage() {
+  return NC == 32 ? 3 : 2;
+}
+template <int NC>
+__host__ __device__ constexpr int h_stage_bytes() {
+  return HALO_BYTES + himg_bytes<NC>();
+}
+template <int NC>
+__host__ __device__ constexpr int h_smem_bytes() {
+  return h_nstage<NC>() * h_stage_bytes<NC>() + 1024;
+}
+template <int NC>
+__host__ __device__ constexpr int h_tmem_cols() {
+  return 2 * HT_Z * NC <= 128 ? 128 : (2 * HT_Z * NC <= 256 ? 256 : 512);
+}
+template <int NC>
+__host__ __device__ constexpr int h_ctas_per_sm() {
+  return NC == 16 ? 2 : 1;
 }
 
-template <int COUT>
-__global__ void __launch_bounds__(CONV_THREADS)
-k_conv3d_fwd(const bf16 *__restrict__ xa, const bf16 *__restrict__ xb,
-             const bf16 *__restrict__ w, const float *__restrict__ bias, bf16 *__restrict__ y,
-             float *__restrict__ y32, ConvGeom g, int relu, int *__restrict__ err) {
-  constexpr int TM = tmem_cols<COUT>();  // TMEM allocation: a power of two >= 32
-  constexpr int BST = b_stage_bytes<COUT>();
-  extern __shared__ __align__(1024) uint8_t conv_smem[];
-  uint8_t *sm = conv_smem + ((1024 - (smem_u32(conv_smem) & 1023)) & 1023);
-  uint8_t *sA = sm;
-  uint8_t *sB = sm + NSTAGE * A_STAGE_BYTES;
-  __shared__ __align__(8) uint64_t mbar[NSTAGE];
+struct HaloArgs {
+  const bf16 *xa;       // first input (read by threads when upsampled)
+  const bf16 *wimg;     // packed weights [nsplit][nchunk][27][2][NC/8][8][8]
+  const float *bias;    // cout or NULL
+  bf16 *y;              // output (BF16) ...
+  float *y32;           // ... or FP32 when not NULL
+  int nx, ny, nz;       // output grid
+  int ca, up_a, cout, relu;
+  int tiles_x, tiles_y, ntiles, nsplit, nchunk;
+  int *err;
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], "
+      "[%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(mbar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+template <int NC>
+__global__ void __launch_bounds__(CONV_THREADS, h_ctas_per_sm<NC>())
+k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+              const HaloArgs a) {
+  constexpr int NS = h_nstage<NC>();
+  constexpr int SB = h_stage_bytes<NC>();
+  constexpr int WB = himg_bytes<NC>();
+  constexpr int TM = h_tmem_cols<NC>();
+  constexpr uint32_t IDESC = idesc_bf16(128, NC, 0, 0);
+  extern __shared__ __align__(1024) uint8_t hsm_raw[];
+  uint8_t *sm = hsm_raw + ((1024 - (smem_u32(hsm_raw) & 1023)) & 1023);
+  __shared__ __align__(8) uint64_t full[NS], done[NS];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
 
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // this thread's voxel: brick of 8 x 4 x 4 voxels
-  const int vx = blockIdx.x * 8 + (tid & 7), vy = blockIdx.y * 4 + ((tid >> 3) & 3),
-            vz = blockIdx.z * 4 + (tid >> 5);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(&mbar[s]);
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s]);
+      mbar_init(&done[s]);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -177,97 +231,212 @@ k_conv3d_fwd(const bf16 *__restrict__ xa, const bf16 *__restrict__ xb,
   tc_fence_after();
   const uint32_t taddr = tslot;
 
-  const int cpt = g.cin >> 4;          // 16-channel chunks per tap
-  const int ksteps = 27 * cpt;
-  const int nst = (ksteps + 3) >> 2;
-  const size_t wrow = (size_t)27 * g.cin;  // weights per output channel
-  constexpr uint32_t IDESC = idesc_bf16(128, COUT, 0, 0);
-  bool ok = true;
-  for (int s = 0; s < nst && ok; ++s) {
-    const int buf = s % NSTAGE;
-    if (s >= NSTAGE) {
-      bool done = mbar_wait(&mbar[buf], (uint32_t)((s / NSTAGE - 1) & 1));
-      if (!done) abort_flag = 1;
-      __syncthreads();
-      if (abort_flag) {
-        ok = false;
-        break;
+  // the grid is a multiple of nsplit: a CTA keeps one output-channel slice
+  const int split = blockIdx.x % a.nsplit;
+  const int tile0 = blockIdx.x / a.nsplit, tstep = gridDim.x / a.nsplit;
+  const int my_tiles = tile0 < a.ntiles ? (a.ntiles - 1 - tile0) / tstep + 1 : 0;
+  const int nst = my_tiles * a.nchunk;
+  // a stage's weights equal those NS stages earlier when NS % nchunk == 0
+  const bool w_reuse = (NS % a.nchunk) == 0;
+  const int anx = a.up_a ? a.nx >> 1 : a.nx, any = a.up_a ? a.ny >> 1 : a.ny;
+
+  auto tile_origin = [&](int lt, int &x0, int &y0, int &z0) {
+    const int tile = tile0 + lt * tstep;
+    const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
+    x0 = tx * 8;
+    y0 = (r % a.tiles_y) * 16;
+    z0 = (r / a.tiles_y) * HT_Z;
+  };
+
+  // fill the stage buffer of stage s: TMA (thread 0) and upsampled gathers (all)
+  auto produce = [&](int s) {
+    const int buf = s % NS, lt = s / a.nchunk, c = s - lt * a.nchunk;
+    int x0, y0, z0;
+    tile_origin(lt, x0, y0, z0);
+    uint8_t *st = sm + buf * SB;
+    const bool wload = !(s >= NS && w_reuse);
+    if (tid == 0) {
+      uint32_t bytes = wload ? (uint32_t)WB : 0u;
+      for (int g = 0; g < 2; ++g) {
+        const int cc = 16 * c + 8 * g;
+        if (!(a.up_a && cc < a.ca)) bytes += HPLANE;
       }
+      mbar_expect_tx(&full[buf], bytes);
+      for (int g = 0; g < 2; ++g) {
+        const int cc = 16 * c + 8 * g;
+        if (a.up_a && cc < a.ca) continue;
+        if (cc < a.ca)
+          tma_load_4d(st + g * HPLANE, &map_a, cc, x0 - 1, y0 - 1, z0 - 1, &full[buf]);
+        else
+          tma_load_4d(st + g * HPLANE, &map_b, cc - a.ca, x0 - 1, y0 - 1, z0 - 1, &full[buf]);
+      }
+      if (wload)
+        bulk_load(st + HALO_BYTES,
+                  a.wimg + ((size_t)split * a.nchunk + c) * (size_t)(WB / 2), (uint32_t)WB,
+                  &full[buf]);
     }
-    uint8_t *a_st = sA + buf * A_STAGE_BYTES;
-    uint8_t *b_st = sB + buf * BST;
-    const int kq = min(4, ksteps - 4 * s);
-    // A: this thread's voxel, 4 K-steps x 16 channels
-    for (int q = 0; q < kq; ++q) {
-      const int j = 4 * s + q, t = j / cpt, ci0 = (j - t * cpt) << 4;
-      const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-      uint4 lo, hi;
-      gather16(xa, xb, g, vx + dx, vy + dy, vz + dz, ci0, lo, hi);
-      const uint32_t rowoff = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
-      *reinterpret_cast<uint4 *>(a_st + (2 * q) * 2048 + rowoff) = lo;
-      *reinterpret_cast<uint4 *>(a_st + (2 * q + 1) * 2048 + rowoff) = hi;
-    }
-    // B: COUT rows x kq K-steps x 2 halves of 8 channels
-    for (int e = tid; e < COUT * kq * 2; e += CONV_THREADS) {
-      const int co = e % COUT, qh = e / COUT, q = qh >> 1, h = qh & 1;
-      const int j = 4 * s + q, t = j / cpt, ci0 = (j - t * cpt) << 4;
-      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(w + co * wrow + (size_t)t * g.cin +
-                                                            ci0 + 8 * h));
-      *reinterpret_cast<uint4 *>(b_st + (2 * q + h) * (COUT / 8) * 128 + (co >> 3) * 128 +
-                                 (co & 7) * 16) = v;
+    for (int g = 0; g < 2; ++g) {
+      const int cc = 16 * c + 8 * g;
+      if (!(a.up_a && cc < a.ca)) continue;
+      uint8_t *dst = st + g * HPLANE;
+      for (int v0 = 0; v0 < HVOX; v0 += 4 * CONV_THREADS) {
+        uint4 val[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * CONV_THREADS + tid;
+          val[u] = make_uint4(0, 0, 0, 0);
+          if (v < HVOX) {
+            const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+            if (gx >= 0 && gy >= 0 && gz >= 0 && gx < a.nx && gy < a.ny && gz < a.nz)
+              val[u] = __ldg(reinterpret_cast<const uint4 *>(
+                  a.xa + (((size_t)(gz >> 1) * any + (gy >> 1)) * anx + (gx >> 1)) * a.ca + cc));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * CONV_THREADS + tid;
+          if (v < HVOX) *reinterpret_cast<uint4 *>(dst + v * 16) = val[u];
+        }
+      }
     }
     fence_async_smem();
-    __syncthreads();
+  };
+
+  auto epilogue = [&](int lt) {
+    int x0, y0, z0;
+    tile_origin(lt, x0, y0, z0);
+    tc_fence_after();
+    const int r = warp * 32 + lane;
+    const int gx = x0 + (r & 7), gy = y0 + (r >> 3);
+    const uint32_t acc = (uint32_t)((lt & 1) * HT_Z * NC);
+    const int co0 = split * NC;
+#pragma unroll 1
+    for (int zp = 0; zp < HT_Z; ++zp) {
+      const int gz = z0 + zp;
+      const bool inside = gx < a.nx && gy < a.ny && gz < a.nz;
+      const size_t vox = ((size_t)gz * a.ny + gy) * a.nx + gx;
+#pragma unroll
+      for (int c0 = 0; c0 < NC; c0 += 16) {
+        float v[16];
+        tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + acc + zp * NC + c0, v);
+        if (inside) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float t = v[q] + (a.bias ? a.bias[co0 + c0 + q] : 0.f);
+            v[q] = a.relu ? fmaxf(t, 0.f) : t;
+          }
+          if (a.y32) {
+            float4 *o = reinterpret_cast<float4 *>(a.y32 + vox * a.cout + co0 + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+            __align__(16) bf16 hv[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) hv[q] = __float2bfloat16_rn(v[q]);
+            uint4 *o = reinterpret_cast<uint4 *>(a.y + vox * a.cout + co0 + c0);
+            o[0] = *reinterpret_cast<uint4 *>(&hv[0]);
+            o[1] = *reinterpret_cast<uint4 *>(&hv[8]);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+  };
+
+  int produced = 0, waited_full = 0, committed = 0, waited_done = 0;
+  for (; produced < NS - 1 && produced < nst; ++produced) produce(produced);
+  for (int s = 0; s < nst; ++s) {
+    const int buf = s % NS;
+    if (__all_sync(0xffffffffu, mbar_wait(&full[buf], (uint32_t)((s / NS) & 1))))
+      waited_full = s + 1;
+    else
+      abort_flag = 1;
+    __syncthreads();  // the gathers of stage s are visible; abort is seen by all
+    if (abort_flag) break;
+    const int lt = s / a.nchunk, c = s - lt * a.nchunk;
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = smem_u32(a_st), b0 = smem_u32(b_st);
-      for (int q = 0; q < kq; ++q) {
-        const uint64_t da = sdesc(a0 + 2 * q * 2048, 2048, 128);
-        const uint64_t db = sdesc(b0 + 2 * q * (COUT / 8) * 128, (COUT / 8) * 128, 128);
-        mma_bf16(taddr, da, db, IDESC, (s > 0 || q > 0) ? 1u : 0u);
+      const uint32_t hbase = smem_u32(sm + buf * SB), wbase = hbase + HALO_BYTES;
+      const uint32_t acc = taddr + (uint32_t)((lt & 1) * HT_Z * NC);
+      const uint64_t a0 = sdesc(hbase, HPLANE, HX * 16), b0 = sdesc(wbase, NC * 16, 128);
+#pragma unroll 1
+      for (int t = 0; t < 27; ++t) {
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        const uint64_t db = b0 + (uint64_t)((t * NC * 32) >> 4);
+#pragma unroll
+        for (int zp = 0; zp < HT_Z; ++zp) {
+          const uint32_t off = (uint32_t)((((zp + dz) * HY + dy) * HX + dx) * 16);
+          mma_bf16(acc + zp * NC, a0 + (uint64_t)(off >> 4), db, IDESC,
+                   (c > 0 || t > 0) ? 1u : 0u);
+        }
       }
-      mma_commit(&mbar[buf]);
+      mma_commit(&done[buf]);
+    }
+    committed = s + 1;
+    if (s >= 1) {
+      // MMAs of stage s-1 are done: its buffer is free and, if it ended a
+      // tile, that tile's accumulators are final
+      if (__all_sync(0xffffffffu, mbar_wait(&done[(s - 1) % NS], (uint32_t)(((s - 1) / NS) & 1))))
+        waited_done = s;
+      else
+        abort_flag = 1;
+      if (!abort_flag && (s - 1) % a.nchunk == a.nchunk - 1) epilogue((s - 1) / a.nchunk);
+    }
+    if (!abort_flag && produced < nst) {
+      produce(produced);
+      ++produced;
     }
   }
-  // wait for the last stage's MMAs (the commit tracks all earlier ones too)
-  if (ok) {
-    const int last = nst - 1;
-    bool done = mbar_wait(&mbar[last % NSTAGE], (uint32_t)((last / NSTAGE) & 1));
-    if (!done) abort_flag = 1;
+  if (!abort_flag && nst > 0) {
+    if (__all_sync(0xffffffffu, mbar_wait(&done[(nst - 1) % NS], (uint32_t)(((nst - 1) / NS) & 1))))
+      waited_done = nst;
+    else
+      abort_flag = 1;
+    if (!abort_flag) epilogue(nst / a.nchunk - 1);
   }
   __syncthreads();
-  tc_fence_after();
   if (abort_flag) {
-    if (tid == 0) atomicExch(err, 1);
-  } else {
-    const bool inside = vx < g.nx && vy < g.ny && vz < g.nz;
-    const size_t vox = ((size_t)vz * g.ny + vy) * g.nx + vx;
-#pragma unroll
-    for (int c0 = 0; c0 < COUT; c0 += 16) {
-      float acc[16];
-      tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + c0, acc);
-      if (inside) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          float v = acc[q] + (bias ? bias[c0 + q] : 0.f);
-          acc[q] = relu ? fmaxf(v, 0.f) : v;
-        }
-        if (y32) {
-          float4 *o = reinterpret_cast<float4 *>(y32 + vox * COUT + c0);
-          for (int q = 0; q < 4; ++q) o[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-        } else {
-          __align__(16) bf16 hv[16];
-          for (int q = 0; q < 16; ++q) hv[q] = __float2bfloat16_rn(acc[q]);
-          uint4 *o = reinterpret_cast<uint4 *>(y + vox * COUT + c0);
-          o[0] = *reinterpret_cast<uint4 *>(&hv[0]);
-          o[1] = *reinterpret_cast<uint4 *>(&hv[8]);
-        }
-      }
-    }
+    // drain: copies still in flight into shared memory, MMAs still reading it
+    for (int s = waited_full; s < produced; ++s) mbar_wait(&full[s % NS], (uint32_t)((s / NS) & 1));
+    for (int s = waited_done; s < committed; ++s) mbar_wait(&done[s % NS], (uint32_t)((s / NS) & 1));
+    if (tid == 0) atomicExch(a.err, 1);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_free(taddr, TM);
+}
+
+// packed weight image of a convolution for k_conv3d_halo:
+// img[sp][c][t][kg][co/8][co%8][ci%8] = W(co = sp*NC + co_l, t, ci = 16c + 8kg + ci%8)
+// with W(co, t, ci) = src[co][t][ci] (src [cout][27][cin]) or, for the input
+// gradient (flip != 0), W(co, t, ci) = src[ci][26 - t][co] (src [cin'][27][cout'] of the layer).
+template <typename S>
+__global__ void k_pack_img(const S *__restrict__ src, int cout, int cin, int flip, int nc,
+                           bf16 *__restrict__ img) {
+  const int nchunk = cin / 16;
+  const size_t total = (size_t)cout * 27 * cin;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t r = e;
+    const int cil = (int)(r % 8);
+    r /= 8;
+    const int col = (int)(r % 8);
+    r /= 8;
+    const int cog = (int)(r % (nc / 8));
+    r /= nc / 8;
+    const int kg = (int)(r % 2);
+    r /= 2;
+    const int t = (int)(r % 27);
+    r /= 27;
+    const int c = (int)(r % nchunk);
+    const int sp = (int)(r / nchunk);
+    const int co = sp * nc + cog * 8 + col, ci = 16 * c + 8 * kg + cil;
+    const float v = flip ? (float)src[((size_t)ci * 27 + (26 - t)) * cout + co]
+                         : (float)src[((size_t)co * 27 + t) * cin + ci];
+    img[e] = __float2bfloat16_rn(v);
+  }
 }
 
 
@@ -636,6 +805,76 @@ __global__ void k_loss(const float *__restrict__ q, const float *__restrict__ t,
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// ------------------------------------------------------ energy-norm loss
+// A x = sum over faces of beta_f (x_c - x_nb) (positive semidefinite), the
+// ghost-fluid faces rebuilt from the input's phi channel f0 = phi / 4h: one
+// fluid gives 1/rho, an interface face the series formula with
+// theta = |f0_a| / (|f0_a| + |f0_b|) (h cancels).
+struct EnergyGeom {
+  int nx, ny, nz, per;
+  float rl, rg, irl, irg;
+};
+__device__ __forceinline__ float e_beta(float fa, float fb, const EnergyGeom &e) {
+  const bool ga = __float_as_int(fa) > 0, gb = __float_as_int(fb) > 0;
+  if (ga == gb) return ga ? e.irg : e.irl;
+  const float ra = ga ? e.rg : e.rl, rb = gb ? e.rg : e.rl;
+  const float th = fabsf(fa) / (fabsf(fa) + fabsf(fb));
+  return 1.f / (th * ra + (1.f - th) * rb);
+}
+
+// Aq, At and block partials of q.At, q.Aq, t.At (three arrays of gridDim.x)
+__global__ void k_energy_apply(const float *__restrict__ q, const float *__restrict__ t,
+                               const bf16 *__restrict__ in16, EnergyGeom e, size_t n,
+                               float *__restrict__ aq, float *__restrict__ at,
+                               double *__restrict__ part) {
+  double sa = 0.0, sc = 0.0, sd = 0.0;
+  for (size_t v = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; v < n;
+       v += (size_t)gridDim.x * RED_THREADS) {
+    const int i = (int)(v % e.nx), j = (int)((v / e.nx) % e.ny), k = (int)(v / ((size_t)e.nx * e.ny));
+    const float fc = __bfloat162float(in16[v * 16]), qc = q[v], tc = t[v];
+    float sq = 0.f, st = 0.f;
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+      const int ax = dir >> 1, hi = dir & 1;
+      const int c = ax == 0 ? i : (ax == 1 ? j : k);
+      const int m = ax == 0 ? e.nx : (ax == 1 ? e.ny : e.nz);
+      const bool wall = !(e.per & (1 << ax)) && (hi ? c == m - 1 : c == 0);
+      if (wall) continue;
+      const int cn = hi ? (c == m - 1 ? 0 : c + 1) : (c == 0 ? m - 1 : c - 1);
+      const int ii = ax == 0 ? cn : i, jj = ax == 1 ? cn : j, kk = ax == 2 ? cn : k;
+      const size_t nb = ((size_t)kk * e.ny + jj) * e.nx + ii;
+      const float fn = __bfloat162float(in16[nb * 16]);
+      const float w = hi ? e_beta(fc, fn, e) : e_beta(fn, fc, e);
+      sq = fmaf(w, qc - q[nb], sq);
+      st = fmaf(w, tc - t[nb], st);
+    }
+    aq[v] = sq;
+    at[v] = st;
+    sa += (double)qc * st;
+    sc += (double)qc * sq;
+    sd += (double)tc * st;
+  }
+  double r = block_sumd(sa);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+  r = block_sumd(sc);
+  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = r;
+  r = block_sumd(sd);
+  if (threadIdx.x == 0) part[2 * gridDim.x + blockIdx.x] = r;
+}
+
+// gq = dL/dq = (2a / (c d)) (alpha Aq - At), alpha = a / c, with
+// (a, c, d) = (q.At, q.Aq, t.At) in acd; the loss 1 - a^2 / (c d) -> loss
+__global__ void k_energy_grad(const float *__restrict__ aq, const float *__restrict__ at,
+                              size_t n, const double *__restrict__ acd, float *__restrict__ gq,
+                              double *__restrict__ loss) {
+  const double a = acd[0], c = fmax(acd[1], 1e-300), d = fmax(acd[2], 1e-300);
+  const float coef = (float)(2.0 * a / (c * d)), alpha = (float)(a / c);
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n;
+       v += (size_t)gridDim.x * blockDim.x)
+    gq[v] = coef * fmaf(alpha, aq[v], -at[v]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *loss = 1.0 - a * a / (c * d);
+}
+
 // Adam, bias-corrected (step >= 1)
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                        float *__restrict__ v, size_t n, float lr, float b1, float b2, float eps,
@@ -648,20 +887,6 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
     m[i] = mi;
     v[i] = vi;
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-  }
-}
-
-// BF16 copies of one layer's weights: forward [co][t][ci] and the flipped,
-// transposed set that turns the input gradient into a forward convolution:
-// wd[ci][t][co] = w[co][26 - t][ci]
-__global__ void k_pack(const float *__restrict__ w, int cout, int cin, bf16 *__restrict__ wf,
-                       bf16 *__restrict__ wd) {
-  const int total = cout * 27 * cin;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int ci = e % cin, t = (e / cin) % 27, co = e / (27 * cin);
-    const bf16 b = __float2bfloat16_rn(w[e]);
-    wf[e] = b;
-    if (wd) wd[((size_t)ci * 27 + (26 - t)) * cout + co] = b;
   }
 }
 
@@ -716,9 +941,11 @@ struct Layer {
   int cout, cin, level;  // level: 0 = finest
   int ca, cb, up_a;      // input composition
   size_t woff, boff;     // offsets of weights and bias in the parameter vector
-  bf16 *wf = nullptr, *wd = nullptr;
+  bf16 *img_f = nullptr;  // packed weights of the forward convolution
+  bf16 *img_d = nullptr;  // packed flipped weights (input-gradient convolution)
   bf16 *y = nullptr;     // output activation
   bf16 *gy = nullptr;    // gradient w.r.t. the output
+  CUtensorMap map_a, map_b, map_d;  // TMA maps of the inputs and of the masked gradient
 };
 
 }  // namespace
@@ -741,6 +968,9 @@ struct mp_net {
   float *cpart = nullptr;         // per-channel partial sums
   double *dpart = nullptr, *dscal = nullptr, *hscal = nullptr;
   int *err = nullptr;
+  int loss_kind = 0;              // 0: gauge-free MSE; 1: energy norm
+  EnergyGeom eg{};                // operator of the energy-norm loss
+  float *e_aq = nullptr, *e_at = nullptr;
   std::vector<void *> allocs;
 };
 
@@ -759,32 +989,116 @@ mp_status nalloc(mp_net *net, T **p, size_t count) {
 }
 
 bool cout_ok(int c) { return c == 16 || c == 32 || c == 48 || c == 64 || c == 96 || c == 128; }
+// output channels per CTA of k_conv3d_halo (96 and 128 are split in two)
+int nc_of(int cout) { return cout <= 64 ? cout : cout / 2; }
 
-template <int COUT>
-mp_status launch_fwd(const ConvGeom &g, const bf16 *xa, const bf16 *xb, const bf16 *w,
-                     const float *bias, bf16 *y, float *y32, int relu, int *err, cudaStream_t st) {
-  const int smem = conv_smem_bytes<COUT>();
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// TMA map of a channels-last BF16 tensor (nz, ny, nx, C) with the halo box
+// (8 channels, HX, HY, HZ); out-of-range elements read as zero
+mp_status make_map(CUtensorMap *m, const bf16 *base, int C, int nx, int ny, int nz) {
+  std::memset(m, 0, sizeof(*m));
+  if (!base) return MP_OK;  // unused input
+  EncodeTiled enc = encode_fn();
+  if (!enc) return MP_ERR_CUDA;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)nx * C * 2,
+                                 (cuuint64_t)ny * nx * C * 2};
+  const cuuint32_t box[4] = {8, HX, HY, HZ};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  if (enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return MP_ERR_INVALID_ARG;
+  return MP_OK;
+}
+
+// maps of a convolution's inputs: xa (unless read through upsampling) and xb
+mp_status make_maps(const ConvGeom &g, const bf16 *xa, const bf16 *xb, CUtensorMap *ma,
+                    CUtensorMap *mb) {
+  NCKS(make_map(ma, g.up_a ? nullptr : xa, g.ca, g.nx, g.ny, g.nz));
+  NCKS(make_map(mb, g.cb > 0 ? xb : nullptr, g.cb, g.nx, g.ny, g.nz));
+  return MP_OK;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 1;
+    }
+  }
+  return n;
+}
+
+template <int NC>
+mp_status launch_halo(const ConvGeom &g, const CUtensorMap &ma, const CUtensorMap &mb,
+                      const bf16 *xa, const bf16 *wimg, const float *bias, int cout, bf16 *y,
+                      float *y32, int relu, int *err, cudaStream_t st) {
+  const int smem = h_smem_bytes<NC>();
   static bool attr = false;
   if (!attr) {
-    NCK(cudaFuncSetAttribute(k_conv3d_fwd<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    NCK(cudaFuncSetAttribute(k_conv3d_halo<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem));
     attr = true;
   }
-  dim3 grid((g.nx + 7) / 8, (g.ny + 3) / 4, (g.nz + 3) / 4);
-  k_conv3d_fwd<COUT><<<grid, CONV_THREADS, smem, st>>>(xa, xb, w, bias, y, y32, g, relu, err);
+  HaloArgs a;
+  a.xa = xa;
+  a.wimg = wimg;
+  a.bias = bias;
+  a.y = y;
+  a.y32 = y32;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.ca = g.ca;
+  a.up_a = g.up_a;
+  a.cout = cout;
+  a.relu = relu;
+  a.tiles_x = (g.nx + 7) / 8;
+  a.tiles_y = (g.ny + 15) / 16;
+  const int tiles_z = (g.nz + HT_Z - 1) / HT_Z;
+  a.ntiles = a.tiles_x * a.tiles_y * tiles_z;
+  a.nsplit = cout / NC;
+  a.nchunk = g.cin / 16;
+  a.err = err;
+  const long items = (long)a.ntiles * a.nsplit;
+  long grid = std::min<long>(items, (long)sm_count() * h_ctas_per_sm<NC>());
+  grid = std::max<long>(a.nsplit, grid - grid % a.nsplit);
+  k_conv3d_halo<NC><<<(int)grid, CONV_THREADS, smem, st>>>(ma, mb, a);
   NCK(cudaGetLastError());
   return MP_OK;
 }
 
-mp_status conv_fwd(const ConvGeom &g, const bf16 *xa, const bf16 *xb, const bf16 *w,
-                   const float *bias, int cout, bf16 *y, float *y32, int relu, int *err,
-                   cudaStream_t st) {
-  switch (cout) {
-    case 16: return launch_fwd<16>(g, xa, xb, w, bias, y, y32, relu, err, st);
-    case 32: return launch_fwd<32>(g, xa, xb, w, bias, y, y32, relu, err, st);
-    case 48: return launch_fwd<48>(g, xa, xb, w, bias, y, y32, relu, err, st);
-    case 64: return launch_fwd<64>(g, xa, xb, w, bias, y, y32, relu, err, st);
-    case 96: return launch_fwd<96>(g, xa, xb, w, bias, y, y32, relu, err, st);
-    case 128: return launch_fwd<128>(g, xa, xb, w, bias, y, y32, relu, err, st);
+// forward convolution through k_conv3d_halo; wimg packed by k_pack_img for nc_of(cout)
+mp_status conv_fwd(const ConvGeom &g, const CUtensorMap &ma, const CUtensorMap &mb,
+                   const bf16 *xa, const bf16 *wimg, const float *bias, int cout, bf16 *y,
+                   float *y32, int relu, int *err, cudaStream_t st) {
+  switch (nc_of(cout)) {
+    case 16: return launch_halo<16>(g, ma, mb, xa, wimg, bias, cout, y, y32, relu, err, st);
+    case 32: return launch_halo<32>(g, ma, mb, xa, wimg, bias, cout, y, y32, relu, err, st);
+    case 48: return launch_halo<48>(g, ma, mb, xa, wimg, bias, cout, y, y32, relu, err, st);
+    case 64: return launch_halo<64>(g, ma, mb, xa, wimg, bias, cout, y, y32, relu, err, st);
   }
   return MP_ERR_INVALID_ARG;
 }
@@ -869,10 +1183,27 @@ void layer_inputs(const mp_net *net, int i, const bf16 **a, const bf16 **b) {
 mp_status pack_all(mp_net *net) {
   for (int i = 0; i < NLAYER; ++i) {
     Layer &l = net->L[i];
-    k_pack<<<grid_for((size_t)l.cout * 27 * l.cin), 256, 0, net->st>>>(
-        net->param + l.woff, l.cout, l.cin, l.wf, i == 0 ? nullptr : l.wd);
+    const size_t nw = (size_t)l.cout * 27 * l.cin;
+    k_pack_img<float><<<grid_for(nw), 256, 0, net->st>>>(net->param + l.woff, l.cout, l.cin, 0,
+                                                         nc_of(l.cout), l.img_f);
+    if (i > 0)  // input gradient: output channels l.cin, input channels l.cout
+      k_pack_img<float><<<grid_for(nw), 256, 0, net->st>>>(net->param + l.woff, l.cin, l.cout, 1,
+                                                           nc_of(l.cin), l.img_d);
   }
   NCK(cudaGetLastError());
+  return MP_OK;
+}
+
+// TMA maps of every layer's inputs (fixed buffers) and of the masked gradient
+mp_status make_all_maps(mp_net *net) {
+  for (int i = 0; i < NLAYER; ++i) {
+    Layer &l = net->L[i];
+    const bf16 *a, *b;
+    layer_inputs(net, i, &a, &b);
+    NCKS(make_maps(geom(net, l), a, b, &l.map_a, &l.map_b));
+    NCKS(make_map(&l.map_d, net->gz, l.cout, net->nx[l.level], net->ny[l.level],
+                  net->nz[l.level]));
+  }
   return MP_OK;
 }
 
@@ -887,8 +1218,8 @@ mp_status forward(mp_net *net) {
     }
     const bf16 *a, *b;
     layer_inputs(net, i, &a, &b);
-    NCKS(conv_fwd(geom(net, l), a, b, l.wf, net->param + l.boff, l.cout, l.y, nullptr, 1,
-                  net->err, net->st));
+    NCKS(conv_fwd(geom(net, l), l.map_a, l.map_b, a, l.img_f, net->param + l.boff, l.cout, l.y,
+                  nullptr, 1, net->err, net->st));
   }
   k_head_fwd<<<grid_for(net->nv[0]), 256, 0, net->st>>>(
       net->L[13].y, net->param + net->head_w, net->param + net->head_b, net->nv[0], CH[0],
@@ -933,8 +1264,8 @@ mp_status backward(mp_net *net) {
     gd.cin = l.cout;
     const bool plain = !(i == 2 || i == 4 || i == 6 || i == 8 || i == 10 || i == 12);
     bf16 *dst = plain ? net->L[i - 1].gy : net->gx;
-    NCKS(conv_fwd(gd, net->gz, nullptr, l.wd, nullptr, l.cin, dst, nullptr, 0, net->err,
-                  net->st));
+    NCKS(conv_fwd(gd, l.map_d, l.map_d, net->gz, l.img_d, nullptr, l.cin, dst, nullptr, 0,
+                  net->err, net->st));
     const int lv = l.level;
     if (i == 12 || i == 10 || i == 8) {  // decoder input: [up(coarse) | skip]
       const int coarse = i == 12 ? 11 : (i == 10 ? 9 : 7);
@@ -963,18 +1294,24 @@ mp_status mp_conv3d_fwd(int nx, int ny, int nz, const void *xa, int ca, int up_a
       cb < 0 || cb % 16 || (cb > 0 && !xb) || !w || !cout_ok(cout) || (!y && !y32) ||
       (up_a && (nx % 2 || ny % 2 || nz % 2)))
     return MP_ERR_INVALID_ARG;
-  int *err = nullptr;
-  NCK(cudaMallocAsync((void **)&err, sizeof(int), (cudaStream_t)stream));
-  NCK(cudaMemsetAsync(err, 0, sizeof(int), (cudaStream_t)stream));
+  cudaStream_t st = (cudaStream_t)stream;
   ConvGeom g{nx, ny, nz, ca, cb, up_a ? 1 : 0, ca + cb};
-  mp_status s = conv_fwd(g, (const bf16 *)xa, (const bf16 *)xb, (const bf16 *)w, bias, cout,
-                         (bf16 *)y, y32, relu, err, (cudaStream_t)stream);
+  CUtensorMap ma, mb;
+  NCKS(make_maps(g, (const bf16 *)xa, (const bf16 *)xb, &ma, &mb));
+  const size_t nw = (size_t)cout * 27 * g.cin;
+  int *err = nullptr;
+  bf16 *img = nullptr;
+  NCK(cudaMallocAsync((void **)&err, sizeof(int), st));
+  NCK(cudaMallocAsync((void **)&img, nw * sizeof(bf16), st));
+  NCK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  k_pack_img<bf16><<<grid_for(nw), 256, 0, st>>>((const bf16 *)w, cout, g.cin, 0, nc_of(cout), img);
+  mp_status s = conv_fwd(g, ma, mb, (const bf16 *)xa, img, bias, cout, (bf16 *)y, y32, relu, err,
+                         st);
   int h = 0;
-  if (s == MP_OK) {
-    NCK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
-  }
-  NCK(cudaFreeAsync(err, (cudaStream_t)stream));
-  NCK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (s == MP_OK) NCK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NCK(cudaFreeAsync(img, st));
+  NCK(cudaFreeAsync(err, st));
+  NCK(cudaStreamSynchronize(st));
   if (s != MP_OK) return s;
   return h ? MP_ERR_TIMEOUT : MP_OK;
 }
@@ -1043,8 +1380,8 @@ mp_status mp_net_create(mp_net_handle *out, int nx, int ny, int nz, void *stream
     const size_t nv = net->nv[l.level];
     wpart = std::max(wpart, wgrad_partial_floats(geom(net, l), l.cout));
     maxact = std::max(maxact, nv * (size_t)std::max(l.cin, l.cout));
-    if ((s = nalloc(net, &l.wf, (size_t)l.cout * 27 * l.cin)) != MP_OK) break;
-    if ((s = nalloc(net, &l.wd, (size_t)l.cout * 27 * l.cin)) != MP_OK) break;
+    if ((s = nalloc(net, &l.img_f, (size_t)l.cout * 27 * l.cin)) != MP_OK) break;
+    if ((s = nalloc(net, &l.img_d, (size_t)l.cout * 27 * l.cin)) != MP_OK) break;
     if ((s = nalloc(net, &l.y, nv * l.cout)) != MP_OK) break;
     s = nalloc(net, &l.gy, nv * l.cout);
   }
@@ -1067,8 +1404,10 @@ mp_status mp_net_create(mp_net_handle *out, int nx, int ny, int nz, void *stream
   if (s == MP_OK) s = nalloc(net, &net->gq, net->nv[0]);
   if (s == MP_OK) s = nalloc(net, &net->wpart, wpart);
   if (s == MP_OK) s = nalloc(net, &net->cpart, (net->nv[0] / 1024 + 64) * 130);
-  if (s == MP_OK) s = nalloc(net, &net->dpart, RED_BLOCKS + 8);
-  if (s == MP_OK) s = nalloc(net, &net->dscal, 8);
+  if (s == MP_OK) s = nalloc(net, &net->dpart, 3 * RED_BLOCKS + 8);
+  if (s == MP_OK) s = nalloc(net, &net->dscal, 16);
+  if (s == MP_OK) s = nalloc(net, &net->e_aq, net->nv[0]);
+  if (s == MP_OK) s = nalloc(net, &net->e_at, net->nv[0]);
   if (s == MP_OK) s = nalloc(net, &net->err, 4);
   if (s == MP_OK && cudaMallocHost((void **)&net->hscal, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -1083,6 +1422,7 @@ mp_status mp_net_create(mp_net_handle *out, int nx, int ny, int nz, void *stream
       s = MP_ERR_CUDA;
   }
   if (s == MP_OK) s = pack_all(net);
+  if (s == MP_OK) s = make_all_maps(net);
   if (s == MP_OK && cudaStreamSynchronize(net->st) != cudaSuccess) s = MP_ERR_CUDA;
   if (s != MP_OK) {
     mp_net_destroy(net);
@@ -1118,6 +1458,21 @@ mp_status mp_net_get_params(mp_net_handle net, float *p) {
   NCK(cudaMemcpyAsync(p, net->param, net->nparam * sizeof(float), cudaMemcpyDeviceToDevice,
                       net->st));
   NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_set_loss(mp_net_handle net, int kind, double rho_l, double rho_g,
+                          const mp_bc bc[3]) {
+  if (!net || !(kind == 0 || kind == 1) || !(rho_l > 0.0) || !(rho_g > 0.0) || !bc)
+    return MP_ERR_INVALID_ARG;
+  int per = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (bc[a] != MP_BC_PERIODIC && bc[a] != MP_BC_NEUMANN) return MP_ERR_INVALID_ARG;
+    if (bc[a] == MP_BC_PERIODIC) per |= 1 << a;
+  }
+  net->loss_kind = kind;
+  net->eg = EnergyGeom{net->nx[0], net->ny[0], net->nz[0], per, (float)rho_l, (float)rho_g,
+                       (float)(1.0 / rho_l), (float)(1.0 / rho_g)};
   return MP_OK;
 }
 
@@ -1224,9 +1579,19 @@ mp_status mp_net_train_step(mp_net_handle net, const float *target, float lr, in
   k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
   k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(target, n, 0, net->dpart);
   k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 1);
-  k_loss<<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, target, n, net->dscal, net->gq,
-                                                 net->dpart);
-  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 2);
+  if (net->loss_kind == 0) {
+    k_loss<<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, target, n, net->dscal, net->gq,
+                                                   net->dpart);
+    k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 2);
+  } else {
+    k_energy_apply<<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, target, net->in16, net->eg, n,
+                                                           net->e_aq, net->e_at, net->dpart);
+    for (int q = 0; q < 3; ++q)
+      k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart + q * RED_BLOCKS, RED_BLOCKS,
+                                               net->dscal + 8 + q);
+    k_energy_grad<<<grid_for(n), 256, 0, net->st>>>(net->e_aq, net->e_at, n, net->dscal + 8,
+                                                    net->gq, net->dscal + 2);
+  }
   NCKS(backward(net));
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);
@@ -1237,7 +1602,7 @@ mp_status mp_net_train_step(mp_net_handle net, const float *target, float lr, in
   NCK(cudaMemcpyAsync(net->hscal, net->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost,
                       net->st));
   NCKS(check_err(net));
-  if (loss_out) *loss_out = net->hscal[0] / (double)n;
+  if (loss_out) *loss_out = net->loss_kind == 0 ? net->hscal[0] / (double)n : net->hscal[0];
   return MP_OK;
 }
 

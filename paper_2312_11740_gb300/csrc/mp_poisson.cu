@@ -419,6 +419,65 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
   return MP_OK;
 }
 
+// Mixed-precision PCG with reliable updates.  The Krylov iteration (V-cycle
+// preconditioner, operator, vector updates) runs in FP32 on a correction e32
+// and residual r32.  Whenever the recurrence residual has fallen by
+// inner_rtol since the last true residual (or after inner_max iterations),
+// the correction is added to the FP64 solution p and r32 is replaced by the
+// true FP64 residual bt - At p (rounded to FP32).  The search direction is
+// kept across replacements (no restart), so the iteration count stays close
+// to that of FP64 PCG while every stencil sweep moves 4-byte values.
+// On entry r32 holds the true residual of p with norm rn.
+mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int maxit, int *iters,
+                    int *outer, std::vector<double> *hist, double inv_b) {
+  Level &l0 = hd->L[0];
+  const mp_opts &o = hd->opts;
+  const size_t n = hd->n;
+  const double nsz = (double)n * sizeof(float);
+  float *e = hd->e32, *r = hd->r32, *z = hd->z32, *dv = hd->d32, *q = hd->q32;
+  int it = 0, nrep = 0, since = 0;
+  double rn_rep = rn, rec = rn;
+  mp_status st = MP_OK;
+  CK(cudaMemsetAsync(e, 0, n * sizeof(float), hd->st));
+  while (true) {
+    if (since > 0 && (rec <= std::fmax(o.inner_rtol * rn_rep, 0.5 * tol_abs) ||
+                      since >= o.inner_max || it >= maxit)) {
+      // reliable update: p += e32 (e32 = 0), r32 = bt - At p from FP64
+      LAUNCH(hd, K_ADDF32, 0, n * 24.0, k_add_f32, VEC_BLOCKS, VEC_THREADS, p, e, n);
+      LAUNCH(hd, K_RESIDMIX, 0, n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b, r,
+             l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
+      CKS(read_scalars(hd));
+      rn = std::sqrt(hd->scal_h[S_RR]);
+      rn_rep = rec = rn;
+      since = 0;
+      ++nrep;
+      if (hist) hist->push_back(rn * inv_b);
+    }
+    if (bad(rec)) { st = MP_ERR_DIVERGED; break; }
+    if (since == 0 && rn <= tol_abs) break;  // converged on a true residual
+    if (it >= maxit) { st = MP_ERR_NOT_CONVERGED; break; }
+    CKS(run_vcycle<float>(hd, r, z));
+    LAUNCH(hd, K_DOT32, 0, 2.0 * nsz, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, z, n, hd->partial);
+    CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
+    LAUNCH(hd, K_XPBY32, 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<float>, VEC_BLOCKS, VEC_THREADS,
+           dv, z, n, hd->scal, it == 0);
+    LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot<float>, zgrid(l0.d), kBlock, dv, q, l0.bx32,
+           l0.by32, l0.bz32, (float *)nullptr, l0.d, zper_of(l0.d), hd->partial);
+    CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
+    LAUNCH(hd, K_AXPY32, 0, 6.0 * nsz, k_axpy2<float>, VEC_BLOCKS, VEC_THREADS, e, r, dv, q, n,
+           hd->scal, hd->partial);
+    CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
+    ++it;
+    ++since;
+    CKS(read_scalars(hd));
+    rec = std::sqrt(hd->scal_h[S_RR]);
+  }
+  *iters = it;
+  *outer = nrep;
+  return st;
+}
+
 // Stationary V-cycle iteration: x += V(r); r = bt - At x.
 template <typename T>
 mp_status stationary(mp_poisson *hd, T *x, const T *bt, T *r, T *z, double tol_abs, int maxit,
@@ -503,11 +562,12 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     if (hist) hist->push_back(0.0);
     return MP_OK;
   }
+  // the residual of a learned guess, once formed, is the solve's initial residual
+  bool have_r = false;
   if (o.initial_guess == 2) {
-    // learned guess: features from phi and the assembled rhs, network,
-    // p0 = s c (q - mean q); kept only if its FP64 residual is below ||b||
-    // the network gives the shape q; its scale is the energy-optimal
-    // alpha = (q . bt) / (q . At q) (minimises the A-norm error of alpha q)
+    // learned guess: features from phi and the assembled rhs, network output q
+    // (the shape), scaled by the energy-optimal alpha = (q . bt) / (q . At q),
+    // which minimises the A-norm error of alpha q; kept per net_check
     double s = 1.0;
     CK(cudaStreamSynchronize(hd->st));
     CKS(mp_net_set_stream(hd->net, hd->st));
@@ -524,14 +584,20 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     double alpha = hd->scal_h[S_RZ] / hd->scal_h[S_TMP];
     if (!std::isfinite(alpha)) alpha = 0.0;
     LAUNCH(hd, K_SCALE, 0, hd->n * 16.0, k_scale, VEC_BLOCKS, VEC_THREADS, p, p, hd->n, alpha);
-    LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b,
-           hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+    if (o.precision == 0)
+      LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b,
+             hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+    else
+      LAUNCH(hd, K_RESIDMIX, 0, hd->n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b,
+             hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
     CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
     CKS(read_scalars(hd));
     const double rnet = std::sqrt(hd->scal_h[S_RR]);
     hd->stats.net_relres = rnet / hd->bnorm;
-    if (rnet < hd->bnorm) {
+    const bool keep = o.net_check == 0 ? rnet < hd->bnorm : alpha != 0.0;
+    if (keep && std::isfinite(rnet)) {
       hd->stats.used_net = 1;
+      have_r = true;
     } else {
       CK(cudaMemsetAsync(p, 0, hd->n * sizeof(double), hd->st));
       zero = 1;
@@ -542,10 +608,12 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
   mp_status st = MP_OK;
   int iters = 0;
   if (o.precision == 0) {
-    LAUNCH(hd, K_RESID64, 0, hd->n * (zero ? 16.0 : 56.0), k_residual<double>, zgrid(l0.d),
-           kBlock, p, hd->b, hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial,
-           zero);
-    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
+    if (!have_r) {
+      LAUNCH(hd, K_RESID64, 0, hd->n * (zero ? 16.0 : 56.0), k_residual<double>, zgrid(l0.d),
+             kBlock, p, hd->b, hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d),
+             hd->partial, zero);
+      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
+    }
     CKS(read_scalars(hd));
     hd->stats.r0 = std::sqrt(hd->scal_h[S_RR]) * inv_b;
     if (hist) hist->push_back(hd->stats.r0);
@@ -559,10 +627,12 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     hd->stats.outer_steps = iters;
   } else {
     // FP64 iterative refinement around an FP32 inner solve
-    LAUNCH(hd, K_RESIDMIX, 0, hd->n * (zero ? 12.0 : 52.0), k_residual_mixed, zgrid(l0.d),
-           kBlock, p, hd->b, hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d),
-           hd->partial, zero);
-    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
+    if (!have_r) {
+      LAUNCH(hd, K_RESIDMIX, 0, hd->n * (zero ? 12.0 : 52.0), k_residual_mixed, zgrid(l0.d),
+             kBlock, p, hd->b, hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d),
+             hd->partial, zero);
+      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
+    }
     CKS(read_scalars(hd));
     double rn = std::sqrt(hd->scal_h[S_RR]);
     hd->stats.r0 = rn * inv_b;
@@ -572,22 +642,20 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
       if (bad(rn)) { st = MP_ERR_DIVERGED; break; }
       if (rn <= tol_abs) { st = MP_OK; break; }
       if (total >= o.max_iters) { st = MP_ERR_NOT_CONVERGED; break; }
-      int inner = 0;
-      CK(cudaMemsetAsync(hd->e32, 0, hd->n * sizeof(float), hd->st));
       if (o.method == 0) {
-        double inner_tol = std::fmax(o.inner_rtol * rn, 0.25 * tol_abs);
-        int cap = std::min(o.inner_max, o.max_iters - total);
-        mp_status si = pcg<float>(hd, hd->e32, hd->r32, hd->z32, hd->d32, hd->q32, inner_tol,
-                                  cap, &inner, nullptr, 0.0);
-        if (si == MP_ERR_DIVERGED) { st = si; break; }
-        if (si != MP_OK && si != MP_ERR_NOT_CONVERGED) return si;
-      } else {
-        CKS(run_vcycle<float>(hd, hd->r32, hd->e32));
-        inner = 1;
+        // PCG with reliable updates (replaces the refinement loop)
+        int pit = 0, pout = 0;
+        st = pcg_mixed(hd, p, rn, tol_abs, o.max_iters, &pit, &pout, hist, inv_b);
+        total = pit;
+        outer = pout;
+        if (st != MP_OK && st != MP_ERR_NOT_CONVERGED && st != MP_ERR_DIVERGED) return st;
+        break;
       }
-      total += inner;
+      // stationary: one FP32 V-cycle per FP64 refinement step
+      CKS(run_vcycle<float>(hd, hd->r32, hd->e32));
+      total += 1;
       ++outer;
-      LAUNCH(hd, K_ADDF32, 0, hd->n * 20.0, k_add_f32, VEC_BLOCKS, VEC_THREADS, p, hd->e32,
+      LAUNCH(hd, K_ADDF32, 0, hd->n * 24.0, k_add_f32, VEC_BLOCKS, VEC_THREADS, p, hd->e32,
              hd->n);
       LAUNCH(hd, K_RESIDMIX, 0, hd->n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b,
              hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
@@ -615,7 +683,7 @@ bool valid_opts(const mp_opts &o) {
   return (o.precision == 0 || o.precision == 1) && (o.method == 0 || o.method == 1) &&
          o.initial_guess >= 0 && o.initial_guess <= 2 && o.max_iters >= 0 && o.nu1 >= 1 &&
          o.nu2 >= 1 && o.nu_growth >= 1 && o.nu_max >= 1 && o.inner_rtol > 0.0 &&
-         o.inner_rtol < 1.0 && o.inner_max >= 1;
+         o.inner_rtol < 1.0 && o.inner_max >= 1 && (o.net_check == 0 || o.net_check == 1);
 }
 
 void apply_nu(mp_poisson *hd) {
@@ -788,9 +856,10 @@ void mp_opts_default(mp_opts *o) {
   o->nu1 = 2;
   o->nu2 = 2;
   o->nu_growth = 2;
-  o->nu_max = 16;
+  o->nu_max = 8;
   o->inner_rtol = 1e-4;
   o->inner_max = 12;
+  o->net_check = 0;
   o->stream = nullptr;
 }
 
@@ -875,7 +944,7 @@ mp_status mp_poisson_project_step(mp_handle hd, double *ux, double *uy, double *
   if (s != MP_OK) return s;
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
-         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, hd->h);
+         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, 1.0 / hd->h);
   CKS(launch_ok());
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);
@@ -942,7 +1011,7 @@ mp_status mp_poisson_project(mp_handle hd, const double *p, double *ux, double *
   if (!hd || !p || !ux || !uy || !uz) return MP_ERR_INVALID_ARG;
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
-         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, hd->h);
+         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, 1.0 / hd->h);
   CKS(launch_ok());
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);

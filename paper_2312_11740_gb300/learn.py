@@ -7,12 +7,18 @@ relative residual 1e-10.  Stored on the GPU: the network's two input
 channels (BF16) and the target q = p / rms(p) (FP32, mean-free): the
 network learns the shape, the solver fits the scale.
 
-Training: Adam on the gauge-free MSE, one sample per step, every forward
-and backward operation in the library's tcgen05 kernels.
+Training: Adam, one sample per step, every forward and backward operation
+in the library's tcgen05 kernels.  Default loss: the energy norm of the
+best-scaled guess, 1 - (q.At)^2/((q.Aq)(t.At)) with A the ghost-fluid
+operator of the sample (the solver scales the network output by the
+energy-optimal factor, so this is the quantity the guess is judged by);
+--loss mse trains on the gauge-free mean squared error instead.
 
 Evaluation on held-out seeds: the number of solver iterations to 1e-10 from
-the zero guess and from the learned guess (with its residual check and
-zero-guess fallback), hence the iterations saved and the fallback rate.
+the zero guess and from the learned guess, with the residual check
+(net_check 0: kept only if ||b - A p0|| < ||b||) and with the energy check
+(net_check 1), hence the iterations saved and the fallback rates, and the
+guess's relative L2 and A-norm errors.
 
     python -m paper_2312_11740_gb300.learn --n 128 --train 2000 --epochs 3 \\
         --eval 200 --out net128.npz
@@ -105,10 +111,11 @@ def init_params(net, seed):
     return torch.from_numpy(vec).cuda()
 
 
-def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None):
+def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None, loss="energy"):
     """Adam over shuffled samples; returns the loss history (one per step)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     count = X.shape[0]
+    net.set_loss(1 if loss == "energy" else 0, RHO_L, RHO_G, BC)
     losses = []
     step = 0
     total = epochs * count
@@ -124,6 +131,13 @@ def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None):
             log("  epoch %d  mean loss %.4e  %.1fs" % (ep + 1, float(np.mean(losses[-count:])),
                                                        time.time() - t0))
     return losses
+
+
+def pg_forced(solver, rhs):
+    """The scaled network guess itself (energy check, no iterations)."""
+    solver.set_opts(initial_guess=2, max_iters=0, net_check=1)
+    pg, _, _ = solver.solve(rhs, tol=1e-10, allow_not_converged=True)
+    return pg
 
 
 def evaluate(net, seeds, n, precision=0, stream=None, log=print):
@@ -143,26 +157,43 @@ def evaluate(net, seeds, n, precision=0, stream=None, log=print):
         rhs = solver.divergence(*u)
         solver.set_opts(initial_guess=0)
         p0, it0, _ = solver.solve(rhs, tol=1e-10)
-        solver.set_opts(initial_guess=2, max_iters=0)
-        pg, _, _ = solver.solve(rhs, tol=1e-10, allow_not_converged=True)  # the guess itself
+        pg = pg_forced(solver, rhs)  # the scaled guess itself
         guess_err = float(torch.linalg.norm(pg - p0) / torch.linalg.norm(p0))
-        solver.set_opts(initial_guess=2, max_iters=200)
+        solver.set_opts(initial_guess=2, max_iters=200, net_check=0)
         p1, it1, _ = solver.solve(rhs, tol=1e-10)
         st = solver.stats()
         err = float(torch.linalg.norm(p1 - p0) / torch.linalg.norm(p0))
+        # the guess kept whenever it lowers the A-norm error (net_check = 1)
+        solver.set_opts(initial_guess=2, max_iters=200, net_check=1)
+        p2, it2, _ = solver.solve(rhs, tol=1e-10)
+        st2 = solver.stats()
+        solver.set_opts(net_check=0)
+        # A-norm error of the scaled guess relative to the solution's A-norm
+        e = pg - p0
+        relA = float(torch.sqrt(torch.abs((e * solver.apply(e)).sum()) /
+                                torch.abs((p0 * solver.apply(p0)).sum())))
         rows.append(dict(seed=seed, zero_iters=it0, net_iters=it1, used_net=st["used_net"],
                          net_relres=st["net_relres"], guess_rel_err=guess_err,
-                         diff_vs_zero_guess=err))
+                         diff_vs_zero_guess=err, energy_iters=it2,
+                         energy_used=st2["used_net"], guess_rel_energy_err=relA,
+                         diff_energy=float(torch.linalg.norm(p2 - p0) / torch.linalg.norm(p0))))
     mp_poisson_set_net(solver.handle, None)
     solver.close()
     zero = np.array([r["zero_iters"] for r in rows])
     lrn = np.array([r["net_iters"] for r in rows])
     used = np.array([r["used_net"] for r in rows])
+    en = np.array([r["energy_iters"] for r in rows])
     summary = dict(samples=len(rows), mean_zero_iters=float(zero.mean()),
                    mean_net_iters=float(lrn.mean()), iterations_saved=float((zero - lrn).mean()),
                    fallback_rate=float(1.0 - used.mean()),
                    median_net_relres=float(np.median([r["net_relres"] for r in rows])),
-                   median_guess_rel_err=float(np.median([r["guess_rel_err"] for r in rows])))
+                   median_guess_rel_err=float(np.median([r["guess_rel_err"] for r in rows])),
+                   median_guess_rel_energy_err=float(
+                       np.median([r["guess_rel_energy_err"] for r in rows])),
+                   energy_check_mean_iters=float(en.mean()),
+                   energy_check_iterations_saved=float((zero - en).mean()),
+                   energy_check_fallback_rate=float(
+                       1.0 - np.mean([r["energy_used"] for r in rows])))
     if log:
         log("  eval: " + json.dumps(summary))
     return summary, rows
@@ -179,6 +210,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lr-final", type=float, default=1e-4)
     ap.add_argument("--init-seed", type=int, default=7)
+    ap.add_argument("--loss", choices=("energy", "mse"), default="energy")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
     a = ap.parse_args(argv)
@@ -192,12 +224,13 @@ def main(argv=None):
     net.set_params(init_params(net, a.init_seed))
     print("train: %d epochs" % a.epochs, flush=True)
     t1 = time.time()
-    losses = train(net, X, Q, a.epochs, a.lr, a.init_seed, lr_final=a.lr_final)
+    losses = train(net, X, Q, a.epochs, a.lr, a.init_seed, lr_final=a.lr_final, loss=a.loss)
     t_train = time.time() - t1
     del X, Q
     torch.cuda.empty_cache()
     summary, rows = evaluate(net, list(range(a.eval_seed0, a.eval_seed0 + a.eval)), n)
-    report = dict(n=n, train_samples=a.train, epochs=a.epochs, lr=a.lr, lr_final=a.lr_final,
+    report = dict(n=n, loss=a.loss, train_samples=a.train, epochs=a.epochs, lr=a.lr,
+                  lr_final=a.lr_final,
                   data_seconds=t_data, train_seconds=t_train,
                   steps=len(losses), loss_first=float(np.mean(losses[:50])),
                   loss_last=float(np.mean(losses[-50:])), train_solver_iters=float(np.mean(its)),

@@ -121,6 +121,13 @@ class Net:
                                        _ptr(g, torch.float32)), "mp_net_backward")
         return g
 
+    def set_loss(self, kind, rho_l=1.0, rho_g=1e-3, bc=(0, 0, 1)):
+        """Training loss: 0 = gauge-free MSE, 1 = energy norm of the
+        best-scaled guess under the ghost-fluid operator of the input's phi."""
+        arr = (ctypes.c_int * 3)(*[int(b) for b in bc])
+        _check(_lib_().mp_net_set_loss(self.handle, int(kind), float(rho_l), float(rho_g), arr),
+               "mp_net_set_loss")
+
     def train_step(self, target, lr, step):
         loss = ctypes.c_double(0.0)
         _check(_lib_().mp_net_train_step(self.handle, _ptr(target, torch.float32, self.n),
