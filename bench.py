@@ -214,7 +214,8 @@ def run_mine(args, rank, world, local_rank):
     import synth
     from paper_2312_11740_gb300 import build as pkg_build
     pkg_build.build()
-    from paper_2312_11740_gb300 import Poisson, mp_poisson_project_step_host
+    from paper_2312_11740_gb300 import Net, Poisson, mp_poisson_project_step_host
+    from paper_2312_11740_gb300 import mp_poisson_set_net
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -233,18 +234,32 @@ def run_mine(args, rank, world, local_rank):
 
     stream = torch.cuda.Stream(device=dev)
     results = {}
-    modes = [(m, {"fp64": 0, "mixed": 1}[m]) for m in args.modes.split(",")]
-    for name, precision in modes:
+    # (precision, initial guess): fp64 and mixed from zero; learned = mixed with the
+    # packaged network (trained at 128^3) run on the half-resolution grid
+    mode_cfg = {"fp64": (0, 0), "mixed": (1, 0), "learned": (1, 2)}
+    names = args.modes.split(",")
+    headline = names[-1]
+    for name in names:
+        precision, guess = mode_cfg[name]
         us = fresh_u()
         ps = [torch.zeros(shape, dtype=torch.float64, device=dev) for _ in range(nsteps)]
         torch.cuda.synchronize()
         s = Poisson(phi, h, bc, w["rho_l"], w["rho_g"], w["sigma"], precision=precision,
                     stream=stream)
+        net = None
+        if guess == 2:
+            net = Net(n // 2, n // 2, n // 2, stream=stream)
+            net.load()
+            mp_poisson_set_net(s.handle, net)
+            s.set_opts(initial_guess=2)
+        used = []
 
         def step(k):
             s.set_geometry(phi, w["rho_l"], w["rho_g"], w["sigma"])
             it = s.project_step(*us[k], ps[k], tol=TOL)
-            return it, s.stats()["relres"]
+            st = s.stats()
+            used.append(st["used_net"])
+            return it, st["relres"]
 
         for k in range(args.warmup):
             step(k)
@@ -253,7 +268,8 @@ def run_mine(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        sampler = ClockSampler(local_rank) if name == "mixed" else None
+        sampler = ClockSampler(local_rank) if name == headline else None
+        n0 = net.launches() if net else 0
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         if sampler:
@@ -276,7 +292,8 @@ def run_mine(args, rank, world, local_rank):
             t = torch.tensor([ms], dtype=torch.float64, device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
-        launches = sum(e["launches"] for e in s.profile())
+        launches = sum(e["launches"] for e in s.profile()) + (net.launches() - n0 if net else 0)
+        used_timed = used[args.warmup:]
         # profiled pass on further inputs: every launch bracketed by CUDA events on
         # the library's stream (per-kernel durations for the roofline)
         s.set_profiling(True)
@@ -287,9 +304,9 @@ def run_mine(args, rank, world, local_rank):
         st = s.stats()
         results[name] = dict(ms=ms, iters=its, relres=max(relres), prof=prof, clocks=clocks,
                              levels=st["levels"], outer=st["outer_steps"], launches=launches,
-                             prof_steps=nprof)
+                             prof_steps=nprof, guess_used=used_timed)
         # end to end through the host-buffer entry point (pinned host memory)
-        if name == "mixed":
+        if name == headline:
             hx = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(3)]
             hp = torch.empty(shape, dtype=torch.float64).pin_memory()
             e2e_steps = max(2, min(args.steps, 5))
@@ -305,6 +322,9 @@ def run_mine(args, rank, world, local_rank):
                 mp_poisson_project_step_host(s.handle, hx[0], hx[1], hx[2], hp, TOL)
                 t_e2e += time.perf_counter() - t0
             results[name]["e2e"] = dict(steps=e2e_steps, seconds=t_e2e)
+        if net:
+            mp_poisson_set_net(s.handle, None)
+            net.close()
         s.close()
         del us, ps
         torch.cuda.empty_cache()
@@ -312,10 +332,10 @@ def run_mine(args, rank, world, local_rank):
     if rank != 0:
         return
     K = args.steps
-    mixed = results["mixed"]
+    mixed = results[headline]
     fp64 = results.get("fp64", mixed)
     value = world * K / (mixed["ms"] * 1e-3)
-    # dominant (kernel, level) by time in the mixed timed region
+    # dominant (kernel, level) by time in the headline mode's profiled steps
     prof = mixed["prof"]
     top = max(prof, key=lambda e: e["total_ms"])
     hbm, peak_kind = peaks()
@@ -334,23 +354,36 @@ def run_mine(args, rank, world, local_rank):
     total_prof_ms = sum(e["total_ms"] for e in prof)
 
     def mode_line(r):
-        return {"solves_per_s": world * K / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / K,
-                "iterations": r["iters"], "outer_steps_last": r["outer"],
-                "max_relres": r["relres"], "levels": r["levels"]}
+        d = {"solves_per_s": world * K / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / K,
+             "iterations": r["iters"], "outer_steps_last": r["outer"],
+             "max_relres": r["relres"], "levels": r["levels"]}
+        if any(r["guess_used"]):
+            d["learned_guess_kept"] = sum(r["guess_used"])
+        return d
+
+    modes_out = {k: mode_line(v) for k, v in results.items()}
+    if "fp64" in results:
+        for k in results:
+            if k != "fp64":
+                modes_out["%s_over_fp64" % k] = results["fp64"]["ms"] / results[k]["ms"]
+    forms = {"fp64": "FP64 MG-preconditioned CG",
+             "mixed": "mixed FP32/FP64 (FP32 MG-preconditioned CG with FP64 reliable updates)",
+             "learned": "mixed FP32/FP64 + learned initial guess (U-Net trained at 128^3, run "
+                        "on the half-resolution grid, energy-optimal scale, residual check)"}
 
     e2e = mixed["e2e"]
     nbytes = n * n * n * 8
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": mixed["ms"] / K, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32+f64", "learned": "f32+f64+bf16"}[headline],
+        "data": "synthetic",
         "config": {"workload": workload_desc(n), "grid": [n, n, n], "tol": TOL,
-                   "form": "mixed FP32/FP64 iterative refinement, MG-preconditioned CG",
+                   "form": forms[headline],
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2: each step touches ~2 GB of fields"},
-        "modes": {"mixed": mode_line(mixed), "fp64": mode_line(fp64),
-                  "mixed_over_fp64": fp64["ms"] / mixed["ms"]} if "fp64" in results else
-                 {"mixed": mode_line(mixed)},
+        "modes": modes_out,
         "roofline": {"kernel": "%s@L%d" % (top["name"], top["level"]), "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": peak_kind, "traffic": traffic,
@@ -374,7 +407,7 @@ def run_mine(args, rank, world, local_rank):
             line["cpu_baseline"] = {"value": None, "error": repr(ex)}
     if args.profile_out:
         with open(args.profile_out, "w") as f:
-            json.dump({"mixed": mixed["prof"], "fp64": fp64["prof"]}, f, indent=1)
+            json.dump({k: v["prof"] for k, v in results.items()}, f, indent=1)
     print(json.dumps(line), flush=True)
 
 
@@ -386,7 +419,8 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--n", type=int, default=256, help="grid cells per axis (default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--modes", default="fp64,mixed", help="comma list of fp64,mixed (mixed last)")
+    ap.add_argument("--modes", default="fp64,mixed,learned",
+                    help="comma list of fp64, mixed, learned; the last one is the headline value")
     ap.add_argument("--profile-out", default=None, help="write per-kernel profile JSON here")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -70,6 +70,10 @@ mp_status mp_net_dims(mp_net_handle net, int *nx, int *ny, int *nz);
 /* Number of FP32 parameters (all conv weights and biases, then the head). */
 size_t mp_net_param_count(mp_net_handle net);
 
+/* Kernels the network has launched on inference paths (features, forward,
+ * pressure) since creation. */
+unsigned long long mp_net_launches(mp_net_handle net);
+
 /* Copy the FP32 master parameters in or out (device pointers, param_count
  * floats); setting them also refreshes the BF16 copies the kernels use. */
 mp_status mp_net_set_params(mp_net_handle net, const float *params_dev);
@@ -82,6 +86,20 @@ mp_status mp_net_get_params(mp_net_handle net, float *params_dev);
  * s = rms(bt) (host).  h: cell size. */
 mp_status mp_net_features(mp_net_handle net, const double *phi_dev, const double *b_dev, double h,
                           double b_scale, double *s_out);
+
+/* mp_net_features for fields on a grid `factor` (1 or 2) times finer than the
+ * network's in every dimension (phi, b: device FP64 on that grid; h its cell
+ * size): with factor 2 the features are formed from the means of the 8
+ * children of every network cell (cell size 2h). */
+mp_status mp_net_features_at(mp_net_handle net, int factor, const double *phi_dev,
+                             const double *b_dev, double h, double b_scale, double *s_out);
+
+/* mp_net_pressure onto a grid `factor` (1 or 2) times finer: with factor 2,
+ * p = s (q - mean q) interpolated trilinearly (cell-centred weights 3/4 and
+ * 1/4 per axis; periodic axes wrap, wall axes clamp). p_dev: device FP64 on
+ * the fine grid. */
+mp_status mp_net_pressure_at(mp_net_handle net, int factor, const mp_bc bc[3], double s,
+                             double *p_dev);
 
 /* The two used input channels (f0, f1) as a compact BF16 array (N*2), out
  * of or into the network input; set_input2 zero-fills the other 14. */
@@ -133,12 +151,15 @@ mp_status mp_net_set_stream(mp_net_handle net, void *stream);
 
 void mp_net_destroy(mp_net_handle net);
 
-/* Use `net` (or NULL to detach) for initial_guess = 2 in mp_poisson_solve:
- * the solve builds the features from phi and b, runs the network, takes
+/* Use `net` (or NULL to detach) for initial_guess = 2 in mp_poisson_solve.
+ * The network grid equals the solver grid, or is half of it in every
+ * dimension (the guess is then formed on the coarser grid from restricted
+ * features and interpolated, see mp_net_features_at / mp_net_pressure_at).
+ * The solve builds the features from phi and b, runs the network, takes
  * p0 = alpha (q - mean q) with the energy-optimal alpha = (q.bt)/(q.A q),
  * and keeps it according to mp_opts.net_check (default: only if
  * ||b - A p0|| < ||b||; mp_stats.used_net, mp_stats.net_relres); otherwise
- * it starts from zero.  The grid must match. */
+ * it starts from zero. */
 mp_status mp_poisson_set_net(mp_handle hd, mp_net_handle net);
 
 #ifdef __cplusplus

@@ -103,6 +103,7 @@ SIGNATURES = {
     "mp_net_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _P]),
     "mp_net_dims": (_I, [_P, _IP, _IP, _IP]),
     "mp_net_param_count": (ctypes.c_size_t, [_P]),
+    "mp_net_launches": (ctypes.c_ulonglong, [_P]),
     "mp_net_set_params": (_I, [_P, _P]),
     "mp_net_get_params": (_I, [_P, _P]),
     "mp_net_features": (_I, [_P, _P, _P, _D, _D, _DP]),
@@ -115,6 +116,8 @@ SIGNATURES = {
     "mp_net_pressure": (_I, [_P, _D, _P]),
     "mp_net_set_stream": (_I, [_P, _P]),
     "mp_net_set_loss": (_I, [_P, _I, _D, _D, _IP]),
+    "mp_net_features_at": (_I, [_P, _I, _P, _P, _D, _D, _DP]),
+    "mp_net_pressure_at": (_I, [_P, _I, _IP, _D, _P]),
     "mp_net_make_target": (_I, [_P, _P, _P]),
     "mp_net_destroy": (None, [_P]),
 }

@@ -663,6 +663,75 @@ __global__ void k_features(const double *__restrict__ phi, const double *__restr
   }
 }
 
+// Fields of a grid twice as fine as the network's (nxc, nyc, nzc coarse
+// cells): the mean of the 8 children of phi and of b, in FP64
+__global__ void k_restrict_fields(const double *__restrict__ phi, const double *__restrict__ b,
+                                  int nxc, int nyc, int nzc, double *__restrict__ phic,
+                                  double *__restrict__ bc) {
+  const size_t n = (size_t)nxc * nyc * nzc;
+  const size_t fx = 2 * (size_t)nxc, fxy = 4 * (size_t)nxc * nyc;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n;
+       v += (size_t)gridDim.x * blockDim.x) {
+    const size_t I = v % nxc, J = (v / nxc) % nyc, K = v / ((size_t)nxc * nyc);
+    const size_t f = 2 * K * fxy + 2 * J * fx + 2 * I;
+    double sp = 0.0, sb = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const size_t e = f + (q & 1) + ((q >> 1) & 1) * fx + (q >> 2) * fxy;
+      sp += phi[e];
+      sb += b[e];
+    }
+    phic[v] = 0.125 * sp;
+    bc[v] = 0.125 * sb;
+  }
+}
+
+// p_fine = s * (q - mean q) interpolated trilinearly from the network grid to
+// the grid twice as fine (cell-centred weights 3/4, 1/4 per axis; periodic
+// axes wrap, wall axes clamp)
+__global__ void k_prolong_tri(const float *__restrict__ q, const double *__restrict__ sum_q,
+                              int nxc, int nyc, int nzc, int per, double s,
+                              double *__restrict__ p) {
+  const size_t nc = (size_t)nxc * nyc * nzc;
+  const double m = *sum_q / (double)nc;
+  const int nx = 2 * nxc, ny = 2 * nyc, nz = 2 * nzc;
+  const size_t n = (size_t)nx * ny * nz;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n;
+       v += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((size_t)nx * ny));
+    int I[2], J[2], K[2];
+    float wi[2], wj[2], wk[2];
+    const int c[3] = {i, j, k}, nn[3] = {nxc, nyc, nzc};
+    int *idx[3] = {I, J, K};
+    float *w[3] = {wi, wj, wk};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int lo = (c[a] - 1) >> 1;  // coarse cell below the fine centre
+      const float w1 = (c[a] & 1) ? 0.25f : 0.75f;
+      int l0 = lo, l1 = lo + 1;
+      if (per & (1 << a)) {
+        l0 = (l0 + nn[a]) % nn[a];
+        l1 = l1 % nn[a];
+      } else {
+        l0 = l0 < 0 ? 0 : l0;
+        l1 = l1 > nn[a] - 1 ? nn[a] - 1 : l1;
+      }
+      idx[a][0] = l0;
+      idx[a][1] = l1;
+      w[a][0] = 1.f - w1;
+      w[a][1] = w1;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int q8 = 0; q8 < 8; ++q8) {
+      const int a = q8 & 1, bq = (q8 >> 1) & 1, cq = q8 >> 2;
+      const double wt = (double)wi[a] * wj[bq] * wk[cq];
+      acc += wt * ((double)q[((size_t)K[cq] * nyc + J[bq]) * nxc + I[a]] - m);
+    }
+    p[v] = s * acc;
+  }
+}
+
 // 2x2x2 average pooling (fine nx, ny, nz; C channels)
 __global__ void k_pool2(const bf16 *__restrict__ in, bf16 *__restrict__ out, int nx, int ny, int nz,
                         int C) {
@@ -968,6 +1037,8 @@ struct mp_net {
   float *cpart = nullptr;         // per-channel partial sums
   double *dpart = nullptr, *dscal = nullptr, *hscal = nullptr;
   int *err = nullptr;
+  double *phic = nullptr, *bc = nullptr;  // restricted fields (guess for a 2x finer grid)
+  unsigned long long launches = 0;  // kernels launched by the network (all entry points)
   int loss_kind = 0;              // 0: gauge-free MSE; 1: energy norm
   EnergyGeom eg{};                // operator of the energy-norm loss
   float *e_aq = nullptr, *e_at = nullptr;
@@ -1225,6 +1296,7 @@ mp_status forward(mp_net *net) {
       net->L[13].y, net->param + net->head_w, net->param + net->head_b, net->nv[0], CH[0],
       net->q);
   NCK(cudaGetLastError());
+  net->launches += NLAYER + 3 + 1;  // convolutions, poolings, head
   return MP_OK;
 }
 
@@ -1434,6 +1506,8 @@ mp_status mp_net_create(mp_net_handle *out, int nx, int ny, int nz, void *stream
 
 size_t mp_net_param_count(mp_net_handle net) { return net ? net->nparam : 0; }
 
+unsigned long long mp_net_launches(mp_net_handle net) { return net ? net->launches : 0; }
+
 mp_status mp_net_dims(mp_net_handle net, int *nx, int *ny, int *nz) {
   if (!net) return MP_ERR_INVALID_ARG;
   if (nx) *nx = net->nx[0];
@@ -1503,8 +1577,47 @@ mp_status mp_net_features(mp_net_handle net, const double *phi, const double *b,
   if (!(rb > 0.0) || !std::isfinite(rb)) rb = 1.0;
   k_features<<<grid_for(n), 256, 0, net->st>>>(phi, b, n, 0.25 / h, 1.0 / rb, net->in16);
   NCK(cudaGetLastError());
+  net->launches += 3;
   NCK(cudaStreamSynchronize(net->st));
   if (s_out) *s_out = b_scale * rb;
+  return MP_OK;
+}
+
+mp_status mp_net_features_at(mp_net_handle net, int factor, const double *phi, const double *b,
+                             double h, double b_scale, double *s_out) {
+  if (!net || !(factor == 1 || factor == 2)) return MP_ERR_INVALID_ARG;
+  if (factor == 1) return mp_net_features(net, phi, b, h, b_scale, s_out);
+  if (!phi || !b || !(h > 0.0) || !(b_scale > 0.0)) return MP_ERR_INVALID_ARG;
+  const size_t n = net->nv[0];
+  if (!net->phic) {
+    NCKS(nalloc(net, &net->phic, n));
+    NCKS(nalloc(net, &net->bc, n));
+  }
+  k_restrict_fields<<<grid_for(n), 256, 0, net->st>>>(phi, b, net->nx[0], net->ny[0], net->nz[0],
+                                                      net->phic, net->bc);
+  NCK(cudaGetLastError());
+  net->launches += 1;
+  // the restricted b is the mean of the children: same scale as b
+  return mp_net_features(net, net->phic, net->bc, 2.0 * h, b_scale, s_out);
+}
+
+mp_status mp_net_pressure_at(mp_net_handle net, int factor, const mp_bc bc[3], double s,
+                             double *p_dev) {
+  if (!net || !(factor == 1 || factor == 2) || !p_dev || !bc) return MP_ERR_INVALID_ARG;
+  if (factor == 1) return mp_net_pressure(net, s, p_dev);
+  int per = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (bc[a] != MP_BC_PERIODIC && bc[a] != MP_BC_NEUMANN) return MP_ERR_INVALID_ARG;
+    if (bc[a] == MP_BC_PERIODIC) per |= 1 << a;
+  }
+  const size_t n = net->nv[0];
+  k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, n, 0, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
+  k_prolong_tri<<<grid_for(8 * n), 256, 0, net->st>>>(net->q, net->dscal, net->nx[0], net->ny[0],
+                                                      net->nz[0], per, s, p_dev);
+  NCK(cudaGetLastError());
+  net->launches += 3;
+  NCK(cudaStreamSynchronize(net->st));
   return MP_OK;
 }
 
@@ -1540,6 +1653,7 @@ mp_status mp_net_pressure(mp_net_handle net, double s, double *p_dev) {
   k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
   k_to_pressure<<<grid_for(n), 256, 0, net->st>>>(net->q, n, net->dscal, s, p_dev);
   NCK(cudaGetLastError());
+  net->launches += 3;
   NCK(cudaStreamSynchronize(net->st));
   return MP_OK;
 }

@@ -91,6 +91,7 @@ struct mp_poisson {
   double bnorm = 0.0;
   mp_stats stats{};
   mp_net_handle net = nullptr;  // learned initial guess (initial_guess = 2)
+  int net_factor = 1;           // solver grid / network grid (1 or 2)
   std::vector<void *> allocs;
   // launch accounting / CUDA-event profiling
   ProfEntry prof[K_COUNT][MAX_LEVELS];
@@ -571,9 +572,12 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     double s = 1.0;
     CK(cudaStreamSynchronize(hd->st));
     CKS(mp_net_set_stream(hd->net, hd->st));
-    CKS(mp_net_features(hd->net, hd->phi, hd->b, hd->h, 1.0, &s));
+    CKS(mp_net_features_at(hd->net, hd->net_factor, hd->phi, hd->b, hd->h, 1.0, &s));
     CKS(mp_net_forward(hd->net, nullptr));
-    CKS(mp_net_pressure(hd->net, 1.0, p));
+    const mp_bc nbc[3] = {(hd->per & 1) ? MP_BC_PERIODIC : MP_BC_NEUMANN,
+                          (hd->per & 2) ? MP_BC_PERIODIC : MP_BC_NEUMANN,
+                          (hd->per & 4) ? MP_BC_PERIODIC : MP_BC_NEUMANN};
+    CKS(mp_net_pressure_at(hd->net, hd->net_factor, nbc, 1.0, p));
     LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, p, hd->q,
            l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial);
     CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_TMP));
@@ -1080,7 +1084,12 @@ mp_status mp_poisson_set_net(mp_handle hd, mp_net_handle net) {
   if (net) {
     int nx = 0, ny = 0, nz = 0;
     CKS(mp_net_dims(net, &nx, &ny, &nz));
-    if (nx != hd->g.nx || ny != hd->g.ny || nz != hd->g.nz) return MP_ERR_INVALID_ARG;
+    if (nx == hd->g.nx && ny == hd->g.ny && nz == hd->g.nz)
+      hd->net_factor = 1;
+    else if (2 * nx == hd->g.nx && 2 * ny == hd->g.ny && 2 * nz == hd->g.nz)
+      hd->net_factor = 2;
+    else
+      return MP_ERR_INVALID_ARG;
   }
   hd->net = net;
   return MP_OK;

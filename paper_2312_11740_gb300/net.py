@@ -6,11 +6,16 @@ their helpers); this module only converts torch tensors to pointers.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import torch
 
 from . import _lib
 from .poisson import MPError, _check, _ptr, _stream_ptr
+
+# network trained at 128^3 on 1-16-bubble problems with the energy loss
+DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                               "unet128_energy.npz")
 
 
 def _lib_():
@@ -120,6 +125,37 @@ class Net:
         _check(_lib_().mp_net_backward(self.handle, _ptr(gq, torch.float32, self.n),
                                        _ptr(g, torch.float32)), "mp_net_backward")
         return g
+
+    def launches(self):
+        """Kernels launched by the network's inference paths so far."""
+        return int(_lib_().mp_net_launches(self.handle))
+
+    def load(self, path=None):
+        """Parameters from an .npz written by learn.py (default: the packaged
+        network trained at 128^3 with the energy loss); returns its metadata."""
+        import json
+        import numpy as np
+        d = np.load(path or DEFAULT_WEIGHTS)
+        self.set_params(torch.from_numpy(d["params"].astype(np.float32)).cuda())
+        return json.loads(str(d["meta"])) if "meta" in d.files else {}
+
+    def features_at(self, factor, phi, b, h, b_scale):
+        """features() for fields on a grid `factor` (1, 2) times finer."""
+        s = ctypes.c_double(0.0)
+        nf = self.n * factor ** 3
+        _check(_lib_().mp_net_features_at(self.handle, int(factor), _ptr(phi, numel=nf),
+                                          _ptr(b, numel=nf), float(h), float(b_scale),
+                                          ctypes.byref(s)), "mp_net_features_at")
+        return s.value
+
+    def pressure_at(self, factor, bc, s):
+        """pressure() interpolated onto a grid `factor` (1, 2) times finer."""
+        shape = tuple(factor * d for d in self.shape)
+        p = torch.empty(shape, dtype=torch.float64, device="cuda")
+        arr = (ctypes.c_int * 3)(*[int(v) for v in bc])
+        _check(_lib_().mp_net_pressure_at(self.handle, int(factor), arr, float(s), _ptr(p)),
+               "mp_net_pressure_at")
+        return p
 
     def set_loss(self, kind, rho_l=1.0, rho_g=1e-3, bc=(0, 0, 1)):
         """Training loss: 0 = gauge-free MSE, 1 = energy norm of the

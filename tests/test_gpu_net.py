@@ -287,3 +287,84 @@ def test_energy_loss_matches_oracle_operator():
     ref = 1.0 - a * a / (c * d)
     assert abs(loss - ref) <= 1e-5 * abs(ref) + 1e-7, (loss, ref)
     net.close()
+
+
+def _trilinear_up2(q, per):
+    """Reference cell-centred x2 interpolation (weights 3/4, 1/4 per axis;
+    periodic axes wrap, wall axes clamp), axes (z, y, x) with per bits
+    (x = 1, y = 2, z = 4)."""
+    out = q
+    for ax, bit in ((0, 4), (1, 2), (2, 1)):
+        n = out.shape[ax]
+        i = np.arange(2 * n)
+        lo = (i - 1) // 2
+        w1 = np.where(i % 2 == 1, 0.25, 0.75)
+        if per & bit:
+            l0, l1 = lo % n, (lo + 1) % n
+        else:
+            l0, l1 = np.clip(lo, 0, n - 1), np.clip(lo + 1, 0, n - 1)
+        shp = [1, 1, 1]
+        shp[ax] = 2 * n
+        out = (np.take(out, l0, axis=ax) * (1 - w1).reshape(shp) +
+               np.take(out, l1, axis=ax) * w1.reshape(shp))
+    return out
+
+
+def test_half_resolution_features_and_prolongation():
+    """A network on a grid half as fine as the solver's: features from the
+    means of 8 children (cell size 2h), and the output interpolated back."""
+    n = 32
+    h = 1.0 / (2 * n)
+    net = Net(n, n, n)
+    net.set_params(to_f32(random_param_vector(net, 31)))
+    g = rng(32)
+    phi = g.standard_normal((2 * n,) * 3) * 4 * h
+    b = g.standard_normal((2 * n,) * 3)
+    net.features_at(2, torch.from_numpy(phi).cuda(), torch.from_numpy(b).cuda(), h, 1.0)
+    x2 = net.get_input2().float().cpu().numpy()
+
+    def mean8(a):
+        return a.reshape(n, 2, n, 2, n, 2).mean(axis=(1, 3, 5))
+
+    pc, bc = mean8(phi), mean8(b)
+    f0 = bf16_round(np.clip(pc / (4 * 2 * h), -1, 1))
+    f1 = bf16_round(bc / np.sqrt(np.mean(bc * bc)))
+    # FP64 sums in another order: a BF16 tie may round the other way (1 ulp)
+    assert np.max(np.abs(x2[..., 0] - f0)) <= 2 ** -8
+    assert np.mean(x2[..., 0] != f0) < 1e-3
+    assert np.max(np.abs(x2[..., 1] - f1)) <= 2 ** -7 * np.max(np.abs(f1))
+    q = net.forward().cpu().numpy().astype(np.float64)
+    for bcs, per in (((0, 0, 1), 3), ((1, 1, 1), 0), ((0, 0, 0), 7)):
+        p = net.pressure_at(2, bcs, 1.5).cpu().numpy()
+        ref = 1.5 * _trilinear_up2(q - q.mean(), per)
+        assert np.max(np.abs(p - ref)) <= 1e-6 * np.max(np.abs(ref)), bcs
+    net.close()
+
+
+def test_solver_with_half_resolution_trained_net():
+    """The packaged trained network (conv weights do not depend on the grid)
+    on a 32^3 grid guesses for a 64^3 solve: the guess is kept, lowers the
+    A-norm error, and the solve reaches the same pressure as from zero."""
+    import synth
+    from paper_2312_11740_gb300 import Poisson, mp_poisson_set_net
+    n = 64
+    h = 1.0 / n
+    shape = (n, n, n)
+    phi = synth.level_set(shape, h, [((0.5, 0.5, 0.4), 0.2), ((0.3, 0.7, 0.7), 0.1)])
+    u = synth.velocity(41, shape, h)
+    bc = (0, 0, 1)
+    s = Poisson(torch.from_numpy(phi).cuda(), h, bc, 1.0, 1e-3, 0.07, precision=1)
+    rhs = s.divergence(*[torch.from_numpy(c).cuda() for c in u])
+    p0, it0, _ = s.solve(rhs, tol=1e-10)
+    net = Net(n // 2, n // 2, n // 2)
+    meta = net.load()
+    assert meta.get("loss") == "energy"
+    mp_poisson_set_net(s.handle, net)
+    s.set_opts(initial_guess=2, net_check=1)
+    p1, it1, _ = s.solve(rhs, tol=1e-10)
+    st = s.stats()
+    assert st["used_net"] == 1 and st["relres"] <= 1e-10
+    assert float(torch.linalg.norm(p1 - p0) / torch.linalg.norm(p0)) < 1e-8
+    mp_poisson_set_net(s.handle, None)
+    s.close()
+    net.close()
