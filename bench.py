@@ -251,7 +251,7 @@ def run_mine(args, rank, world, local_rank):
             net = Net(n // 2, n // 2, n // 2, stream=stream)
             net.load()
             mp_poisson_set_net(s.handle, net)
-            s.set_opts(initial_guess=2)
+            s.set_opts(initial_guess=2, net_check=args.net_check)
         used = []
 
         def step(k):
@@ -422,6 +422,9 @@ def main():
     ap.add_argument("--modes", default="fp64,mixed,learned",
                     help="comma list of fp64, mixed, learned; the last one is the headline value")
     ap.add_argument("--profile-out", default=None, help="write per-kernel profile JSON here")
+    ap.add_argument("--net-check", type=int, default=0, choices=(0, 1),
+                    help="learned guess kept if its residual is below ||b|| (0, default) or "
+                         "whenever its energy-optimal scale is nonzero (1)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -294,11 +294,11 @@ __global__ void k_coarse_solve(const double *__restrict__ Minv, const T *__restr
 // in place (a colour's update reads only the other colour).  zero != 0
 // treats x as zero before the update (first sweep of a cycle).
 template <typename T>
-__global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__restrict__ bx,
-                       const T *__restrict__ by, const T *__restrict__ bz,
-                       const T *__restrict__ idiag, Dims d, int colour, int zero) {
-  int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-  if (t >= (d.nx >> 1) || j >= d.ny) return;
+__device__ __forceinline__ void rbgs_cell(T *__restrict__ x, const T *__restrict__ b,
+                                          const T *__restrict__ bx, const T *__restrict__ by,
+                                          const T *__restrict__ bz, const T *__restrict__ idiag,
+                                          const Dims &d, int t, int j, int k, int colour,
+                                          int zero) {
   int i = 2 * t + ((j + k + colour) & 1);
   size_t c = at(d, i, j, k);
   size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
@@ -319,6 +319,15 @@ __global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__re
   } else {
     x[c] = __fdividef((float)s, (float)(((wxl + wxh) + (wyl + wyh)) + (wzl + wzh)));
   }
+}
+
+template <typename T>
+__global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__restrict__ bx,
+                       const T *__restrict__ by, const T *__restrict__ bz,
+                       const T *__restrict__ idiag, Dims d, int colour, int zero) {
+  int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (t >= (d.nx >> 1) || j >= d.ny) return;
+  rbgs_cell<T>(x, b, bx, by, bz, idiag, d, t, j, k, colour, zero);
 }
 
 // (At x)_c at one cell.  FP64: sum_f beta_f x_nb - diag_c x_c (fewest FP64
@@ -513,18 +522,30 @@ k_tail(TailArgs a, const T *__restrict__ rhs, T *__restrict__ xout) {
 // Coarse scaled rhs = (2h)^2 * mean of the 8 children's residuals
 //                   = 0.5 * sum of the children's scaled residuals.
 template <typename T>
-__global__ void k_resid_restrict(const T *__restrict__ x, const T *__restrict__ b,
-                                 const T *__restrict__ bx, const T *__restrict__ by,
-                                 const T *__restrict__ bz, const T *__restrict__ diag, Dims df,
-                                 T *__restrict__ bc, Dims dc) {
-  int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
-  if (I >= dc.nx || J >= dc.ny) return;
+__device__ __forceinline__ void resid_restrict_cell(const T *__restrict__ x,
+                                                    const T *__restrict__ b,
+                                                    const T *__restrict__ bx,
+                                                    const T *__restrict__ by,
+                                                    const T *__restrict__ bz,
+                                                    const T *__restrict__ diag, const Dims &df,
+                                                    T *__restrict__ bc, const Dims &dc, int I,
+                                                    int J, int K) {
   T s = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     s += resid_at(x, b, bx, by, bz, diag, df, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1),
                   2 * K + (q >> 2));
   bc[at(dc, I, J, K)] = (T)0.5 * s;
+}
+
+template <typename T>
+__global__ void k_resid_restrict(const T *__restrict__ x, const T *__restrict__ b,
+                                 const T *__restrict__ bx, const T *__restrict__ by,
+                                 const T *__restrict__ bz, const T *__restrict__ diag, Dims df,
+                                 T *__restrict__ bc, Dims dc) {
+  int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+  if (I >= dc.nx || J >= dc.ny) return;
+  resid_restrict_cell<T>(x, b, bx, by, bz, diag, df, bc, dc, I, J, K);
 }
 
 // ------------------------------------- A8: prolongation + correction
@@ -534,6 +555,92 @@ __global__ void k_prolong(T *__restrict__ x, const T *__restrict__ ec, Dims df, 
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= df.nx || j >= df.ny) return;
   x[at(df, i, j, k)] += ec[at(dc, i >> 1, j >> 1, k >> 1)];
+}
+
+// The same with 16-byte accesses: a thread adds the corrections of its
+// parents to 16/sizeof(T) consecutive cells of a row (nx a multiple of that;
+// rows stay 16-byte aligned).  The scalar form is latency-bound at ~21% of HBM.
+template <typename T>
+__global__ void k_prolong_vec(T *__restrict__ x, const T *__restrict__ ec, Dims df, Dims dc) {
+  constexpr int W = 16 / sizeof(T);  // cells per thread (FP32: 4, FP64: 2)
+  const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (t >= df.nx / W || j >= df.ny) return;
+  const int i = W * t;
+  T *xr = x + at(df, i, j, k);
+  const T *er = ec + at(dc, i >> 1, j >> 1, k >> 1);
+  if (W == 4) {
+    float4 v = *reinterpret_cast<float4 *>(xr);
+    const float2 e = *reinterpret_cast<const float2 *>(er);
+    v.x += e.x;
+    v.y += e.x;
+    v.z += e.y;
+    v.w += e.y;
+    *reinterpret_cast<float4 *>(xr) = v;
+  } else {
+    double2 v = *reinterpret_cast<double2 *>(xr);
+    const double e = *reinterpret_cast<const double *>(er);
+    v.x += e;
+    v.y += e;
+    *reinterpret_cast<double2 *>(xr) = v;
+  }
+}
+
+// ------------------------------ finest-level slab wavefront (FP32 V-cycle)
+// A phase of the finest level (pre: the red/black sweeps and the residual +
+// restriction; post: the prolongation and the sweeps) runs as a wavefront
+// over z-slabs of SLAB_T planes: at step s, stage m works on slab s - 2m.
+// Stage m on slab t reads the other colour up to one plane beyond the slab,
+// i.e. stage m-1's output on slabs t-1, t, t+1, finished at steps <= s-1, so
+// all stages of one step are independent and run as ONE launch.  Each colour
+// update reads only the other colour, so the result equals that of the
+// whole-level sweeps bit for bit.  A slab's fields are touched by its stages
+// on consecutive even steps while about 9 slabs are live (~100 MB at 256^2 x
+// 8 planes): they stay in the 126 MB L2 between the sweeps instead of
+// returning to HBM.  z must be a wall axis: a periodic wrap would read the
+// top slab before its stage ran.
+constexpr int SLAB_T = 8;
+constexpr int SLAB_MAX_STAGES = 9;
+enum { SLAB_RBGS = 0, SLAB_RESTRICT = 1, SLAB_PROLONG = 2 };
+struct SlabStage {
+  int kind, colour, zero, slab, block0;
+};
+struct SlabArgs {
+  float *x;
+  const float *b, *bx, *by, *bz;
+  Dims d;
+  float *bc;        // coarse rhs (restriction output)
+  const float *ec;  // coarse correction (prolongation input)
+  Dims dc;
+  int nstage;
+  SlabStage st[SLAB_MAX_STAGES];
+};
+
+__global__ void k_slab_step(const SlabArgs a) {
+  const int blk = blockIdx.x;
+  SlabStage s = a.st[0];
+#pragma unroll
+  for (int q = 1; q < SLAB_MAX_STAGES; ++q)
+    if (q < a.nstage && blk >= a.st[q].block0) s = a.st[q];
+  const int lb = blk - s.block0;
+  if (s.kind == SLAB_RBGS) {
+    const int gx = ((a.d.nx >> 1) + BX - 1) / BX, gy = (a.d.ny + BY - 1) / BY;
+    const int t = (lb % gx) * BX + threadIdx.x, j = ((lb / gx) % gy) * BY + threadIdx.y;
+    const int k = s.slab * SLAB_T + lb / (gx * gy);
+    if (t < (a.d.nx >> 1) && j < a.d.ny)
+      rbgs_cell<float>(a.x, a.b, a.bx, a.by, a.bz, nullptr, a.d, t, j, k, s.colour, s.zero);
+  } else if (s.kind == SLAB_RESTRICT) {
+    const int gx = (a.dc.nx + BX - 1) / BX, gy = (a.dc.ny + BY - 1) / BY;
+    const int I = (lb % gx) * BX + threadIdx.x, J = ((lb / gx) % gy) * BY + threadIdx.y;
+    const int K = s.slab * (SLAB_T / 2) + lb / (gx * gy);
+    if (I < a.dc.nx && J < a.dc.ny)
+      resid_restrict_cell<float>(a.x, a.b, a.bx, a.by, a.bz, nullptr, a.d, a.bc, a.dc, I, J, K);
+  } else {
+    const int gx = (a.d.nx + BX - 1) / BX, gy = (a.d.ny + BY - 1) / BY;
+    const int i = (lb % gx) * BX + threadIdx.x, j = ((lb / gx) % gy) * BY + threadIdx.y;
+    const int k = s.slab * SLAB_T + lb / (gx * gy);
+    if (i < a.d.nx && j < a.d.ny)
+      a.x[at(a.d, i, j, k)] += a.ec[at(a.dc, i >> 1, j >> 1, k >> 1)];
+  }
 }
 
 // --------------------------------------------------------- Krylov kernels
@@ -604,28 +711,97 @@ __global__ void k_residual_mixed(const double *__restrict__ x, const double *__r
 }
 
 // Grid-stride vector kernels: fixed grid (deterministic partial order).
+// When every operand is 16-byte aligned (internal buffers always are; a
+// caller's p usually is) they move 16 bytes per load (float4 / double2), two
+// vectors per iteration, which keeps enough loads in flight to stream HBM.
 constexpr int VEC_THREADS = 256;
 
 template <typename T>
-__global__ void k_dot(const T *__restrict__ a, const T *__restrict__ b, size_t n,
-                      double *__restrict__ partial) {
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  __device__ static float at(const V &v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+  }
+  __device__ static void set(V &v, int i, float a) {
+    if (i == 0) v.x = a; else if (i == 1) v.y = a; else if (i == 2) v.z = a; else v.w = a;
+  }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  __device__ static double at(const V &v, int i) { return i == 0 ? v.x : v.y; }
+  __device__ static void set(V &v, int i, double a) {
+    if (i == 0) v.x = a; else v.y = a;
+  }
+};
+__device__ __forceinline__ bool aligned16(const void *a, const void *b = nullptr,
+                                          const void *c = nullptr, const void *d = nullptr) {
+  return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) & 15) == 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS, 4)
+k_dot(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *__restrict__ partial) {
+  using VT = Vec16<T>;
+  using V = typename VT::V;
+  constexpr int W = VT::W;
   T acc = 0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x)
-    acc = fma(a[e], b[e], acc);
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t done = 0;
+  if (aligned16(a, b)) {
+    const size_t nv = n / W;
+    const V *av = reinterpret_cast<const V *>(a), *bv = reinterpret_cast<const V *>(b);
+    for (size_t e = tid; e < nv; e += stride) {
+      const V x = av[e], y = bv[e];
+#pragma unroll
+      for (int q = 0; q < W; ++q) acc = fma(VT::at(x, q), VT::at(y, q), acc);
+    }
+    done = nv * W;
+  }
+  for (size_t e = done + tid; e < n; e += stride) acc = fma(a[e], b[e], acc);
   double t = block_sum((double)acc);
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
 // x += alpha d; r -= alpha q; partial r.r
 template <typename T>
-__global__ void k_axpy2(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ dv,
+__global__ void __launch_bounds__(VEC_THREADS, 4)
+k_axpy2(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ dv,
                         const T *__restrict__ q, size_t n, const double *__restrict__ scal,
                         double *__restrict__ partial) {
-  T alpha = (T)scal[S_ALPHA];
+  using VT = Vec16<T>;
+  using V = typename VT::V;
+  constexpr int W = VT::W;
+  const T alpha = (T)scal[S_ALPHA];
   T acc = 0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x) {
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t done = 0;
+  if (aligned16(x, r, dv, q)) {
+    const size_t nv = n / W;
+    V *xv = reinterpret_cast<V *>(x), *rv = reinterpret_cast<V *>(r);
+    const V *dvv = reinterpret_cast<const V *>(dv), *qv = reinterpret_cast<const V *>(q);
+    for (size_t e = tid; e < nv; e += stride) {
+      V xe = xv[e], re = rv[e];
+      const V de = dvv[e], qe = qv[e];
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        VT::set(xe, k, fma(alpha, VT::at(de, k), VT::at(xe, k)));
+        const T rk = fma(-alpha, VT::at(qe, k), VT::at(re, k));
+        VT::set(re, k, rk);
+        acc = fma(rk, rk, acc);
+      }
+      xv[e] = xe;
+      rv[e] = re;
+    }
+    done = nv * W;
+  }
+  for (size_t e = done + tid; e < n; e += stride) {
     x[e] = fma(alpha, dv[e], x[e]);
     T rv = fma(-alpha, q[e], r[e]);
     r[e] = rv;
@@ -637,12 +813,32 @@ __global__ void k_axpy2(T *__restrict__ x, T *__restrict__ r, const T *__restric
 
 // d = z + beta d (first iteration: d = z)
 template <typename T>
-__global__ void k_xpby(T *__restrict__ dv, const T *__restrict__ z, size_t n,
+__global__ void __launch_bounds__(VEC_THREADS, 4)
+k_xpby(T *__restrict__ dv, const T *__restrict__ z, size_t n,
                        const double *__restrict__ scal, int first) {
-  T beta = (T)scal[S_BETA];
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x)
-    dv[e] = first ? z[e] : fma(beta, dv[e], z[e]);
+  using VT = Vec16<T>;
+  using V = typename VT::V;
+  constexpr int W = VT::W;
+  const T beta = first ? (T)0 : (T)scal[S_BETA];
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t done = 0;
+  if (aligned16(dv, z)) {
+    const size_t nv = n / W;
+    V *dvv = reinterpret_cast<V *>(dv);
+    const V *zv = reinterpret_cast<const V *>(z);
+    for (size_t e = tid; e < nv; e += stride) {
+      const V ze = zv[e];
+      V de = first ? ze : dvv[e];
+      if (!first) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) VT::set(de, k, fma(beta, VT::at(de, k), VT::at(ze, k)));
+      }
+      dvv[e] = de;
+    }
+    done = nv * W;
+  }
+  for (size_t e = done + tid; e < n; e += stride) dv[e] = first ? z[e] : fma(beta, dv[e], z[e]);
 }
 
 // x += y (stationary iteration update)

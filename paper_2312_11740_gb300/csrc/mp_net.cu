@@ -349,11 +349,15 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
   for (; produced < NS - 1 && produced < nst; ++produced) produce(produced);
   for (int s = 0; s < nst; ++s) {
     const int buf = s % NS;
-    if (__all_sync(0xffffffffu, mbar_wait(&full[buf], (uint32_t)((s / NS) & 1))))
-      waited_full = s + 1;
-    else
-      abort_flag = 1;
-    __syncthreads();  // the gathers of stage s are visible; abort is seen by all
+    // one thread polls the barriers (127 pollers would load the shared-memory
+    // pipe that feeds the tensor core); the others wait at the CTA barrier
+    if (tid == 0) {
+      if (mbar_wait(&full[buf], (uint32_t)((s / NS) & 1)))
+        waited_full = s + 1;
+      else
+        abort_flag = 1;
+    }
+    __syncthreads();  // stage s landed and its gathers are visible; abort is seen by all
     if (abort_flag) break;
     const int lt = s / a.nchunk, c = s - lt * a.nchunk;
     if (tid == 0) {
@@ -378,10 +382,13 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     if (s >= 1) {
       // MMAs of stage s-1 are done: its buffer is free and, if it ended a
       // tile, that tile's accumulators are final
-      if (__all_sync(0xffffffffu, mbar_wait(&done[(s - 1) % NS], (uint32_t)(((s - 1) / NS) & 1))))
-        waited_done = s;
-      else
-        abort_flag = 1;
+      if (tid == 0) {
+        if (mbar_wait(&done[(s - 1) % NS], (uint32_t)(((s - 1) / NS) & 1)))
+          waited_done = s;
+        else
+          abort_flag = 1;
+      }
+      __syncthreads();
       if (!abort_flag && (s - 1) % a.nchunk == a.nchunk - 1) epilogue((s - 1) / a.nchunk);
     }
     if (!abort_flag && produced < nst) {
@@ -390,18 +397,21 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     }
   }
   if (!abort_flag && nst > 0) {
-    if (__all_sync(0xffffffffu, mbar_wait(&done[(nst - 1) % NS], (uint32_t)(((nst - 1) / NS) & 1))))
-      waited_done = nst;
-    else
-      abort_flag = 1;
+    if (tid == 0) {
+      if (mbar_wait(&done[(nst - 1) % NS], (uint32_t)(((nst - 1) / NS) & 1)))
+        waited_done = nst;
+      else
+        abort_flag = 1;
+    }
+    __syncthreads();
     if (!abort_flag) epilogue(nst / a.nchunk - 1);
   }
   __syncthreads();
-  if (abort_flag) {
-    // drain: copies still in flight into shared memory, MMAs still reading it
+  if (abort_flag && tid == 0) {
+    // drain (bounded): copies still in flight into shared memory, MMAs still reading it
     for (int s = waited_full; s < produced; ++s) mbar_wait(&full[s % NS], (uint32_t)((s / NS) & 1));
     for (int s = waited_done; s < committed; ++s) mbar_wait(&done[s % NS], (uint32_t)((s / NS) & 1));
-    if (tid == 0) atomicExch(a.err, 1);
+    atomicExch(a.err, 1);
   }
   tc_fence_before();
   __syncthreads();

@@ -40,8 +40,12 @@ def test_pool256_sequence_all_modes():
         r = sequence.run(phi, prm, us, mode, warmup=0, keep=True)
         assert r["max_relres"] <= TOL, mode
         for k, (a, b) in enumerate(zip(r["pressures"], ref["pressures"])):
-            assert rel(a, b) <= PARITY, (mode, k)
-        assert oracle_relres(phi_h, us[-1], prm, r["pressures"][-1]) <= 1.5 * TOL, mode
+            # every pressure meets the target through the oracle's operator
+            assert oracle_relres(phi_h, us[k], prm, a) <= 1.5 * TOL, (mode, k)
+            # two solutions that each meet ||b - Ap|| <= 1e-10 ||b|| differ by up to
+            # cond x 1e-10: this pool geometry gives 5e-8 for warm starts (which stop
+            # at a different point of the iteration), zero-guess forms agree to 1e-9
+            assert rel(a, b) <= (1e-6 if mode == "previous" else PARITY), (mode, k)
 
 
 def test_bubbles512_mixed_full_size():
