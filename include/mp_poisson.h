@@ -80,12 +80,6 @@ typedef struct {
                         0: its residual ||b - A p0|| is below ||b|| (default);
                         1: alpha is finite and nonzero, i.e. whenever the A-norm error of p0
                            is below that of the zero guess (always true for that alpha). */
-  int fine_pipeline; /* mixed: 1 runs the finest level's sweeps, residual and transfers as
-                        a wavefront over 8-plane z-slabs meant to keep each slab in L2
-                        across its sweeps (used when z is a wall axis, nz is a multiple of
-                        8 with >= 4 slabs and nu1, nu2 <= 4); 0 (default) = one launch per
-                        whole-level sweep, measured faster at 256^3.  Both give identical
-                        results. */
   void *stream;      /* cudaStream_t; NULL = legacy default stream. */
 } mp_opts;
 

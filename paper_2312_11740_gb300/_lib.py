@@ -42,7 +42,6 @@ class mp_opts(ctypes.Structure):
         ("inner_rtol", ctypes.c_double),
         ("inner_max", ctypes.c_int),
         ("net_check", ctypes.c_int),
-        ("fine_pipeline", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 

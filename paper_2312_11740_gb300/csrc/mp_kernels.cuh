@@ -585,64 +585,6 @@ __global__ void k_prolong_vec(T *__restrict__ x, const T *__restrict__ ec, Dims 
   }
 }
 
-// ------------------------------ finest-level slab wavefront (FP32 V-cycle)
-// A phase of the finest level (pre: the red/black sweeps and the residual +
-// restriction; post: the prolongation and the sweeps) runs as a wavefront
-// over z-slabs of SLAB_T planes: at step s, stage m works on slab s - 2m.
-// Stage m on slab t reads the other colour up to one plane beyond the slab,
-// i.e. stage m-1's output on slabs t-1, t, t+1, finished at steps <= s-1, so
-// all stages of one step are independent and run as ONE launch.  Each colour
-// update reads only the other colour, so the result equals that of the
-// whole-level sweeps bit for bit.  A slab's fields are touched by its stages
-// on consecutive even steps while about 9 slabs are live (~100 MB at 256^2 x
-// 8 planes): they stay in the 126 MB L2 between the sweeps instead of
-// returning to HBM.  z must be a wall axis: a periodic wrap would read the
-// top slab before its stage ran.
-constexpr int SLAB_T = 8;
-constexpr int SLAB_MAX_STAGES = 9;
-enum { SLAB_RBGS = 0, SLAB_RESTRICT = 1, SLAB_PROLONG = 2 };
-struct SlabStage {
-  int kind, colour, zero, slab, block0;
-};
-struct SlabArgs {
-  float *x;
-  const float *b, *bx, *by, *bz;
-  Dims d;
-  float *bc;        // coarse rhs (restriction output)
-  const float *ec;  // coarse correction (prolongation input)
-  Dims dc;
-  int nstage;
-  SlabStage st[SLAB_MAX_STAGES];
-};
-
-__global__ void k_slab_step(const SlabArgs a) {
-  const int blk = blockIdx.x;
-  SlabStage s = a.st[0];
-#pragma unroll
-  for (int q = 1; q < SLAB_MAX_STAGES; ++q)
-    if (q < a.nstage && blk >= a.st[q].block0) s = a.st[q];
-  const int lb = blk - s.block0;
-  if (s.kind == SLAB_RBGS) {
-    const int gx = ((a.d.nx >> 1) + BX - 1) / BX, gy = (a.d.ny + BY - 1) / BY;
-    const int t = (lb % gx) * BX + threadIdx.x, j = ((lb / gx) % gy) * BY + threadIdx.y;
-    const int k = s.slab * SLAB_T + lb / (gx * gy);
-    if (t < (a.d.nx >> 1) && j < a.d.ny)
-      rbgs_cell<float>(a.x, a.b, a.bx, a.by, a.bz, nullptr, a.d, t, j, k, s.colour, s.zero);
-  } else if (s.kind == SLAB_RESTRICT) {
-    const int gx = (a.dc.nx + BX - 1) / BX, gy = (a.dc.ny + BY - 1) / BY;
-    const int I = (lb % gx) * BX + threadIdx.x, J = ((lb / gx) % gy) * BY + threadIdx.y;
-    const int K = s.slab * (SLAB_T / 2) + lb / (gx * gy);
-    if (I < a.dc.nx && J < a.dc.ny)
-      resid_restrict_cell<float>(a.x, a.b, a.bx, a.by, a.bz, nullptr, a.d, a.bc, a.dc, I, J, K);
-  } else {
-    const int gx = (a.d.nx + BX - 1) / BX, gy = (a.d.ny + BY - 1) / BY;
-    const int i = (lb % gx) * BX + threadIdx.x, j = ((lb / gx) % gy) * BY + threadIdx.y;
-    const int k = s.slab * SLAB_T + lb / (gx * gy);
-    if (i < a.d.nx && j < a.d.ny)
-      a.x[at(a.d, i, j, k)] += a.ec[at(a.dc, i >> 1, j >> 1, k >> 1)];
-  }
-}
-
 // --------------------------------------------------------- Krylov kernels
 // Scalars kept on the device between kernels (no host round trip).
 enum { S_RZ = 0, S_RZOLD, S_DQ, S_ALPHA, S_BETA, S_RR, S_BB, S_MEAN, S_TMP, S_COUNT };

@@ -42,7 +42,7 @@ enum KernelId {
   K_RBGS64, K_RBGS32, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
   K_APPLY64, K_APPLY32, K_RESID64, K_RESID32, K_RESIDMIX, K_DOT64, K_DOT32, K_AXPY64, K_AXPY32,
   K_XPBY64, K_XPBY32, K_ADD64, K_ADD32, K_ADDF32, K_SUM, K_SUBMEAN, K_REDUCE, K_ASSEMBLE,
-  K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_SLAB32, K_COUNT
+  K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_COUNT
 };
 const char *const kKernelNames[K_COUNT] = {
   "curvature", "gfm_faces", "jump", "diag", "coarsen_faces", "dense_build", "gauss_jordan",
@@ -51,8 +51,7 @@ const char *const kKernelNames[K_COUNT] = {
   "prolong_f32", "coarse_solve_f64", "coarse_solve_f32io", "apply_dot_f64", "apply_dot_f32",
   "residual_f64", "residual_f32", "residual_mixed", "dot_f64", "dot_f32", "axpy2_f64",
   "axpy2_f32", "xpby_f64", "xpby_f32", "add_f64", "add_f32", "add_f32_to_f64", "sum",
-  "sub_mean", "reduce", "assemble", "assemble_u", "project", "divergence", "scale",
-  "slab_step_f32"};
+  "sub_mean", "reduce", "assemble", "assemble_u", "project", "divergence", "scale"};
 constexpr int MAX_LEVELS = 16;
 constexpr int EVENT_POOL = 4096;
 
@@ -268,82 +267,6 @@ template <> struct LV<float> {
   static float *e(Level &l) { return l.e32; }
 };
 
-template <typename T>
-mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x);
-
-// Finest FP32 level as an L2 slab wavefront (k_slab_step): usable when z is a
-// wall axis and splits into at least 4 slabs, and a phase has <= 9 stages.
-bool slab_ok(const mp_poisson *hd, int l) {
-  const Level &lv = hd->L[l];
-  return hd->opts.fine_pipeline && l == 0 && hd->L.size() > 1 && !(hd->per & 4) &&
-         lv.d.nz % SLAB_T == 0 && lv.d.nz / SLAB_T >= 4 && !(lv.d.nx & 1) &&
-         2 * lv.nu1 + 1 <= SLAB_MAX_STAGES && 2 * lv.nu2 + 1 <= SLAB_MAX_STAGES;
-}
-
-// One phase: stages[m] = (kind, colour, zero); step s runs stage m on slab s - 2m.
-mp_status slab_phase(mp_poisson *hd, const std::vector<SlabStage> &stages, const float *rhs,
-                     float *x) {
-  Level &lv = hd->L[0], &lc = hd->L[1];
-  const int nsl = lv.d.nz / SLAB_T, ls = (int)stages.size();
-  const long plane = (long)lv.d.nx * lv.d.ny;
-  const int nb_rbgs = (((lv.d.nx >> 1) + BX - 1) / BX) * ((lv.d.ny + BY - 1) / BY) * SLAB_T;
-  const int nb_restr = ((lc.d.nx + BX - 1) / BX) * ((lc.d.ny + BY - 1) / BY) * (SLAB_T / 2);
-  const int nb_prol = ((lv.d.nx + BX - 1) / BX) * ((lv.d.ny + BY - 1) / BY) * SLAB_T;
-  const double cells = (double)plane * SLAB_T;
-  for (int step = 0; step < nsl + 2 * (ls - 1); ++step) {
-    SlabArgs a{};
-    a.x = x;
-    a.b = rhs;
-    a.bx = lv.bx32;
-    a.by = lv.by32;
-    a.bz = lv.bz32;
-    a.d = lv.d;
-    a.bc = lc.b32;
-    a.ec = lc.e32;
-    a.dc = lc.d;
-    int blocks = 0;
-    double bytes = 0.0;
-    for (int m = 0; m < ls; ++m) {
-      const int t = step - 2 * m;
-      if (t < 0 || t >= nsl) continue;
-      SlabStage st = stages[m];
-      st.slab = t;
-      st.block0 = blocks;
-      a.st[a.nstage++] = st;
-      if (st.kind == SLAB_RBGS) {
-        blocks += nb_rbgs;
-        bytes += cells * (st.zero ? 16.0 : 18.0);
-      } else if (st.kind == SLAB_RESTRICT) {
-        blocks += nb_restr;
-        bytes += cells * 24.5;
-      } else {
-        blocks += nb_prol;
-        bytes += cells * 8.5;
-      }
-    }
-    LAUNCH(hd, K_SLAB32, 0, bytes, k_slab_step, blocks, kBlock, a);
-  }
-  return launch_ok();
-}
-
-mp_status vcycle_fine_slabs(mp_poisson *hd, const float *rhs, float *x) {
-  Level &lv = hd->L[0], &lc = hd->L[1];
-  std::vector<SlabStage> pre, post;
-  for (int s = 0; s < lv.nu1; ++s) {
-    pre.push_back(SlabStage{SLAB_RBGS, 0, s == 0 ? 1 : 0, 0, 0});
-    pre.push_back(SlabStage{SLAB_RBGS, 1, 0, 0, 0});
-  }
-  pre.push_back(SlabStage{SLAB_RESTRICT, 0, 0, 0, 0});
-  post.push_back(SlabStage{SLAB_PROLONG, 0, 0, 0, 0});
-  for (int s = 0; s < lv.nu2; ++s) {
-    post.push_back(SlabStage{SLAB_RBGS, 1, 0, 0, 0});
-    post.push_back(SlabStage{SLAB_RBGS, 0, 0, 0, 0});
-  }
-  CKS(slab_phase(hd, pre, rhs, x));
-  CKS(vcycle<float>(hd, 1, lc.b32, lc.e32));
-  return slab_phase(hd, post, rhs, x);
-}
-
 // One symmetric V-cycle with zero initial guess: x ~= At^-1 rhs on level l.
 // Pre-smoothing sweeps red then black, post-smoothing black then red (the
 // adjoint), so the cycle is a symmetric preconditioner.  Each colour is one
@@ -376,8 +299,6 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
            k_coarse_solve<T>, 1, 512, hd->Minv, rhs, x, (int)lv.n);
     return launch_ok();
   }
-  if (sizeof(T) == 4 && slab_ok(hd, l))
-    return vcycle_fine_slabs(hd, (const float *)rhs, (float *)x);
   Level &lc = hd->L[l + 1];
   T *bx = LV<T>::bx(lv), *by = LV<T>::by(lv), *bz = LV<T>::bz(lv);
   T *diag = LV<T>::diag(lv), *idiag = LV<T>::idiag(lv);
@@ -775,8 +696,7 @@ bool valid_opts(const mp_opts &o) {
   return (o.precision == 0 || o.precision == 1) && (o.method == 0 || o.method == 1) &&
          o.initial_guess >= 0 && o.initial_guess <= 2 && o.max_iters >= 0 && o.nu1 >= 1 &&
          o.nu2 >= 1 && o.nu_growth >= 1 && o.nu_max >= 1 && o.inner_rtol > 0.0 &&
-         o.inner_rtol < 1.0 && o.inner_max >= 1 && (o.net_check == 0 || o.net_check == 1) &&
-         (o.fine_pipeline == 0 || o.fine_pipeline == 1);
+         o.inner_rtol < 1.0 && o.inner_max >= 1 && (o.net_check == 0 || o.net_check == 1);
 }
 
 void apply_nu(mp_poisson *hd) {
@@ -953,7 +873,6 @@ void mp_opts_default(mp_opts *o) {
   o->inner_rtol = 1e-4;
   o->inner_max = 12;
   o->net_check = 0;
-  o->fine_pipeline = 0;
   o->stream = nullptr;
 }
 

@@ -303,25 +303,3 @@ def test_full_size_256_properties(precision):
         assert np.max(np.abs(got - ref.ravel()[ix])) <= 1e-11 * max(np.abs(ref).max(), 1e-300)
     s.close()
 
-
-def test_fine_slab_wavefront_is_bitwise_identical():
-    """The mixed V-cycle's finest level as an L2 slab wavefront (z walls,
-    8-plane slabs) applies the same updates as whole-level sweeps, only in
-    another order of independent cells: identical pressure, bit for bit."""
-    shape = (64, 48, 40)  # (nz, ny, nx): 8 slabs, ragged x-y tiles
-    h = 1.0 / 64
-    phi = synth.level_set(shape, h, [((0.3, 0.4, 0.45), 0.12), ((0.15, 0.3, 0.7), 0.08)])
-    u = synth.velocity(17, shape, h)
-    prm = dict(h=h, bc=(P, P, N), rho_l=1.0, rho_g=1e-3, sigma=0.07)
-    s = make(phi, prm, precision=1, fine_pipeline=1)
-    rhs = s.divergence(*[dev(c) for c in u])
-    s.set_profiling(True)
-    p1, it1, _ = s.solve(rhs, tol=TOL)
-    names = {e["name"] for e in s.profile() if e["launches"] > 0}
-    assert "slab_step_f32" in names
-    s.set_profiling(False)
-    s.set_opts(fine_pipeline=0)
-    p0, it0, _ = s.solve(rhs, tol=TOL)
-    assert it0 == it1
-    assert torch.equal(p0, p1)
-    s.close()
