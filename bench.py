@@ -208,6 +208,23 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- multi-rank
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's timed-region length (ms): replicas run the same
+    number of steps, so whole-job throughput is world * K / max(ms)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, ms_max):
+    """Whole-job solves per second: every rank solves `steps` problems."""
+    return world * steps / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------- GPU arm
 def run_mine(args, rank, world, local_rank):
     import torch
@@ -287,11 +304,7 @@ def run_mine(args, rank, world, local_rank):
         if sampler:
             sampler.mark_end()
         clocks = sampler.stop() if sampler else None
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         launches = sum(e["launches"] for e in s.profile()) + (net.launches() - n0 if net else 0)
         used_timed = used[args.warmup:]
         # profiled pass on further inputs: every launch bracketed by CUDA events on
@@ -334,7 +347,7 @@ def run_mine(args, rank, world, local_rank):
     K = args.steps
     mixed = results[headline]
     fp64 = results.get("fp64", mixed)
-    value = world * K / (mixed["ms"] * 1e-3)
+    value = job_value(world, K, mixed["ms"])
     # dominant (kernel, level) by time in the headline mode's profiled steps
     prof = mixed["prof"]
     top = max(prof, key=lambda e: e["total_ms"])
@@ -354,7 +367,7 @@ def run_mine(args, rank, world, local_rank):
     total_prof_ms = sum(e["total_ms"] for e in prof)
 
     def mode_line(r):
-        d = {"solves_per_s": world * K / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / K,
+        d = {"solves_per_s": job_value(world, K, r["ms"]), "ms_per_step": r["ms"] / K,
              "iterations": r["iters"], "outer_steps_last": r["outer"],
              "max_relres": r["relres"], "levels": r["levels"]}
         if any(r["guess_used"]):
