@@ -77,9 +77,15 @@ typedef struct {
   int inner_max;     /* mixed: at most this many FP32 iterations between true residuals.
                         Default 12. */
   int net_check;     /* learned guess p0 = alpha q (alpha energy-optimal) is kept when
-                        0: its residual ||b - A p0|| is below ||b|| (default);
+                        0: its residual ||b - A p0|| is below ||b|| (default); with
+                           deflation active, the residuals compared are those deflated CG
+                           starts from, ||P (b - A p0)|| and ||P b|| (P = I - A Z E^-1 Z^T);
                         1: alpha is finite and nonzero, i.e. whenever the A-norm error of p0
                            is below that of the zero guess (always true for that alpha). */
+  int deflate;       /* method 0: 1 (default) deflates CG by the indicator vectors of the
+                        connected gas components (phi > 0), removing the bubbles' pressure
+                        levels, which the V-cycle resolves poorly at density ratio 1000;
+                        0 = plain MG-preconditioned CG.  Same converged answer. */
   void *stream;      /* cudaStream_t; NULL = legacy default stream. */
 } mp_opts;
 
@@ -90,9 +96,12 @@ typedef struct {
   double relres;       /* final ||b - A p|| / ||b||, FP64, true residual */
   double r0;           /* initial ||b - A p0|| / ||b|| */
   int used_net;        /* 1 if the learned guess was kept, 0 if not requested or rejected */
-  double net_relres;   /* ||b - A p_net|| / ||b|| of the learned guess (0 if not requested) */
+  double net_relres;   /* ||b - A p_net|| / ||b|| of the learned guess, deflated as in
+                          net_check 0 (0 if not requested); the guess is kept by the
+                          residual check iff this is below 1 */
   int levels;          /* multigrid levels */
   int coarse_n;        /* unknowns of the coarsest (direct) level */
+  int components;      /* gas components used as deflation vectors (0: deflation off) */
 } mp_stats;
 
 typedef struct mp_poisson *mp_handle;
@@ -182,6 +191,13 @@ mp_status mp_poisson_get_fields(mp_handle hd, double *kappa_dev, double *bx_dev,
 
 /* Statistics of the last solve. */
 mp_status mp_poisson_get_stats(mp_handle hd, mp_stats *st);
+
+/* Connected gas components of the current geometry (face neighbours, periodic
+ * axes wrapped): comp_dev (device, N int32, may be NULL) gets each cell's
+ * component id (0..m-1 in the order of each component's lowest cell index,
+ * -1 for liquid); m (host) gets the count.  m = 0 when deflation is off for
+ * this geometry (no gas, or more than 4096 components). */
+mp_status mp_poisson_get_components(mp_handle hd, int *comp_dev, int *m);
 
 /* Per-(kernel, level) launch record, filled by mp_poisson_get_profile. */
 typedef struct {

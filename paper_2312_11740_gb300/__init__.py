@@ -12,6 +12,7 @@ from .poisson import (  # noqa: F401
     mp_poisson_apply,
     mp_poisson_destroy,
     mp_poisson_divergence,
+    mp_poisson_get_components,
     mp_poisson_get_fields,
     mp_poisson_get_profile,
     mp_poisson_get_stats,

@@ -42,6 +42,7 @@ class mp_opts(ctypes.Structure):
         ("inner_rtol", ctypes.c_double),
         ("inner_max", ctypes.c_int),
         ("net_check", ctypes.c_int),
+        ("deflate", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -56,6 +57,7 @@ class mp_stats(ctypes.Structure):
         ("net_relres", ctypes.c_double),
         ("levels", ctypes.c_int),
         ("coarse_n", ctypes.c_int),
+        ("components", ctypes.c_int),
     ]
 
 
@@ -98,6 +100,7 @@ SIGNATURES = {
     "mp_poisson_rhs_noalloc": (_I, [ctypes.c_longlong, _P, _P, _P, _P]),
     "mp_poisson_destroy": (None, [_P]),
     "mp_poisson_set_net": (_I, [_P, _P]),
+    "mp_poisson_get_components": (_I, [_P, _P, _IP]),
     "mp_conv3d_fwd": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _P, _I, _I, _P, _P, _P]),
     "mp_conv3d_wgrad": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P, _P]),
     "mp_net_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _P]),

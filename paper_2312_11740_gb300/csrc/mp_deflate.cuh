@@ -1,0 +1,442 @@
+// Deflation of the MG-preconditioned CG by the gas components (bubbles).
+//
+// At density ratio 1000 the slowest error components of the V-cycle are the
+// pressure levels of the individual gas regions: inside a bubble the
+// coefficient is 1000x that of the liquid, the level is set only through the
+// thin interface layer, and after two or three coarsenings a small bubble is
+// no longer resolved by the coarse grids.  CG is therefore deflated by the
+// indicator vectors z_j of the connected gas components (Tang & Vuik's
+// deflated PCG for bubbly flows): with Z = [z_1 .. z_m], E = Z^T A Z and
+// P = I - A Z E^-1 Z^T, CG solves P A x = P b and the solution is
+// x + Z E^-1 Z^T (b - A x).  Components never share a face, so E is diagonal
+// (E_jj = -sum of the face coefficients on component j's boundary), and for
+// any v the products Z^T A v and A Z c are nonzero only on the band of cells
+// with a face to another component (or to liquid): the per-iteration work is a
+// few passes over that band, not over the grid.
+//
+// Components come from a union-find labelling of the gas cells (lowest cell
+// index as root); ids follow the roots' cell order, and every sum over cells
+// uses fixed-point int64 atomics, so results are bitwise reproducible.
+#pragma once
+
+namespace mp {
+
+constexpr int DEFL_MAX = 4096;          // components handled (more: deflation off)
+constexpr int DEFL_REP = 16;            // replicas of each accumulator (atomic contention)
+constexpr int CCL_FIND_LIMIT = 8192;    // bound on a find walk (path halving keeps walks short)
+constexpr int CCL_UNITE_LIMIT = 512;    // bound on the retries of one union
+constexpr int SCAN_THREADS = 1024;
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// root of x.  Labels only decrease (lab[x] <= x always), so walks end at a
+// root; path halving (lab[x] <- lab[lab[x]], by atomicMin) keeps them short.
+__device__ __forceinline__ int ccl_find(int *lab, int x, int *err) {
+  for (int it = 0; it < CCL_FIND_LIMIT; ++it) {
+    const int p = ld_volatile(lab + x);
+    if (p == x) return x;
+    const int g = ld_volatile(lab + p);
+    if (g < p) atomicMin(lab + x, g);
+    x = p;
+  }
+  atomicExch(err, 1);
+  return x;
+}
+
+// union of the components of a and b: the larger root is hooked under the
+// smaller with atomicMin, retried on the new root if another thread got there
+__device__ void ccl_unite(int *lab, int a, int b, int *err) {
+  for (int it = 0; it < CCL_UNITE_LIMIT; ++it) {
+    a = ccl_find(lab, a, err);
+    b = ccl_find(lab, b, err);
+    if (a == b) return;
+    if (a < b) {
+      const int old = atomicMin(lab + b, a);
+      if (old == b) return;
+      b = old;
+    } else {
+      const int old = atomicMin(lab + a, b);
+      if (old == a) return;
+      a = old;
+    }
+  }
+  atomicExch(err, 1);
+}
+
+__global__ void k_ccl_init(const double *__restrict__ phi, int *__restrict__ lab, size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x)
+    lab[c] = gas(phi[c]) ? (int)c : -1;
+}
+
+// unite every gas cell with its gas neighbours in +x, +y, +z (wrapping on
+// periodic axes only)
+__global__ void k_ccl_merge(int *lab, Dims d, int per, int *err) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nx || j >= d.ny) return;
+  const int c = (int)at(d, i, j, k);
+  if (ld_volatile(lab + c) < 0) return;
+  if (i + 1 < d.nx || (per & 1)) {
+    const int nb = (int)at(d, whi(i, d.nx), j, k);
+    if (ld_volatile(lab + nb) >= 0) ccl_unite(lab, c, nb, err);
+  }
+  if (j + 1 < d.ny || (per & 2)) {
+    const int nb = (int)at(d, i, whi(j, d.ny), k);
+    if (ld_volatile(lab + nb) >= 0) ccl_unite(lab, c, nb, err);
+  }
+  if (k + 1 < d.nz || (per & 4)) {
+    const int nb = (int)at(d, i, j, whi(k, d.nz));
+    if (ld_volatile(lab + nb) >= 0) ccl_unite(lab, c, nb, err);
+  }
+}
+
+__global__ void k_ccl_flatten(int *lab, size_t n, int *err) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x)
+    if (lab[c] >= 0) lab[c] = ccl_find(lab, (int)c, err);
+}
+
+// ---------------------------------------------- ordered compaction (scan)
+// flag(c): kind 0 = component root (lab[c] == c); kind 1 = band cell (a face
+// neighbour, wrapped as in the stencils, has another component id)
+__device__ __forceinline__ bool defl_flag(int kind, const int *lab, const int *comp, const Dims &d,
+                                          size_t c) {
+  if (kind == 0) return lab[c] == (int)c;
+  const int i = (int)(c % d.nx), j = (int)((c / d.nx) % d.ny), k = (int)(c / ((size_t)d.nx * d.ny));
+  const int m = comp[c];
+  return comp[at(d, wlo(i, d.nx), j, k)] != m || comp[at(d, whi(i, d.nx), j, k)] != m ||
+         comp[at(d, i, wlo(j, d.ny), k)] != m || comp[at(d, i, whi(j, d.ny), k)] != m ||
+         comp[at(d, i, j, wlo(k, d.nz))] != m || comp[at(d, i, j, whi(k, d.nz))] != m;
+}
+
+// per-block count of flagged cells (256 cells per block, cell order)
+__global__ void k_flag_count(int kind, const int *__restrict__ lab, const int *__restrict__ comp,
+                             Dims d, size_t n, int *__restrict__ cnt) {
+  const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const int f = c < n && defl_flag(kind, lab, comp, d, c);
+  const int s = __syncthreads_count(f);
+  if (threadIdx.x == 0) cnt[blockIdx.x] = s;
+}
+
+// exclusive scan of nb block counts in place (one block), total -> *total
+__global__ void k_scan_counts(int *cnt, int nb, int *total) {
+  __shared__ int part[SCAN_THREADS];
+  const int t = threadIdx.x;
+  const int per = (nb + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int lo = t * per, hi = min(nb, lo + per);
+  int s = 0;
+  for (int e = lo; e < hi; ++e) s += cnt[e];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < SCAN_THREADS; o <<= 1) {  // inclusive Hillis-Steele scan
+    const int v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - s;  // exclusive start of this thread's chunk
+  for (int e = lo; e < hi; ++e) {
+    const int v = cnt[e];
+    cnt[e] = run;
+    run += v;
+  }
+  if (t == SCAN_THREADS - 1) *total = part[t];
+}
+
+// write the flagged cells' ordinals: kind 0 -> comp[root] = id; kind 1 -> list[id] = c
+__global__ void k_flag_assign(int kind, const int *__restrict__ lab, int *__restrict__ comp,
+                              Dims d, size_t n, const int *__restrict__ off,
+                              int *__restrict__ list) {
+  __shared__ int wcount[8];
+  const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const int f = c < n && defl_flag(kind, lab, comp, d, c);
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wcount[w] = __popc(bal);
+  __syncthreads();
+  int base = off[blockIdx.x];
+  for (int q = 0; q < w; ++q) base += wcount[q];
+  const int id = base + __popc(bal & ((1u << lane) - 1u));
+  if (f) {
+    if (kind == 0)
+      comp[c] = id;
+    else
+      list[id] = (int)c;
+  }
+}
+
+// comp[c] = id of c's root (roots already hold their id), -1 for liquid
+__global__ void k_comp_from_roots(const int *__restrict__ lab, int *comp, size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int r = lab[c];
+    comp[c] = r < 0 ? -1 : comp[r];
+  }
+}
+
+// ----------------------------------------- fixed-point deterministic sums
+// A sum is accumulated as v * scale in two int64 words per replica: the
+// nearest integer (hi) and the remaining fraction in units of 2^-28 (lo).
+// The caller's scale bounds |sum of v * scale| by 2^60, so hi cannot
+// overflow; the fraction word extends the resolution to 2^-88 of that bound,
+// which keeps the sums exact to FP64 rounding even when the bound is far above
+// the sum (a whole-grid bound for a small bubble).  Integer addition is
+// associative, so every sum is bitwise reproducible.
+constexpr double FX_LO = 268435456.0;  // 2^28
+
+__device__ __forceinline__ unsigned long long *fx_slot(unsigned long long *acc, int j, int rep) {
+  return acc + ((size_t)j * DEFL_REP + rep) * 2;
+}
+__device__ __forceinline__ void fx_add(unsigned long long *acc, int j, double v, double scale) {
+  const double y = v * scale;
+  const double yh = rint(y);
+  const long long hi = (long long)yh;
+  const long long lo = llrint((y - yh) * FX_LO);  // y - yh is exact
+  unsigned long long *a = fx_slot(acc, j, blockIdx.x % DEFL_REP);
+  if (hi != 0) atomicAdd(a, (unsigned long long)hi);
+  if (lo != 0) atomicAdd(a + 1, (unsigned long long)lo);
+}
+// the sum of component j (clear: zero its words after reading)
+__device__ __forceinline__ double fx_value(unsigned long long *acc, int j, double scale,
+                                           bool clear) {
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int q = 0; q < DEFL_REP; ++q) {
+    unsigned long long *a = fx_slot(acc, j, q);
+    hi += (long long)a[0];
+    lo += (long long)a[1];
+    if (clear) a[0] = a[1] = 0ull;
+  }
+  return ((double)hi + (double)lo / FX_LO) / scale;
+}
+
+// (A z_j)_c of band cell c for every component j it touches (A = sum_f
+// beta_f (x_nb - x_c)): slot f < 6 holds +beta_f for the component k_f of a
+// face neighbour outside comp(c); slot 6 holds, for c in component m, minus
+// the sum of its faces to other ids.  k = -1 marks an empty slot.
+template <typename F>
+__device__ __forceinline__ void band_row(const F *__restrict__ bx, const F *__restrict__ by,
+                                         const F *__restrict__ bz, const int *__restrict__ comp,
+                                         const Dims &d, size_t c, int ks[7], double ws[7]) {
+  const int i = (int)(c % d.nx), j = (int)((c / d.nx) % d.ny), k = (int)(c / ((size_t)d.nx * d.ny));
+  const int m = comp[c];
+  const size_t nb[6] = {at(d, wlo(i, d.nx), j, k), at(d, whi(i, d.nx), j, k),
+                        at(d, i, wlo(j, d.ny), k), at(d, i, whi(j, d.ny), k),
+                        at(d, i, j, wlo(k, d.nz)), at(d, i, j, whi(k, d.nz))};
+  const double w[6] = {(double)bx[c], (double)bx[nb[1]], (double)by[c],
+                       (double)by[nb[3]], (double)bz[c], (double)bz[nb[5]]};
+  double self = 0.0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int mk = comp[nb[f]];
+    const bool cross = mk != m && w[f] != 0.0;
+    if (cross && m >= 0) self += w[f];
+    ks[f] = cross && mk >= 0 ? mk : -1;
+    ws[f] = w[f];
+  }
+  ks[6] = m >= 0 && self != 0.0 ? m : -1;
+  ws[6] = -self;
+}
+
+// Warp-aggregated fixed-point add of the (ks[f], vals[f]) pairs of every lane:
+// the contributions to the warp's leading component (the first one met in
+// lane order) are summed across the warp in a fixed shuffle tree and added
+// once; the others are added per lane.  Called by all 32 lanes.
+__device__ __forceinline__ void fx_add_warp(unsigned long long *acc, const int ks[7],
+                                            const double vals[7], double scale) {
+  int mine = -1;
+#pragma unroll
+  for (int f = 0; f < 7; ++f)
+    if (mine < 0 && ks[f] >= 0) mine = ks[f];
+  const unsigned has = __ballot_sync(0xffffffffu, mine >= 0);
+  if (has == 0u) return;
+  const int mm = __shfl_sync(0xffffffffu, mine, __ffs(has) - 1);
+  double s = 0.0;
+  bool other = false;
+#pragma unroll
+  for (int f = 0; f < 7; ++f) {
+    if (ks[f] == mm)
+      s += vals[f];
+    else if (ks[f] >= 0)
+      other = true;
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0 && s != 0.0) fx_add(acc, mm, s, scale);
+  if (other) {
+#pragma unroll
+    for (int f = 0; f < 7; ++f)
+      if (ks[f] >= 0 && ks[f] != mm) fx_add(acc, ks[f], vals[f], scale);
+  }
+}
+
+// E_jj = z_j^T A z_j over the band (fixed point, scale)
+template <typename F>
+__global__ void k_defl_E(const int *__restrict__ band, int nband, const int *__restrict__ comp,
+                         const F *__restrict__ bx, const F *__restrict__ by,
+                         const F *__restrict__ bz, Dims d, unsigned long long *acc, double scale) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < nband; e0 += stride) {
+    const int e = e0 + (threadIdx.x & 31);
+    int ks[7];
+    double ws[7];
+#pragma unroll
+    for (int f = 0; f < 7; ++f) ks[f] = -1, ws[f] = 0.0;
+    if (e < nband) band_row(bx, by, bz, comp, d, (size_t)band[e], ks, ws);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) ks[f] = -1;  // only the diagonal term z_j^T A z_j
+    fx_add_warp(acc, ks, ws, scale);
+  }
+}
+
+// max |v| over the band (as the ordered bits of a non-negative double)
+template <typename T>
+__global__ void k_defl_maxabs(const int *__restrict__ band, int nband, const T *__restrict__ v,
+                              unsigned long long *mx) {
+  double m = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nband; e += gridDim.x * blockDim.x)
+    m = fmax(m, fabs((double)v[band[e]]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+// sums[j] += sum over the band of (A z_j)_c v_c  ( = (A Z)^T v ), scale from the
+// band maximum of |v| (6 faces of at most beta_max each)
+template <typename T, typename F>
+__global__ void k_defl_azt(const int *__restrict__ band, int nband, const int *__restrict__ comp,
+                           const F *__restrict__ bx, const F *__restrict__ by,
+                           const F *__restrict__ bz, Dims d, const T *__restrict__ v,
+                           const unsigned long long *__restrict__ mx, double beta_max,
+                           unsigned long long *acc, double *scale_out) {
+  const double vmax = __longlong_as_double((long long)*mx);
+  const double bound = vmax * 6.0 * beta_max * (double)nband;
+  const double scale = bound > 0.0 ? ldexp(1.0, 60) / bound : 1.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale_out = scale;
+  const int stride = gridDim.x * blockDim.x;
+  for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < nband; e0 += stride) {
+    const int e = e0 + (threadIdx.x & 31);
+    int ks[7];
+    double ws[7];
+#pragma unroll
+    for (int f = 0; f < 7; ++f) ks[f] = -1, ws[f] = 0.0;
+    if (e < nband) {
+      const size_t c = (size_t)band[e];
+      band_row(bx, by, bz, comp, d, c, ks, ws);
+      const double vc = (double)v[c];
+#pragma unroll
+      for (int f = 0; f < 7; ++f) ws[f] *= vc;
+    }
+    fx_add_warp(acc, ks, ws, scale);
+  }
+}
+
+// sums[j] += sum of v over all cells of component j (|sum| bounded by the caller's scale)
+template <typename T>
+__global__ void k_defl_zt(const int *__restrict__ comp, const T *__restrict__ v, size_t n,
+                          unsigned long long *acc, double scale) {
+  for (size_t c0 = blockIdx.x * (size_t)blockDim.x; c0 < n; c0 += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = c0 + threadIdx.x;
+    const int m = c < n ? comp[c] : -1;
+    const double val = m >= 0 ? (double)v[c] : 0.0;
+    // a full warp whose gas cells all lie in one component adds its sum once
+    const unsigned gasl = __ballot_sync(0xffffffffu, m >= 0);
+    if (gasl == 0u) continue;
+    const int mm = __shfl_sync(0xffffffffu, m, __ffs(gasl) - 1);
+    if (__all_sync(0xffffffffu, m < 0 || m == mm)) {
+      const double s = warp_sum(val);
+      if ((threadIdx.x & 31) == 0) fx_add(acc, mm, s, scale);
+    } else if (m >= 0) {
+      fx_add(acc, m, val, scale);
+    }
+  }
+}
+
+// c_j = E_jj^-1 (s_j - t_j): s from the sum sa (scale *scale_a, or fixed_scale_a
+// when scale_a is null), t from the sum sb (scale *scale_b), either may be
+// absent.  The per-projection sums (sb, or sa when clear_a) and the band
+// maximum mx are zeroed for the next projection.
+__global__ void k_defl_coef(int m, unsigned long long *sa, const double *scale_a,
+                            double fixed_scale_a, int clear_a, unsigned long long *sb,
+                            const double *scale_b, const double *__restrict__ einv,
+                            double *__restrict__ coef, unsigned long long *mx) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) *mx = 0ull;
+  if (j >= m) return;
+  double s = 0.0;
+  if (sa) s = fx_value(sa, j, scale_a ? *scale_a : fixed_scale_a, clear_a != 0);
+  if (sb) s -= fx_value(sb, j, *scale_b, true);
+  coef[j] = einv[j] * s;
+}
+
+// v_c -= (A w)_c on the band, w = coef[comp] (0 in liquid); optional per-block
+// partial sums of u_c (A w)_c (the change of u.v)
+template <typename T, typename F>
+__global__ void k_defl_sub_aw(const int *__restrict__ band, int nband, const int *__restrict__ comp,
+                              const F *__restrict__ bx, const F *__restrict__ by,
+                              const F *__restrict__ bz, Dims d, const double *__restrict__ coef,
+                              T *__restrict__ v, const T *__restrict__ u,
+                              double *__restrict__ partial) {
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nband; e += gridDim.x * blockDim.x) {
+    const size_t c = (size_t)band[e];
+    const int i = (int)(c % d.nx), j = (int)((c / d.nx) % d.ny), k = (int)(c / ((size_t)d.nx * d.ny));
+    const int m = comp[c];
+    const double wc = m >= 0 ? coef[m] : 0.0;
+    const size_t nb[6] = {at(d, wlo(i, d.nx), j, k), at(d, whi(i, d.nx), j, k),
+                          at(d, i, wlo(j, d.ny), k), at(d, i, whi(j, d.ny), k),
+                          at(d, i, j, wlo(k, d.nz)), at(d, i, j, whi(k, d.nz))};
+    const double w[6] = {(double)bx[c], (double)bx[nb[1]], (double)by[c],
+                         (double)by[nb[3]], (double)bz[c], (double)bz[nb[5]]};
+    double aw = 0.0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int mk = comp[nb[f]];
+      const double wn = mk >= 0 ? coef[mk] : 0.0;
+      aw += w[f] * (wn - wc);
+    }
+    v[c] = (T)((double)v[c] - aw);
+    if (u) acc += (double)u[c] * aw;
+  }
+  if (partial) {
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
+// x_c += coef[comp_c] on every cell of a component (the deflation correction)
+__global__ void k_defl_add_z(double *__restrict__ x, const int *__restrict__ comp, size_t n,
+                             const double *__restrict__ coef) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int m = comp[c];
+    if (m >= 0) x[c] += coef[m];
+  }
+}
+
+// z_c -= coef[comp_c] on every cell of a component (z <- P^T z = z - Z E^-1 (A Z)^T z)
+template <typename T>
+__global__ void k_defl_sub_z(T *__restrict__ z, const int *__restrict__ comp, size_t n,
+                             const double *__restrict__ coef) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int m = comp[c];
+    if (m >= 0) z[c] = (T)((double)z[c] - coef[m]);
+  }
+}
+
+// E -> 1/E (fixed-point sums with a fixed scale; the sums are zeroed)
+__global__ void k_defl_einv(int m, unsigned long long *acc, double scale,
+                            double *__restrict__ einv) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const double e = fx_value(acc, j, scale, true);
+  einv[j] = e != 0.0 ? 1.0 / e : 0.0;
+}
+
+}  // namespace mp

@@ -588,7 +588,7 @@ __global__ void k_prolong_vec(T *__restrict__ x, const T *__restrict__ ec, Dims 
 // --------------------------------------------------------- Krylov kernels
 // Scalars kept on the device between kernels (no host round trip).
 enum { S_RZ = 0, S_RZOLD, S_DQ, S_ALPHA, S_BETA, S_RR, S_BB, S_MEAN, S_TMP, S_COUNT };
-enum { OP_STORE = 0, OP_ALPHA, OP_BETA, OP_MEAN };
+enum { OP_STORE = 0, OP_ALPHA, OP_BETA, OP_MEAN, OP_ALPHA_DEFL };
 
 // Stencil kernels with a reduction walk a column of `zper` planes per
 // thread (grid z = ceil(nz / zper)), so the partial-sum count stays ~2k.
@@ -800,6 +800,20 @@ __global__ void k_add_f32(double *__restrict__ x, float *__restrict__ e, size_t 
   }
 }
 
+// dst32 = fl32(src64), per-block partial of src.src (FP64)
+__global__ void k_to_f32_norm(const double *__restrict__ src, float *__restrict__ dst, size_t n,
+                              double *__restrict__ partial) {
+  double acc = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double v = src[e];
+    dst[e] = (float)v;
+    acc = fma(v, v, acc);
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 template <typename T>
 __global__ void k_sum(const T *__restrict__ a, size_t n, double *__restrict__ partial) {
   double acc = 0.0;
@@ -842,6 +856,10 @@ __global__ void k_reduce(const double *__restrict__ partial, int np, double *__r
         scal[S_BETA] = s / scal[S_RZOLD];
         break;
       case OP_MEAN: scal[S_MEAN] = s / count; break;
+      case OP_ALPHA_DEFL:  // d.(P A d) = d.(A d) (in S_DQ) - s
+        scal[S_DQ] -= s;
+        scal[S_ALPHA] = scal[S_RZ] / scal[S_DQ];
+        break;
     }
   }
 }

@@ -19,6 +19,7 @@
 #include "../../include/mp_net.h"
 #include "../../include/mp_poisson.h"
 #include "mp_kernels.cuh"
+#include "mp_deflate.cuh"
 
 using namespace mp;
 
@@ -42,7 +43,7 @@ enum KernelId {
   K_RBGS64, K_RBGS32, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
   K_APPLY64, K_APPLY32, K_RESID64, K_RESID32, K_RESIDMIX, K_DOT64, K_DOT32, K_AXPY64, K_AXPY32,
   K_XPBY64, K_XPBY32, K_ADD64, K_ADD32, K_ADDF32, K_SUM, K_SUBMEAN, K_REDUCE, K_ASSEMBLE,
-  K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_COUNT
+  K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_DEFL, K_COUNT
 };
 const char *const kKernelNames[K_COUNT] = {
   "curvature", "gfm_faces", "jump", "diag", "coarsen_faces", "dense_build", "gauss_jordan",
@@ -51,7 +52,8 @@ const char *const kKernelNames[K_COUNT] = {
   "prolong_f32", "coarse_solve_f64", "coarse_solve_f32io", "apply_dot_f64", "apply_dot_f32",
   "residual_f64", "residual_f32", "residual_mixed", "dot_f64", "dot_f32", "axpy2_f64",
   "axpy2_f32", "xpby_f64", "xpby_f32", "add_f64", "add_f32", "add_f32_to_f64", "sum",
-  "sub_mean", "reduce", "assemble", "assemble_u", "project", "divergence", "scale"};
+  "sub_mean", "reduce", "assemble", "assemble_u", "project", "divergence", "scale",
+  "deflation"};
 constexpr int MAX_LEVELS = 16;
 constexpr int EVENT_POOL = 4096;
 
@@ -90,6 +92,13 @@ struct mp_poisson {
   int npart = 0;
   double bnorm = 0.0;
   mp_stats stats{};
+  // deflation by the gas components (mp_deflate.cuh)
+  int *lab = nullptr, *comp = nullptr, *band = nullptr, *cnt = nullptr, *dint = nullptr;
+  int defl_m = 0, defl_nband = 0;
+  double beta_max = 1.0, ztb_scale = 1.0;
+  double *einv = nullptr, *coef = nullptr, *dscale = nullptr;
+  unsigned long long *acc_a = nullptr, *acc_b = nullptr, *acc_ztb = nullptr, *dmax = nullptr;
+  int *hint = nullptr;  // pinned host copy of dint
   mp_net_handle net = nullptr;  // learned initial guess (initial_guess = 2)
   int net_factor = 1;           // solver grid / network grid (1 or 2)
   std::vector<void *> allocs;
@@ -387,6 +396,150 @@ mp_status run_vcycle(mp_poisson *hd, const T *rhs, T *x) {
 
 bool bad(double v) { return !std::isfinite(v); }
 
+// ------------------------------------------------ deflation (mp_deflate.cuh)
+// bytes of the fixed-point sums of m components (two words per replica)
+size_t defl_acc_bytes(int m) { return (size_t)m * DEFL_REP * 2 * sizeof(unsigned long long); }
+
+// Gas components of the current geometry, their boundary band and E = Z^T A Z.
+// Deflation is off for this geometry (defl_m = 0) when there is no gas, more
+// than DEFL_MAX components, or a labelling loop ran out of its bound.
+mp_status deflation_setup(mp_poisson *hd) {
+  Level &l0 = hd->L[0];
+  const size_t n = hd->n;
+  const int nblk = (int)((n + 255) / 256);
+  hd->defl_m = 0;
+  hd->defl_nband = 0;
+  CK(cudaMemsetAsync(hd->dint, 0, 4 * sizeof(int), hd->st));
+  LAUNCH(hd, K_DEFL, 0, n * 12.0, k_ccl_init, VEC_BLOCKS, VEC_THREADS, hd->phi, hd->lab, n);
+  LAUNCH(hd, K_DEFL, 0, n * 16.0, k_ccl_merge, cell_grid(l0.d), kBlock, hd->lab, l0.d, hd->per,
+         hd->dint + 2);
+  LAUNCH(hd, K_DEFL, 0, n * 8.0, k_ccl_flatten, VEC_BLOCKS, VEC_THREADS, hd->lab, n, hd->dint + 2);
+  LAUNCH(hd, K_DEFL, 0, n * 4.0, k_flag_count, nblk, 256, 0, hd->lab, hd->comp, l0.d, n, hd->cnt);
+  LAUNCH(hd, K_DEFL, 0, nblk * 8.0, k_scan_counts, 1, SCAN_THREADS, hd->cnt, nblk, hd->dint);
+  LAUNCH(hd, K_DEFL, 0, n * 8.0, k_flag_assign, nblk, 256, 0, hd->lab, hd->comp, l0.d, n, hd->cnt,
+         (int *)nullptr);
+  LAUNCH(hd, K_DEFL, 0, n * 12.0, k_comp_from_roots, VEC_BLOCKS, VEC_THREADS, hd->lab, hd->comp,
+         n);
+  CK(cudaMemcpyAsync(hd->hint, hd->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost, hd->st));
+  CK(cudaStreamSynchronize(hd->st));
+  const int m = hd->hint[0];
+  if (hd->hint[2] != 0 || m <= 0 || m > DEFL_MAX) return MP_OK;
+  LAUNCH(hd, K_DEFL, 0, n * 28.0, k_flag_count, nblk, 256, 1, hd->lab, hd->comp, l0.d, n, hd->cnt);
+  LAUNCH(hd, K_DEFL, 0, nblk * 8.0, k_scan_counts, 1, SCAN_THREADS, hd->cnt, nblk, hd->dint + 1);
+  LAUNCH(hd, K_DEFL, 0, n * 28.0, k_flag_assign, nblk, 256, 1, hd->lab, hd->comp, l0.d, n, hd->cnt,
+         hd->band);
+  CK(cudaMemcpyAsync(hd->hint, hd->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost, hd->st));
+  CK(cudaStreamSynchronize(hd->st));
+  const int nband = hd->hint[1];
+  if (nband <= 0) return MP_OK;
+  // E_jj = -sum of the boundary faces (fixed point: |E| <= 6 beta_max nband)
+  const double escale = std::ldexp(1.0, 60) / (6.0 * hd->beta_max * (double)nband + 1.0);
+  CK(cudaMemsetAsync(hd->acc_a, 0, defl_acc_bytes(m), hd->st));
+  LAUNCH(hd, K_DEFL, 0, nband * 60.0, k_defl_E<double>, VEC_BLOCKS, VEC_THREADS, hd->band, nband,
+         hd->comp, l0.bx, l0.by, l0.bz, l0.d, hd->acc_a, escale);
+  LAUNCH(hd, K_DEFL, 0, m * 8.0, k_defl_einv, (m + 255) / 256, 256, m, hd->acc_a, escale,
+         hd->einv);
+  CKS(launch_ok());
+  hd->defl_m = m;
+  hd->defl_nband = nband;
+  return MP_OK;
+}
+
+bool defl_active(const mp_poisson *hd) {
+  return hd->opts.deflate && hd->opts.method == 0 && hd->defl_m > 0;
+}
+
+// Z^T b of the current right-hand side (fixed point, |b_c| <= ||b||).  Called
+// at the start of a deflated solve: also clears the per-projection sums and
+// the band maximum, which every projection leaves zeroed for the next.
+mp_status defl_ztb(mp_poisson *hd) {
+  const int m = hd->defl_m;
+  hd->ztb_scale = std::ldexp(1.0, 60) / ((double)hd->n * std::max(hd->bnorm, 1e-300));
+  CK(cudaMemsetAsync(hd->acc_ztb, 0, defl_acc_bytes(m), hd->st));
+  CK(cudaMemsetAsync(hd->acc_a, 0, defl_acc_bytes(m), hd->st));
+  CK(cudaMemsetAsync(hd->acc_b, 0, defl_acc_bytes(m), hd->st));
+  CK(cudaMemsetAsync(hd->dmax, 0, sizeof(unsigned long long), hd->st));
+  LAUNCH(hd, K_DEFL, 0, hd->n * 12.0, k_defl_zt<double>, VEC_BLOCKS, VEC_THREADS, hd->comp, hd->b,
+         hd->n, hd->acc_ztb, hd->ztb_scale);
+  return launch_ok();
+}
+
+// coef = E^-1 (A Z)^T v on the band (minus_ztb: coef = E^-1 (Z^T b - (A Z)^T v),
+// i.e. for v = x, E^-1 Z^T (b - A x))
+template <typename T, typename F>
+mp_status defl_coef(mp_poisson *hd, const T *v, const F *bx, const F *by, const F *bz,
+                    bool with_ztb) {
+  Level &l0 = hd->L[0];
+  const int m = hd->defl_m, nb = hd->defl_nband;
+  unsigned long long *acc = with_ztb ? hd->acc_b : hd->acc_a;
+  LAUNCH(hd, K_DEFL, 0, nb * (double)sizeof(T), k_defl_maxabs<T>, VEC_BLOCKS, VEC_THREADS,
+         hd->band, nb, v, hd->dmax);
+  auto kazt = k_defl_azt<T, F>;
+  LAUNCH(hd, K_DEFL, 0, nb * (7.0 * sizeof(T) + 3.0 * sizeof(F) + 28.0), kazt, VEC_BLOCKS,
+         VEC_THREADS, hd->band, nb, hd->comp, bx, by, bz, l0.d, v, hd->dmax, hd->beta_max, acc,
+         hd->dscale);
+  if (with_ztb)
+    LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, hd->acc_ztb,
+           (const double *)nullptr, hd->ztb_scale, 0, acc, hd->dscale, hd->einv, hd->coef,
+           hd->dmax);
+  else
+    LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, acc, hd->dscale, 0.0, 1,
+           (unsigned long long *)nullptr, (const double *)nullptr, hd->einv, hd->coef, hd->dmax);
+  return launch_ok();
+}
+
+// v -= A Z coef on the band; with u, per-block partials of u.(A Z coef) in hd->partial
+template <typename T, typename F>
+mp_status defl_sub(mp_poisson *hd, T *v, const T *u, const F *bx, const F *by, const F *bz) {
+  Level &l0 = hd->L[0];
+  const int nb = hd->defl_nband;
+  auto ksub = k_defl_sub_aw<T, F>;
+  LAUNCH(hd, K_DEFL, 0, nb * (3.0 * sizeof(T) + 3.0 * sizeof(F) + 28.0), ksub, VEC_BLOCKS,
+         VEC_THREADS, hd->band, nb, hd->comp, bx, by, bz, l0.d, hd->coef, v, u,
+         u ? hd->partial : (double *)nullptr);
+  return launch_ok();
+}
+
+// x += Z E^-1 Z^T (b - A x): the deflation correction of the final iterate
+mp_status defl_finish(mp_poisson *hd, double *x) {
+  Level &l0 = hd->L[0];
+  CKS((defl_coef<double, double>(hd, x, l0.bx, l0.by, l0.bz, true)));
+  LAUNCH(hd, K_DEFL, 0, hd->n * 12.0, k_defl_add_z, VEC_BLOCKS, VEC_THREADS, x, hd->comp, hd->n,
+         hd->coef);
+  return launch_ok();
+}
+
+// The residuals deflated CG starts from, for the guess p and for the zero
+// guess: ||P (bt - At p)|| and ||P bt|| (P = I - At Z E^-1 Z^T), formed in FP64
+// in the scratch vector hd->z.  Uses hd->q as scratch too.
+mp_status defl_guess_residuals(mp_poisson *hd, const double *p, double *rguess, double *rzero) {
+  Level &l0 = hd->L[0];
+  const size_t n = hd->n;
+  CKS(defl_ztb(hd));
+  LAUNCH(hd, K_RESID64, 0, n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b, hd->z,
+         l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+  CKS((defl_coef<double, double>(hd, p, l0.bx, l0.by, l0.bz, true)));
+  CKS((defl_sub<double, double>(hd, hd->z, (const double *)nullptr, l0.bx, l0.by, l0.bz)));
+  LAUNCH(hd, K_DOT64, 0, n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, hd->z, hd->z, n,
+         hd->partial);
+  CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_TMP));
+  CKS(read_scalars(hd));
+  *rguess = std::sqrt(hd->scal_h[S_TMP]);
+  // zero guess: coef = E^-1 Z^T bt, P bt = bt - At Z coef
+  const int m = hd->defl_m;
+  LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, hd->acc_ztb,
+         (const double *)nullptr, hd->ztb_scale, 0, (unsigned long long *)nullptr,
+         (const double *)nullptr, hd->einv, hd->coef, hd->dmax);
+  CK(cudaMemcpyAsync(hd->z, hd->b, n * sizeof(double), cudaMemcpyDeviceToDevice, hd->st));
+  CKS((defl_sub<double, double>(hd, hd->z, (const double *)nullptr, l0.bx, l0.by, l0.bz)));
+  LAUNCH(hd, K_DOT64, 0, n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, hd->z, hd->z, n,
+         hd->partial);
+  CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_TMP));
+  CKS(read_scalars(hd));
+  *rzero = std::sqrt(hd->scal_h[S_TMP]);
+  return MP_OK;
+}
+
 // Preconditioned CG on At x = (rhs), starting from x with residual r already
 // formed and scal[S_RR] = r.r.  Stops when sqrt(r.r) <= tol_abs or after
 // maxit iterations.  hist (may be null) receives sqrt(r.r)/bnorm.
@@ -396,18 +549,29 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
   Level &l0 = hd->L[0];
   T *bx = LV<T>::bx(l0), *by = LV<T>::by(l0), *bz = LV<T>::bz(l0), *diag = LV<T>::diag(l0);
   size_t n = hd->n;
+  const double nsz = (double)n * sizeof(T);
+  // deflated CG (FP64): r <- P r, iterate on P A, finish with x += Z E^-1 Z^T (b - A x)
+  const bool defl = sizeof(T) == 8 && defl_active(hd);
+  if (defl) {
+    CKS(defl_ztb(hd));
+    CKS((defl_coef<T, T>(hd, x, bx, by, bz, true)));
+    CKS((defl_sub<T, T>(hd, r, (const T *)nullptr, bx, by, bz)));
+    LAUNCH(hd, kid<T>(K_DOT64, K_DOT32), 0, 2.0 * nsz, k_dot<T>, VEC_BLOCKS, VEC_THREADS, r, r, n,
+           hd->partial);
+    CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
+  }
   int it = 0;
+  mp_status st = MP_OK;
   CKS(read_scalars(hd));
   double rn = std::sqrt(hd->scal_h[S_RR]);
   while (true) {
     if (bad(rn)) return MP_ERR_DIVERGED;
     if (rn <= tol_abs) break;
     if (it >= maxit) {
-      *iters = it;
-      return MP_ERR_NOT_CONVERGED;
+      st = MP_ERR_NOT_CONVERGED;
+      break;
     }
     CKS(run_vcycle<T>(hd, r, z));
-    const double nsz = (double)n * sizeof(T);
     LAUNCH(hd, kid<T>(K_DOT64, K_DOT32), 0, 2.0 * nsz, k_dot<T>, VEC_BLOCKS, VEC_THREADS, r, z, n,
            hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
@@ -416,7 +580,14 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
     LAUNCH(hd, kid<T>(K_APPLY64, K_APPLY32), 0, (sizeof(T) == 8 ? 6.0 : 5.0) * nsz,
            k_apply_dot<T>, zgrid(l0.d), kBlock, dv, q, bx, by, bz, diag, l0.d, zper_of(l0.d),
            hd->partial);
-    CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
+    if (defl) {  // q <- P q = q - A Z E^-1 (A Z)^T d; alpha = rz / (d . P q)
+      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_DQ));
+      CKS((defl_coef<T, T>(hd, dv, bx, by, bz, false)));
+      CKS((defl_sub<T, T>(hd, q, dv, bx, by, bz)));
+      CKS(reduce(hd, VEC_BLOCKS, OP_ALPHA_DEFL, 0));
+    } else {
+      CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
+    }
     LAUNCH(hd, kid<T>(K_AXPY64, K_AXPY32), 0, 6.0 * nsz, k_axpy2<T>, VEC_BLOCKS, VEC_THREADS, x,
            r, dv, q, n, hd->scal, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
@@ -425,8 +596,9 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
     rn = std::sqrt(hd->scal_h[S_RR]);
     if (hist) hist->push_back(rn * hist_scale);
   }
+  if (defl) CKS(defl_finish(hd, reinterpret_cast<double *>(x)));
   *iters = it;
-  return MP_OK;
+  return st;
 }
 
 // Mixed-precision PCG with reliable updates.  The Krylov iteration (V-cycle
@@ -446,19 +618,46 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
   const double nsz = (double)n * sizeof(float);
   float *e = hd->e32, *r = hd->r32, *z = hd->z32, *dv = hd->d32, *q = hd->q32;
   int it = 0, nrep = 0, since = 0;
-  double rn_rep = rn, rec = rn;
   mp_status st = MP_OK;
+  // deflated: every true residual is projected, r32 = fl32(P (bt - At p)), with
+  // Z^T (bt - At p) = Z^T bt - (At Z)^T p from FP64 p; the iteration uses P At
+  // in FP32; the exit adds Z E^-1 Z^T (bt - At p) to p
+  const bool defl = defl_active(hd);
+  // the true residual is projected in FP64 and rounded afterwards: near the
+  // components both bt - At p and A Z c are large, and rounding before the
+  // subtraction would leave their FP32 rounding error in the projected residual
+  auto project_true = [&](double &rnorm) -> mp_status {
+    LAUNCH(hd, K_RESID64, 0, n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b, hd->r,
+           l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+    CKS((defl_coef<double, double>(hd, p, l0.bx, l0.by, l0.bz, true)));
+    CKS((defl_sub<double, double>(hd, hd->r, (const double *)nullptr, l0.bx, l0.by, l0.bz)));
+    LAUNCH(hd, K_RESIDMIX, 0, n * 12.0, k_to_f32_norm, VEC_BLOCKS, VEC_THREADS, hd->r, r, n,
+           hd->partial);
+    CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
+    CKS(read_scalars(hd));
+    rnorm = std::sqrt(hd->scal_h[S_RR]);
+    return MP_OK;
+  };
+  if (defl) {
+    CKS(defl_ztb(hd));
+    CKS(project_true(rn));
+  }
+  double rn_rep = rn, rec = rn;
   CK(cudaMemsetAsync(e, 0, n * sizeof(float), hd->st));
   while (true) {
     if (since > 0 && (rec <= std::fmax(o.inner_rtol * rn_rep, 0.5 * tol_abs) ||
                       since >= o.inner_max || it >= maxit)) {
       // reliable update: p += e32 (e32 = 0), r32 = bt - At p from FP64
       LAUNCH(hd, K_ADDF32, 0, n * 24.0, k_add_f32, VEC_BLOCKS, VEC_THREADS, p, e, n);
-      LAUNCH(hd, K_RESIDMIX, 0, n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b, r,
-             l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
-      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
-      CKS(read_scalars(hd));
-      rn = std::sqrt(hd->scal_h[S_RR]);
+      if (defl) {
+        CKS(project_true(rn));
+      } else {
+        LAUNCH(hd, K_RESIDMIX, 0, n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b, r,
+               l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+        CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
+        CKS(read_scalars(hd));
+        rn = std::sqrt(hd->scal_h[S_RR]);
+      }
       rn_rep = rec = rn;
       since = 0;
       ++nrep;
@@ -468,13 +667,28 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
     if (since == 0 && rn <= tol_abs) break;  // converged on a true residual
     if (it >= maxit) { st = MP_ERR_NOT_CONVERGED; break; }
     CKS(run_vcycle<float>(hd, r, z));
+    if (defl) {
+      // z <- P^T z (balancing form): keeps every direction A-orthogonal to the
+      // components; without it the directions drift in span(Z), which P A does
+      // not see, until the drift swamps the FP32 correction
+      CKS((defl_coef<float, float>(hd, z, l0.bx32, l0.by32, l0.bz32, false)));
+      LAUNCH(hd, K_DEFL, 0, n * 8.0, k_defl_sub_z<float>, VEC_BLOCKS, VEC_THREADS, z, hd->comp, n,
+             hd->coef);
+    }
     LAUNCH(hd, K_DOT32, 0, 2.0 * nsz, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, z, n, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
     LAUNCH(hd, K_XPBY32, 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<float>, VEC_BLOCKS, VEC_THREADS,
            dv, z, n, hd->scal, it == 0);
     LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot<float>, zgrid(l0.d), kBlock, dv, q, l0.bx32,
            l0.by32, l0.bz32, (float *)nullptr, l0.d, zper_of(l0.d), hd->partial);
-    CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
+    if (defl) {  // q <- P q; alpha = rz / (d . P q)
+      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_DQ));
+      CKS((defl_coef<float, float>(hd, dv, l0.bx32, l0.by32, l0.bz32, false)));
+      CKS((defl_sub<float, float>(hd, q, dv, l0.bx32, l0.by32, l0.bz32)));
+      CKS(reduce(hd, VEC_BLOCKS, OP_ALPHA_DEFL, 0));
+    } else {
+      CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
+    }
     LAUNCH(hd, K_AXPY32, 0, 6.0 * nsz, k_axpy2<float>, VEC_BLOCKS, VEC_THREADS, e, r, dv, q, n,
            hd->scal, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
@@ -483,6 +697,7 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
     CKS(read_scalars(hd));
     rec = std::sqrt(hd->scal_h[S_RR]);
   }
+  if (defl && st != MP_ERR_DIVERGED) CKS(defl_finish(hd, p));
   *iters = it;
   *outer = nrep;
   return st;
@@ -563,6 +778,7 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
   hd->stats = mp_stats{};
   hd->stats.levels = (int)hd->L.size();
   hd->stats.coarse_n = hd->nc;
+  hd->stats.components = defl_active(hd) ? hd->defl_m : 0;
   if (o.initial_guess == 2 && !hd->net) return MP_ERR_NO_NET;
   int zero = o.initial_guess == 0;
   if (zero) CK(cudaMemsetAsync(p, 0, hd->n * sizeof(double), hd->st));
@@ -605,9 +821,11 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
              hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
     CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
     CKS(read_scalars(hd));
-    const double rnet = std::sqrt(hd->scal_h[S_RR]);
-    hd->stats.net_relres = rnet / hd->bnorm;
-    const bool keep = o.net_check == 0 ? rnet < hd->bnorm : alpha != 0.0;
+    double rnet = std::sqrt(hd->scal_h[S_RR]), rzero = hd->bnorm;
+    if (defl_active(hd) && o.net_check == 0 && std::isfinite(rnet))
+      CKS(defl_guess_residuals(hd, p, &rnet, &rzero));
+    hd->stats.net_relres = rnet / rzero;
+    const bool keep = o.net_check == 0 ? rnet < rzero : alpha != 0.0;
     if (keep && std::isfinite(rnet)) {
       hd->stats.used_net = 1;
       have_r = true;
@@ -696,7 +914,8 @@ bool valid_opts(const mp_opts &o) {
   return (o.precision == 0 || o.precision == 1) && (o.method == 0 || o.method == 1) &&
          o.initial_guess >= 0 && o.initial_guess <= 2 && o.max_iters >= 0 && o.nu1 >= 1 &&
          o.nu2 >= 1 && o.nu_growth >= 1 && o.nu_max >= 1 && o.inner_rtol > 0.0 &&
-         o.inner_rtol < 1.0 && o.inner_max >= 1 && (o.net_check == 0 || o.net_check == 1);
+         o.inner_rtol < 1.0 && o.inner_max >= 1 && (o.net_check == 0 || o.net_check == 1) &&
+         (o.deflate == 0 || o.deflate == 1);
 }
 
 void apply_nu(mp_poisson *hd) {
@@ -743,6 +962,8 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
          lc.by, lc.bz, lc.diag, hd->Maug, lc.d);
   LAUNCH(hd, K_GJ, lcl, nc * 3.0 * nc * 8.0, k_gauss_jordan, 1, 1024, hd->Maug, hd->Minv, hd->nc);
   CKS(launch_ok());
+  hd->beta_max = std::max(1.0 / rho_l, 1.0 / rho_g);
+  CKS(deflation_setup(hd));
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);
   return MP_OK;
@@ -829,6 +1050,25 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
     return MP_ERR_OOM;
   }
   CK(cudaMemsetAsync(hd->scal, 0, S_COUNT * sizeof(double), hd->st));
+  // deflation workspace
+  const size_t nblk = (n + 255) / 256;
+  CKS(dalloc(hd, &hd->lab, n));
+  CKS(dalloc(hd, &hd->comp, n));
+  CKS(dalloc(hd, &hd->band, n));
+  CKS(dalloc(hd, &hd->cnt, nblk));
+  CKS(dalloc(hd, &hd->dint, 4));
+  CKS(dalloc(hd, &hd->einv, (size_t)DEFL_MAX));
+  CKS(dalloc(hd, &hd->coef, (size_t)DEFL_MAX));
+  CKS(dalloc(hd, &hd->dscale, 4));
+  CKS(dalloc(hd, &hd->acc_a, (size_t)DEFL_MAX * DEFL_REP * 2));
+  CKS(dalloc(hd, &hd->acc_b, (size_t)DEFL_MAX * DEFL_REP * 2));
+  CKS(dalloc(hd, &hd->acc_ztb, (size_t)DEFL_MAX * DEFL_REP * 2));
+  CKS(dalloc(hd, &hd->dmax, 2));
+  if (cudaMallocHost((void **)&hd->hint, 4 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    hd->hint = nullptr;
+    return MP_ERR_OOM;
+  }
   CK(cudaStreamCreateWithFlags(&hd->cap, cudaStreamNonBlocking));
   // coarse tail: the coarsest levels whose iterate, rhs and faces fit the
   // shared-memory budget of one block (coarsest level always included)
@@ -873,6 +1113,7 @@ void mp_opts_default(mp_opts *o) {
   o->inner_rtol = 1e-4;
   o->inner_max = 12;
   o->net_check = 0;
+  o->deflate = 1;
   o->stream = nullptr;
 }
 
@@ -1104,6 +1345,16 @@ mp_status mp_poisson_set_net(mp_handle hd, mp_net_handle net) {
   return MP_OK;
 }
 
+mp_status mp_poisson_get_components(mp_handle hd, int *comp_dev, int *m) {
+  if (!hd) return MP_ERR_INVALID_ARG;
+  if (comp_dev) {
+    CK(cudaMemcpyAsync(comp_dev, hd->comp, hd->n * sizeof(int), cudaMemcpyDeviceToDevice, hd->st));
+    CK(cudaStreamSynchronize(hd->st));
+  }
+  if (m) *m = hd->defl_m;
+  return MP_OK;
+}
+
 mp_status mp_poisson_get_stats(mp_handle hd, mp_stats *st) {
   if (!hd || !st) return MP_ERR_INVALID_ARG;
   *st = hd->stats;
@@ -1118,6 +1369,7 @@ void mp_poisson_destroy(mp_handle hd) {
   destroy_graphs(hd);
   if (hd->cap) cudaStreamDestroy(hd->cap);
   if (hd->scal_h) cudaFreeHost(hd->scal_h);
+  if (hd->hint) cudaFreeHost(hd->hint);
   delete hd;
 }
 

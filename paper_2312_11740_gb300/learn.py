@@ -140,9 +140,11 @@ def pg_forced(solver, rhs):
     return pg
 
 
-def evaluate(net, seeds, n, precision=0, stream=None, log=print):
+def evaluate(net, seeds, n, precision=0, stream=None, log=print, deflate=0):
     """Iterations to 1e-10 from the zero guess and from the learned guess,
-    and the learned guess's relative error against the converged pressure."""
+    and the learned guess's relative error against the converged pressure.
+    deflate = 0 evaluates against plain MG-preconditioned CG, the method the
+    network's targets and loss are set up for; 1 against the deflated solver."""
     dev = torch.device("cuda")
     h = 1.0 / n
     rows = []
@@ -151,6 +153,7 @@ def evaluate(net, seeds, n, precision=0, stream=None, log=print):
         phi, u, _ = geometry(seed, n, dev)
         if solver is None:
             solver = Poisson(phi, h, BC, RHO_L, RHO_G, SIGMA, precision=precision, stream=stream)
+            solver.set_opts(deflate=deflate)
             mp_poisson_set_net(solver.handle, net)
         else:
             solver.set_geometry(phi, RHO_L, RHO_G, SIGMA)
@@ -211,6 +214,8 @@ def main(argv=None):
     ap.add_argument("--lr-final", type=float, default=1e-4)
     ap.add_argument("--init-seed", type=int, default=7)
     ap.add_argument("--loss", choices=("energy", "mse"), default="energy")
+    ap.add_argument("--deflate", type=int, choices=(0, 1), default=0,
+                    help="solver form the evaluation compares against (0: plain MG-PCG)")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
     a = ap.parse_args(argv)
@@ -228,9 +233,10 @@ def main(argv=None):
     t_train = time.time() - t1
     del X, Q
     torch.cuda.empty_cache()
-    summary, rows = evaluate(net, list(range(a.eval_seed0, a.eval_seed0 + a.eval)), n)
+    summary, rows = evaluate(net, list(range(a.eval_seed0, a.eval_seed0 + a.eval)), n,
+                             deflate=a.deflate)
     report = dict(n=n, loss=a.loss, train_samples=a.train, epochs=a.epochs, lr=a.lr,
-                  lr_final=a.lr_final,
+                  lr_final=a.lr_final, deflate=a.deflate,
                   data_seconds=t_data, train_seconds=t_train,
                   steps=len(losses), loss_first=float(np.mean(losses[:50])),
                   loss_last=float(np.mean(losses[-50:])), train_solver_iters=float(np.mean(its)),

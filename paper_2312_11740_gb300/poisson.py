@@ -151,6 +151,16 @@ def mp_poisson_get_stats(handle):
     return {k: getattr(s, k) for k, _ in _lib.mp_stats._fields_}
 
 
+def mp_poisson_get_components(handle, n):
+    """(comp, m): each cell's gas-component id (-1 liquid; int32 device tensor of n cells)
+    and the component count used for deflation."""
+    comp = torch.empty(n, dtype=torch.int32, device="cuda")
+    m = ctypes.c_int(0)
+    _check(_lib_().mp_poisson_get_components(handle, ctypes.c_void_p(comp.data_ptr()),
+                                             ctypes.byref(m)), "mp_poisson_get_components")
+    return comp, m.value
+
+
 def mp_poisson_set_profiling(handle, enable):
     return _check(_lib_().mp_poisson_set_profiling(handle, int(bool(enable))),
                   "mp_poisson_set_profiling")
@@ -227,6 +237,10 @@ class Poisson:
 
     def stats(self):
         return mp_poisson_get_stats(self.handle)
+
+    def components(self):
+        comp, m = mp_poisson_get_components(self.handle, self.shape[0] * self.shape[1] * self.shape[2])
+        return comp.view(self.shape), m
 
     def set_profiling(self, enable=True):
         mp_poisson_set_profiling(self.handle, enable)

@@ -303,3 +303,82 @@ def test_full_size_256_properties(precision):
         assert np.max(np.abs(got - ref.ravel()[ix])) <= 1e-11 * max(np.abs(ref).max(), 1e-300)
     s.close()
 
+
+
+def _components_reference(phi, bc):
+    """Gas components (face neighbours, periodic axes wrapped) by scipy, with
+    ids in the order of each component's lowest cell index."""
+    from scipy import ndimage
+    gas = phi > 0
+    lab, nl = ndimage.label(gas)
+    parent = list(range(nl + 1))
+
+    def find(a):
+        while parent[a] != a:
+            a = parent[a]
+        return a
+
+    for axis, kind in enumerate(bc):
+        if kind != P:
+            continue
+        ax = 2 - axis
+        a, b = np.take(lab, 0, axis=ax), np.take(lab, -1, axis=ax)
+        m = (a > 0) & (b > 0)
+        for x, y in set(zip(a[m].tolist(), b[m].tolist())):
+            rx, ry = find(x), find(y)
+            if rx != ry:
+                parent[max(rx, ry)] = min(rx, ry)
+    flat = lab.ravel()
+    roots = np.array([find(v) if v > 0 else 0 for v in range(nl + 1)])[flat]
+    comp = np.full(flat.shape, -1)
+    first = {}
+    for idx in np.flatnonzero(roots):
+        first.setdefault(roots[idx], idx)
+    order = {r: k for k, r in enumerate(sorted(first, key=first.get))}
+    for idx in np.flatnonzero(roots):
+        comp[idx] = order[roots[idx]]
+    return comp.reshape(phi.shape), len(order)
+
+
+@pytest.mark.parametrize("bc", [(P, P, N), (N, N, N), (P, P, P)])
+def test_gas_components_match_scipy_labelling(bc):
+    """Union-find labelling of the gas cells on the GPU (deflation vectors):
+    the partition and the id order equal scipy's labelling with periodic
+    merging, including bubbles cut by periodic boundaries."""
+    shape = (40, 32, 48)
+    h = 1.0 / 48
+    bubbles = [((0.02, 0.5, 0.5), 0.12), ((0.5, 0.03, 0.3), 0.1), ((0.6, 0.6, 0.7), 0.08),
+               ((0.3, 0.3, 0.25), 0.05), ((0.8, 0.2, 0.15), 0.06)]
+    phi = synth.level_set(shape, h, bubbles, bc=bc)
+    prm = dict(h=h, bc=bc, rho_l=1.0, rho_g=1e-3, sigma=0.07)
+    s = make(phi, prm)
+    comp, m = s.components()
+    ref, mref = _components_reference(phi, bc)
+    assert m == mref
+    assert np.array_equal(comp.cpu().numpy(), ref)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_deflation_same_answer_fewer_iterations(precision):
+    """Deflating CG by the bubbles' indicator vectors changes the iteration,
+    not the answer: both solves meet the target, agree with each other, and
+    the deflated one takes fewer V-cycles on a multi-bubble problem."""
+    n = 64
+    h = 1.0 / n
+    shape = (n, n, n)
+    bubbles = synth.random_bubbles(10, 12, 0.04, 0.1, n)
+    phi = synth.level_set(shape, h, bubbles)
+    u = synth.velocity(11, shape, h)
+    prm = dict(h=h, bc=(P, P, N), rho_l=1.0, rho_g=1e-3, sigma=0.07)
+    s = make(phi, prm, precision=precision)
+    rhs = s.divergence(*[dev(c) for c in u])
+    p1, it1, _ = s.solve(rhs, tol=TOL)
+    st = s.stats()
+    assert st["components"] == 12 and st["relres"] <= TOL
+    s.set_opts(deflate=0)
+    p0, it0, _ = s.solve(rhs, tol=TOL)
+    assert s.stats()["components"] == 0 and s.stats()["relres"] <= TOL
+    assert it1 < it0, (it1, it0)
+    assert float(torch.linalg.norm(p1 - p0) / torch.linalg.norm(p0)) < 1e-7
+    s.close()
