@@ -26,6 +26,18 @@ constexpr int DEFL_REP = 16;            // replicas of each accumulator (atomic 
 constexpr int CCL_FIND_LIMIT = 8192;    // bound on a find walk (path halving keeps walks short)
 constexpr int CCL_UNITE_LIMIT = 512;    // bound on the retries of one union
 constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_TILE = 8 * SCAN_THREADS;  // counts scanned per pass (in shared memory)
+constexpr int BAND_THREADS = 256;
+constexpr int BAND_ROUNDS = 8;
+constexpr int BAND_CELLS = BAND_THREADS * BAND_ROUNDS;  // cells per compaction block
+
+// (i, j, k) of cell c in 32-bit arithmetic (deflation requires n < 2^31)
+__device__ __forceinline__ void cell_ijk(const Dims &d, size_t c, int &i, int &j, int &k) {
+  const unsigned u = (unsigned)c, t = u / (unsigned)d.nx;
+  i = (int)(u - t * (unsigned)d.nx);
+  j = (int)(t % (unsigned)d.ny);
+  k = (int)(t / (unsigned)d.ny);
+}
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
 
@@ -96,78 +108,35 @@ __global__ void k_ccl_merge(int *lab, Dims d, int per, int *err) {
   }
 }
 
-__global__ void k_ccl_flatten(int *lab, size_t n, int *err) {
+// lab[c] <- root of c for every gas cell; every root appends its index to
+// roots (first DEFL_MAX of them; *nroots counts all)
+__global__ void k_ccl_flatten(int *lab, size_t n, int *err, int *roots, int *nroots) {
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x)
-    if (lab[c] >= 0) lab[c] = ccl_find(lab, (int)c, err);
-}
-
-// ---------------------------------------------- ordered compaction (scan)
-// flag(c): kind 0 = component root (lab[c] == c); kind 1 = band cell (a face
-// neighbour, wrapped as in the stencils, has another component id)
-__device__ __forceinline__ bool defl_flag(int kind, const int *lab, const int *comp, const Dims &d,
-                                          size_t c) {
-  if (kind == 0) return lab[c] == (int)c;
-  const int i = (int)(c % d.nx), j = (int)((c / d.nx) % d.ny), k = (int)(c / ((size_t)d.nx * d.ny));
-  const int m = comp[c];
-  return comp[at(d, wlo(i, d.nx), j, k)] != m || comp[at(d, whi(i, d.nx), j, k)] != m ||
-         comp[at(d, i, wlo(j, d.ny), k)] != m || comp[at(d, i, whi(j, d.ny), k)] != m ||
-         comp[at(d, i, j, wlo(k, d.nz))] != m || comp[at(d, i, j, whi(k, d.nz))] != m;
-}
-
-// per-block count of flagged cells (256 cells per block, cell order)
-__global__ void k_flag_count(int kind, const int *__restrict__ lab, const int *__restrict__ comp,
-                             Dims d, size_t n, int *__restrict__ cnt) {
-  const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  const int f = c < n && defl_flag(kind, lab, comp, d, c);
-  const int s = __syncthreads_count(f);
-  if (threadIdx.x == 0) cnt[blockIdx.x] = s;
-}
-
-// exclusive scan of nb block counts in place (one block), total -> *total
-__global__ void k_scan_counts(int *cnt, int nb, int *total) {
-  __shared__ int part[SCAN_THREADS];
-  const int t = threadIdx.x;
-  const int per = (nb + SCAN_THREADS - 1) / SCAN_THREADS;
-  const int lo = t * per, hi = min(nb, lo + per);
-  int s = 0;
-  for (int e = lo; e < hi; ++e) s += cnt[e];
-  part[t] = s;
-  __syncthreads();
-  for (int o = 1; o < SCAN_THREADS; o <<= 1) {  // inclusive Hillis-Steele scan
-    const int v = t >= o ? part[t - o] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+       c += (size_t)gridDim.x * blockDim.x) {
+    if (lab[c] < 0) continue;
+    const int r = ccl_find(lab, (int)c, err);
+    lab[c] = r;
+    if (r == (int)c) {
+      const int q = atomicAdd(nroots, 1);
+      if (q < DEFL_MAX) roots[q] = r;
+    }
   }
-  int run = part[t] - s;  // exclusive start of this thread's chunk
-  for (int e = lo; e < hi; ++e) {
-    const int v = cnt[e];
-    cnt[e] = run;
-    run += v;
-  }
-  if (t == SCAN_THREADS - 1) *total = part[t];
 }
 
-// write the flagged cells' ordinals: kind 0 -> comp[root] = id; kind 1 -> list[id] = c
-__global__ void k_flag_assign(int kind, const int *__restrict__ lab, int *__restrict__ comp,
-                              Dims d, size_t n, const int *__restrict__ off,
-                              int *__restrict__ list) {
-  __shared__ int wcount[8];
-  const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  const int f = c < n && defl_flag(kind, lab, comp, d, c);
-  const unsigned bal = __ballot_sync(0xffffffffu, f);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) wcount[w] = __popc(bal);
+// comp[root] = rank of the root's cell index among all roots (ids follow the
+// roots' cell order whatever order the roots were appended in).  One block.
+__global__ void k_rank_roots(const int *__restrict__ roots, const int *__restrict__ nroots,
+                             int *__restrict__ comp) {
+  __shared__ int sr[DEFL_MAX];
+  const int m = *nroots;
+  if (m > DEFL_MAX) return;  // deflation is off for this geometry
+  for (int q = threadIdx.x; q < m; q += blockDim.x) sr[q] = roots[q];
   __syncthreads();
-  int base = off[blockIdx.x];
-  for (int q = 0; q < w; ++q) base += wcount[q];
-  const int id = base + __popc(bal & ((1u << lane) - 1u));
-  if (f) {
-    if (kind == 0)
-      comp[c] = id;
-    else
-      list[id] = (int)c;
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    const int v = sr[q];
+    int rank = 0;
+    for (int e = 0; e < m; ++e) rank += sr[e] < v;
+    comp[v] = rank;
   }
 }
 
@@ -177,6 +146,106 @@ __global__ void k_comp_from_roots(const int *__restrict__ lab, int *comp, size_t
        c += (size_t)gridDim.x * blockDim.x) {
     const int r = lab[c];
     comp[c] = r < 0 ? -1 : comp[r];
+  }
+}
+
+// ------------------------------------------ ordered band compaction (scan)
+// band cell: a face neighbour (wrapped as in the stencils) has another id
+__device__ __forceinline__ bool band_flag(const int *__restrict__ comp, const Dims &d, size_t c) {
+  int i, j, k;
+  cell_ijk(d, c, i, j, k);
+  const int m = comp[c];
+  return comp[at(d, wlo(i, d.nx), j, k)] != m || comp[at(d, whi(i, d.nx), j, k)] != m ||
+         comp[at(d, i, wlo(j, d.ny), k)] != m || comp[at(d, i, whi(j, d.ny), k)] != m ||
+         comp[at(d, i, j, wlo(k, d.nz))] != m || comp[at(d, i, j, whi(k, d.nz))] != m;
+}
+
+// number of band cells in each block of BAND_CELLS consecutive cells
+__global__ void __launch_bounds__(BAND_THREADS) k_band_count(const int *__restrict__ comp, Dims d,
+                                                             size_t n, int *__restrict__ cnt) {
+  const size_t base = (size_t)blockIdx.x * BAND_CELLS;
+  int total = 0;
+#pragma unroll
+  for (int r = 0; r < BAND_ROUNDS; ++r) {
+    const size_t c = base + (size_t)r * BAND_THREADS + threadIdx.x;
+    total += __syncthreads_count(c < n && band_flag(comp, d, c));
+  }
+  if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
+// exclusive scan of nb counts in place (one block of SCAN_THREADS), total -> *total.
+// Each pass stages SCAN_TILE counts in shared memory (coalesced), every thread
+// sums 8 consecutive ones, and a two-level warp-shuffle scan gives the offsets.
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_counts(int *cnt, int nb, int *total) {
+  __shared__ int tile[SCAN_TILE];
+  __shared__ int wsum[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int carry = 0;
+  for (int t0 = 0; t0 < nb; t0 += SCAN_TILE) {
+    for (int q = t; q < SCAN_TILE; q += SCAN_THREADS) tile[q] = t0 + q < nb ? cnt[t0 + q] : 0;
+    __syncthreads();
+    int s = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) s += tile[t * 8 + e];
+    int incl = s;  // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const int v = wsum[lane];
+      int wi = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += u;
+      }
+      wsum[lane] = wi;  // inclusive over warps
+    }
+    __syncthreads();
+    const int tile_total = wsum[31];
+    int run = carry + (w > 0 ? wsum[w - 1] : 0) + incl - s;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int v = tile[t * 8 + e];
+      tile[t * 8 + e] = run;
+      run += v;
+    }
+    __syncthreads();
+    for (int q = t; q < SCAN_TILE; q += SCAN_THREADS)
+      if (t0 + q < nb) cnt[t0 + q] = tile[q];
+    carry += tile_total;
+    __syncthreads();
+  }
+  if (t == 0) *total = carry;
+}
+
+// band[id] = c for the band cells, in cell order (off: the scanned counts)
+__global__ void __launch_bounds__(BAND_THREADS) k_band_assign(const int *__restrict__ comp, Dims d,
+                                                              size_t n, const int *__restrict__ off,
+                                                              int *__restrict__ band) {
+  __shared__ int wcount[BAND_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t base = (size_t)blockIdx.x * BAND_CELLS;
+  int run = off[blockIdx.x];
+  for (int r = 0; r < BAND_ROUNDS; ++r) {
+    const size_t c = base + (size_t)r * BAND_THREADS + threadIdx.x;
+    const bool f = c < n && band_flag(comp, d, c);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcount[w] = __popc(bal);
+    __syncthreads();
+    int wb = run, tot = 0;
+#pragma unroll
+    for (int q = 0; q < BAND_THREADS / 32; ++q) {
+      if (q < w) wb += wcount[q];
+      tot += wcount[q];
+    }
+    if (f) band[wb + __popc(bal & ((1u << lane) - 1u))] = (int)c;
+    run += tot;
+    __syncthreads();
   }
 }
 
@@ -224,7 +293,8 @@ template <typename F>
 __device__ __forceinline__ void band_row(const F *__restrict__ bx, const F *__restrict__ by,
                                          const F *__restrict__ bz, const int *__restrict__ comp,
                                          const Dims &d, size_t c, int ks[7], double ws[7]) {
-  const int i = (int)(c % d.nx), j = (int)((c / d.nx) % d.ny), k = (int)(c / ((size_t)d.nx * d.ny));
+  int i, j, k;
+  cell_ijk(d, c, i, j, k);
   const int m = comp[c];
   const size_t nb[6] = {at(d, wlo(i, d.nx), j, k), at(d, whi(i, d.nx), j, k),
                         at(d, i, wlo(j, d.ny), k), at(d, i, whi(j, d.ny), k),
@@ -374,6 +444,29 @@ __global__ void k_defl_coef(int m, unsigned long long *sa, const double *scale_a
   coef[j] = einv[j] * s;
 }
 
+// (A w)_c of band cell c for w = coef[comp] (0 in liquid)
+template <typename F>
+__device__ __forceinline__ double band_aw(const F *__restrict__ bx, const F *__restrict__ by,
+                                          const F *__restrict__ bz, const int *__restrict__ comp,
+                                          const Dims &d, size_t c, int i, int j, int k,
+                                          const double *__restrict__ coef) {
+  const int m = comp[c];
+  const double wc = m >= 0 ? coef[m] : 0.0;
+  const size_t nb[6] = {at(d, wlo(i, d.nx), j, k), at(d, whi(i, d.nx), j, k),
+                        at(d, i, wlo(j, d.ny), k), at(d, i, whi(j, d.ny), k),
+                        at(d, i, j, wlo(k, d.nz)), at(d, i, j, whi(k, d.nz))};
+  const double w[6] = {(double)bx[c], (double)bx[nb[1]], (double)by[c],
+                       (double)by[nb[3]], (double)bz[c], (double)bz[nb[5]]};
+  double aw = 0.0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int mk = comp[nb[f]];
+    const double wn = mk >= 0 ? coef[mk] : 0.0;
+    aw += w[f] * (wn - wc);
+  }
+  return aw;
+}
+
 // v_c -= (A w)_c on the band, w = coef[comp] (0 in liquid); optional per-block
 // partial sums of u_c (A w)_c (the change of u.v)
 template <typename T, typename F>
@@ -385,27 +478,34 @@ __global__ void k_defl_sub_aw(const int *__restrict__ band, int nband, const int
   double acc = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nband; e += gridDim.x * blockDim.x) {
     const size_t c = (size_t)band[e];
-    const int i = (int)(c % d.nx), j = (int)((c / d.nx) % d.ny), k = (int)(c / ((size_t)d.nx * d.ny));
-    const int m = comp[c];
-    const double wc = m >= 0 ? coef[m] : 0.0;
-    const size_t nb[6] = {at(d, wlo(i, d.nx), j, k), at(d, whi(i, d.nx), j, k),
-                          at(d, i, wlo(j, d.ny), k), at(d, i, whi(j, d.ny), k),
-                          at(d, i, j, wlo(k, d.nz)), at(d, i, j, whi(k, d.nz))};
-    const double w[6] = {(double)bx[c], (double)bx[nb[1]], (double)by[c],
-                         (double)by[nb[3]], (double)bz[c], (double)bz[nb[5]]};
-    double aw = 0.0;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      const int mk = comp[nb[f]];
-      const double wn = mk >= 0 ? coef[mk] : 0.0;
-      aw += w[f] * (wn - wc);
-    }
+    int i, j, k;
+    cell_ijk(d, c, i, j, k);
+    const double aw = band_aw(bx, by, bz, comp, d, c, i, j, k, coef);
     v[c] = (T)((double)v[c] - aw);
     if (u) acc += (double)u[c] * aw;
   }
   if (partial) {
     const double t = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
+// The projected true residual on the band, formed in FP64 and rounded once:
+// r32_c = fl32((bt - At p)_c - (At Z coef)_c).  Off the band (At Z coef)_c = 0
+// and r32 already holds fl32(bt - At p).  Near a component both terms are
+// large and nearly cancel, so they must not be rounded separately.
+__global__ void k_defl_resid_band(const int *__restrict__ band, int nband,
+                                  const int *__restrict__ comp, const double *__restrict__ bx,
+                                  const double *__restrict__ by, const double *__restrict__ bz,
+                                  const double *__restrict__ diag, Dims d,
+                                  const double *__restrict__ coef, const double *__restrict__ p,
+                                  const double *__restrict__ b, float *__restrict__ r32) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nband; e += gridDim.x * blockDim.x) {
+    const size_t c = (size_t)band[e];
+    int i, j, k;
+    cell_ijk(d, c, i, j, k);
+    const double res = resid_at<double>(p, b, bx, by, bz, diag, d, i, j, k);
+    r32[c] = (float)(res - band_aw(bx, by, bz, comp, d, c, i, j, k, coef));
   }
 }
 
@@ -416,17 +516,6 @@ __global__ void k_defl_add_z(double *__restrict__ x, const int *__restrict__ com
        c += (size_t)gridDim.x * blockDim.x) {
     const int m = comp[c];
     if (m >= 0) x[c] += coef[m];
-  }
-}
-
-// z_c -= coef[comp_c] on every cell of a component (z <- P^T z = z - Z E^-1 (A Z)^T z)
-template <typename T>
-__global__ void k_defl_sub_z(T *__restrict__ z, const int *__restrict__ comp, size_t n,
-                             const double *__restrict__ coef) {
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    const int m = comp[c];
-    if (m >= 0) z[c] = (T)((double)z[c] - coef[m]);
   }
 }
 

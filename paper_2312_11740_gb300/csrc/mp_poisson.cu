@@ -94,6 +94,7 @@ struct mp_poisson {
   mp_stats stats{};
   // deflation by the gas components (mp_deflate.cuh)
   int *lab = nullptr, *comp = nullptr, *band = nullptr, *cnt = nullptr, *dint = nullptr;
+  int *roots = nullptr;
   int defl_m = 0, defl_nband = 0;
   double beta_max = 1.0, ztb_scale = 1.0;
   double *einv = nullptr, *coef = nullptr, *dscale = nullptr;
@@ -406,27 +407,27 @@ size_t defl_acc_bytes(int m) { return (size_t)m * DEFL_REP * 2 * sizeof(unsigned
 mp_status deflation_setup(mp_poisson *hd) {
   Level &l0 = hd->L[0];
   const size_t n = hd->n;
-  const int nblk = (int)((n + 255) / 256);
   hd->defl_m = 0;
   hd->defl_nband = 0;
+  if (n >= ((size_t)1 << 31)) return MP_OK;  // 32-bit cell indices
+  const int nblk = (int)((n + BAND_CELLS - 1) / BAND_CELLS);
+  // dint: [0] components (roots), [1] band cells, [2] labelling bound exceeded
   CK(cudaMemsetAsync(hd->dint, 0, 4 * sizeof(int), hd->st));
   LAUNCH(hd, K_DEFL, 0, n * 12.0, k_ccl_init, VEC_BLOCKS, VEC_THREADS, hd->phi, hd->lab, n);
   LAUNCH(hd, K_DEFL, 0, n * 16.0, k_ccl_merge, cell_grid(l0.d), kBlock, hd->lab, l0.d, hd->per,
          hd->dint + 2);
-  LAUNCH(hd, K_DEFL, 0, n * 8.0, k_ccl_flatten, VEC_BLOCKS, VEC_THREADS, hd->lab, n, hd->dint + 2);
-  LAUNCH(hd, K_DEFL, 0, n * 4.0, k_flag_count, nblk, 256, 0, hd->lab, hd->comp, l0.d, n, hd->cnt);
-  LAUNCH(hd, K_DEFL, 0, nblk * 8.0, k_scan_counts, 1, SCAN_THREADS, hd->cnt, nblk, hd->dint);
-  LAUNCH(hd, K_DEFL, 0, n * 8.0, k_flag_assign, nblk, 256, 0, hd->lab, hd->comp, l0.d, n, hd->cnt,
-         (int *)nullptr);
+  LAUNCH(hd, K_DEFL, 0, n * 8.0, k_ccl_flatten, VEC_BLOCKS, VEC_THREADS, hd->lab, n, hd->dint + 2,
+         hd->roots, hd->dint);
+  LAUNCH(hd, K_DEFL, 0, DEFL_MAX * 8.0, k_rank_roots, 1, 1024, hd->roots, hd->dint, hd->comp);
   LAUNCH(hd, K_DEFL, 0, n * 12.0, k_comp_from_roots, VEC_BLOCKS, VEC_THREADS, hd->lab, hd->comp,
          n);
   CK(cudaMemcpyAsync(hd->hint, hd->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost, hd->st));
   CK(cudaStreamSynchronize(hd->st));
   const int m = hd->hint[0];
   if (hd->hint[2] != 0 || m <= 0 || m > DEFL_MAX) return MP_OK;
-  LAUNCH(hd, K_DEFL, 0, n * 28.0, k_flag_count, nblk, 256, 1, hd->lab, hd->comp, l0.d, n, hd->cnt);
+  LAUNCH(hd, K_DEFL, 0, n * 4.0, k_band_count, nblk, BAND_THREADS, hd->comp, l0.d, n, hd->cnt);
   LAUNCH(hd, K_DEFL, 0, nblk * 8.0, k_scan_counts, 1, SCAN_THREADS, hd->cnt, nblk, hd->dint + 1);
-  LAUNCH(hd, K_DEFL, 0, n * 28.0, k_flag_assign, nblk, 256, 1, hd->lab, hd->comp, l0.d, n, hd->cnt,
+  LAUNCH(hd, K_DEFL, 0, n * 4.0, k_band_assign, nblk, BAND_THREADS, hd->comp, l0.d, n, hd->cnt,
          hd->band);
   CK(cudaMemcpyAsync(hd->hint, hd->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost, hd->st));
   CK(cudaStreamSynchronize(hd->st));
@@ -627,12 +628,13 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
   // components both bt - At p and A Z c are large, and rounding before the
   // subtraction would leave their FP32 rounding error in the projected residual
   auto project_true = [&](double &rnorm) -> mp_status {
-    LAUNCH(hd, K_RESID64, 0, n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b, hd->r,
-           l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
     CKS((defl_coef<double, double>(hd, p, l0.bx, l0.by, l0.bz, true)));
-    CKS((defl_sub<double, double>(hd, hd->r, (const double *)nullptr, l0.bx, l0.by, l0.bz)));
-    LAUNCH(hd, K_RESIDMIX, 0, n * 12.0, k_to_f32_norm, VEC_BLOCKS, VEC_THREADS, hd->r, r, n,
-           hd->partial);
+    LAUNCH(hd, K_RESIDMIX, 0, n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b, r,
+           l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+    const int nb = hd->defl_nband;
+    LAUNCH(hd, K_DEFL, 0, nb * 120.0, k_defl_resid_band, VEC_BLOCKS, VEC_THREADS, hd->band, nb,
+           hd->comp, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->coef, p, hd->b, r);
+    LAUNCH(hd, K_DOT32, 0, 4.0 * n, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, r, n, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
     CKS(read_scalars(hd));
     rnorm = std::sqrt(hd->scal_h[S_RR]);
@@ -667,14 +669,6 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
     if (since == 0 && rn <= tol_abs) break;  // converged on a true residual
     if (it >= maxit) { st = MP_ERR_NOT_CONVERGED; break; }
     CKS(run_vcycle<float>(hd, r, z));
-    if (defl) {
-      // z <- P^T z (balancing form): keeps every direction A-orthogonal to the
-      // components; without it the directions drift in span(Z), which P A does
-      // not see, until the drift swamps the FP32 correction
-      CKS((defl_coef<float, float>(hd, z, l0.bx32, l0.by32, l0.bz32, false)));
-      LAUNCH(hd, K_DEFL, 0, n * 8.0, k_defl_sub_z<float>, VEC_BLOCKS, VEC_THREADS, z, hd->comp, n,
-             hd->coef);
-    }
     LAUNCH(hd, K_DOT32, 0, 2.0 * nsz, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, z, n, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
     LAUNCH(hd, K_XPBY32, 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<float>, VEC_BLOCKS, VEC_THREADS,
@@ -1051,12 +1045,13 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
   }
   CK(cudaMemsetAsync(hd->scal, 0, S_COUNT * sizeof(double), hd->st));
   // deflation workspace
-  const size_t nblk = (n + 255) / 256;
+  const size_t nblk = (n + BAND_CELLS - 1) / BAND_CELLS;
   CKS(dalloc(hd, &hd->lab, n));
   CKS(dalloc(hd, &hd->comp, n));
   CKS(dalloc(hd, &hd->band, n));
   CKS(dalloc(hd, &hd->cnt, nblk));
   CKS(dalloc(hd, &hd->dint, 4));
+  CKS(dalloc(hd, &hd->roots, (size_t)DEFL_MAX));
   CKS(dalloc(hd, &hd->einv, (size_t)DEFL_MAX));
   CKS(dalloc(hd, &hd->coef, (size_t)DEFL_MAX));
   CKS(dalloc(hd, &hd->dscale, 4));
