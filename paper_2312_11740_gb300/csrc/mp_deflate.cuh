@@ -434,7 +434,8 @@ __global__ void k_defl_zt(const int *__restrict__ comp, const T *__restrict__ v,
 __global__ void k_defl_coef(int m, unsigned long long *sa, const double *scale_a,
                             double fixed_scale_a, int clear_a, unsigned long long *sb,
                             const double *scale_b, const double *__restrict__ einv,
-                            double *__restrict__ coef, unsigned long long *mx) {
+                            double *__restrict__ coef, float *__restrict__ coef32,
+                            unsigned long long *mx) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j == 0) *mx = 0ull;
   if (j >= m) return;
@@ -442,6 +443,7 @@ __global__ void k_defl_coef(int m, unsigned long long *sa, const double *scale_a
   if (sa) s = fx_value(sa, j, scale_a ? *scale_a : fixed_scale_a, clear_a != 0);
   if (sb) s -= fx_value(sb, j, *scale_b, true);
   coef[j] = einv[j] * s;
+  coef32[j] = (float)coef[j];
 }
 
 // (A w)_c of band cell c for w = coef[comp] (0 in liquid)
@@ -507,6 +509,67 @@ __global__ void k_defl_resid_band(const int *__restrict__ band, int nband,
     const double res = resid_at<double>(p, b, bx, by, bz, diag, d, i, j, k);
     r32[c] = (float)(res - band_aw(bx, by, bz, comp, d, c, i, j, k, coef));
   }
+}
+
+template <int W>
+struct IVec16;
+template <>
+struct IVec16<4> {
+  using V = int4;
+  __device__ static int at(const V &v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+  }
+};
+template <>
+struct IVec16<2> {
+  using V = int2;
+  __device__ static int at(const V &v, int i) { return i == 0 ? v.x : v.y; }
+};
+
+// z <- P^T z = z - Z coef (coef = E^-1 (A Z)^T z) on every cell of a
+// component, fused with the partial sums of r . (P^T z).  16-byte accesses
+// when z and r are 16-byte aligned (internal buffers always are).
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS, 4)
+k_dot_zdefl(const T *__restrict__ r, T *__restrict__ z, const int *__restrict__ comp,
+            const T *__restrict__ coef, size_t n, double *__restrict__ partial) {
+  using VT = Vec16<T>;
+  using V = typename VT::V;
+  constexpr int W = VT::W;
+  T acc = 0;
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t done = 0;
+  if (aligned16(r, z)) {
+    const size_t nv = n / W;
+    const V *rv = reinterpret_cast<const V *>(r);
+    V *zv = reinterpret_cast<V *>(z);
+    const typename IVec16<W>::V *cv = reinterpret_cast<const typename IVec16<W>::V *>(comp);
+    for (size_t e = tid; e < nv; e += stride) {
+      const V x = rv[e];
+      V y = zv[e];
+      const typename IVec16<W>::V ce = cv[e];
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        const int m = IVec16<W>::at(ce, q);
+        if (m >= 0) {
+          VT::set(y, q, VT::at(y, q) - coef[m]);
+          any = true;
+        }
+        acc = fma(VT::at(x, q), VT::at(y, q), acc);
+      }
+      if (any) zv[e] = y;
+    }
+    done = nv * W;
+  }
+  for (size_t e = done + tid; e < n; e += stride) {
+    const int m = comp[e];
+    if (m >= 0) z[e] -= coef[m];
+    acc = fma(r[e], z[e], acc);
+  }
+  double t = block_sum((double)acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
 // x_c += coef[comp_c] on every cell of a component (the deflation correction)

@@ -588,7 +588,7 @@ __global__ void k_prolong_vec(T *__restrict__ x, const T *__restrict__ ec, Dims 
 // --------------------------------------------------------- Krylov kernels
 // Scalars kept on the device between kernels (no host round trip).
 enum { S_RZ = 0, S_RZOLD, S_DQ, S_ALPHA, S_BETA, S_RR, S_BB, S_MEAN, S_TMP, S_COUNT };
-enum { OP_STORE = 0, OP_ALPHA, OP_BETA, OP_MEAN, OP_ALPHA_DEFL };
+enum { OP_STORE = 0, OP_ALPHA, OP_BETA, OP_MEAN };
 
 // Stencil kernels with a reduction walk a column of `zper` planes per
 // thread (grid z = ceil(nz / zper)), so the partial-sum count stays ~2k.
@@ -856,10 +856,6 @@ __global__ void k_reduce(const double *__restrict__ partial, int np, double *__r
         scal[S_BETA] = s / scal[S_RZOLD];
         break;
       case OP_MEAN: scal[S_MEAN] = s / count; break;
-      case OP_ALPHA_DEFL:  // d.(P A d) = d.(A d) (in S_DQ) - s
-        scal[S_DQ] -= s;
-        scal[S_ALPHA] = scal[S_RZ] / scal[S_DQ];
-        break;
     }
   }
 }

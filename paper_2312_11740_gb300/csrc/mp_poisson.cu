@@ -98,6 +98,7 @@ struct mp_poisson {
   int defl_m = 0, defl_nband = 0;
   double beta_max = 1.0, ztb_scale = 1.0;
   double *einv = nullptr, *coef = nullptr, *dscale = nullptr;
+  float *coef32 = nullptr;
   unsigned long long *acc_a = nullptr, *acc_b = nullptr, *acc_ztb = nullptr, *dmax = nullptr;
   int *hint = nullptr;  // pinned host copy of dint
   mp_net_handle net = nullptr;  // learned initial guess (initial_guess = 2)
@@ -482,10 +483,11 @@ mp_status defl_coef(mp_poisson *hd, const T *v, const F *bx, const F *by, const 
   if (with_ztb)
     LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, hd->acc_ztb,
            (const double *)nullptr, hd->ztb_scale, 0, acc, hd->dscale, hd->einv, hd->coef,
-           hd->dmax);
+           hd->coef32, hd->dmax);
   else
     LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, acc, hd->dscale, 0.0, 1,
-           (unsigned long long *)nullptr, (const double *)nullptr, hd->einv, hd->coef, hd->dmax);
+           (unsigned long long *)nullptr, (const double *)nullptr, hd->einv, hd->coef, hd->coef32,
+           hd->dmax);
   return launch_ok();
 }
 
@@ -530,7 +532,7 @@ mp_status defl_guess_residuals(mp_poisson *hd, const double *p, double *rguess, 
   const int m = hd->defl_m;
   LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, hd->acc_ztb,
          (const double *)nullptr, hd->ztb_scale, 0, (unsigned long long *)nullptr,
-         (const double *)nullptr, hd->einv, hd->coef, hd->dmax);
+         (const double *)nullptr, hd->einv, hd->coef, hd->coef32, hd->dmax);
   CK(cudaMemcpyAsync(hd->z, hd->b, n * sizeof(double), cudaMemcpyDeviceToDevice, hd->st));
   CKS((defl_sub<double, double>(hd, hd->z, (const double *)nullptr, l0.bx, l0.by, l0.bz)));
   LAUNCH(hd, K_DOT64, 0, n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, hd->z, hd->z, n,
@@ -539,6 +541,22 @@ mp_status defl_guess_residuals(mp_poisson *hd, const double *p, double *rguess, 
   CKS(read_scalars(hd));
   *rzero = std::sqrt(hd->scal_h[S_TMP]);
   return MP_OK;
+}
+
+// z <- P^T z = z - Z E^-1 (A Z)^T z after the V-cycle, fused with the partial
+// sums of r . z (the A-DEF2 form of deflated PCG: every search direction is
+// A-orthogonal to the components, so the iteration needs no projection of A d)
+template <typename T, typename F>
+mp_status defl_rz(mp_poisson *hd, const T *r, T *z, const F *bx, const F *by, const F *bz) {
+  CKS((defl_coef<T, F>(hd, z, bx, by, bz, false)));
+  const T *coef;
+  if constexpr (sizeof(T) == 8)
+    coef = hd->coef;
+  else
+    coef = hd->coef32;
+  LAUNCH(hd, K_DEFL, 0, hd->n * (3.0 * sizeof(T) + 4.0), k_dot_zdefl<T>, VEC_BLOCKS, VEC_THREADS,
+         r, z, hd->comp, coef, hd->n, hd->partial);
+  return launch_ok();
 }
 
 // Preconditioned CG on At x = (rhs), starting from x with residual r already
@@ -551,7 +569,9 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
   T *bx = LV<T>::bx(l0), *by = LV<T>::by(l0), *bz = LV<T>::bz(l0), *diag = LV<T>::diag(l0);
   size_t n = hd->n;
   const double nsz = (double)n * sizeof(T);
-  // deflated CG (FP64): r <- P r, iterate on P A, finish with x += Z E^-1 Z^T (b - A x)
+  // deflated CG (FP64, A-DEF2 form): r <- P r = b - A (x + Z c) (c = E^-1 Z^T
+  // (b - A x), the correction itself deferred), z <- P^T M r every iteration,
+  // finish with x += Z E^-1 Z^T (b - A x), which includes c
   const bool defl = sizeof(T) == 8 && defl_active(hd);
   if (defl) {
     CKS(defl_ztb(hd));
@@ -573,22 +593,18 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
       break;
     }
     CKS(run_vcycle<T>(hd, r, z));
-    LAUNCH(hd, kid<T>(K_DOT64, K_DOT32), 0, 2.0 * nsz, k_dot<T>, VEC_BLOCKS, VEC_THREADS, r, z, n,
-           hd->partial);
+    if (defl)
+      CKS((defl_rz<T, T>(hd, r, z, bx, by, bz)));
+    else
+      LAUNCH(hd, kid<T>(K_DOT64, K_DOT32), 0, 2.0 * nsz, k_dot<T>, VEC_BLOCKS, VEC_THREADS, r, z,
+             n, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
     LAUNCH(hd, kid<T>(K_XPBY64, K_XPBY32), 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<T>, VEC_BLOCKS,
            VEC_THREADS, dv, z, n, hd->scal, it == 0);
     LAUNCH(hd, kid<T>(K_APPLY64, K_APPLY32), 0, (sizeof(T) == 8 ? 6.0 : 5.0) * nsz,
            k_apply_dot<T>, zgrid(l0.d), kBlock, dv, q, bx, by, bz, diag, l0.d, zper_of(l0.d),
            hd->partial);
-    if (defl) {  // q <- P q = q - A Z E^-1 (A Z)^T d; alpha = rz / (d . P q)
-      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_DQ));
-      CKS((defl_coef<T, T>(hd, dv, bx, by, bz, false)));
-      CKS((defl_sub<T, T>(hd, q, dv, bx, by, bz)));
-      CKS(reduce(hd, VEC_BLOCKS, OP_ALPHA_DEFL, 0));
-    } else {
-      CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
-    }
+    CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
     LAUNCH(hd, kid<T>(K_AXPY64, K_AXPY32), 0, 6.0 * nsz, k_axpy2<T>, VEC_BLOCKS, VEC_THREADS, x,
            r, dv, q, n, hd->scal, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
@@ -620,9 +636,9 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
   float *e = hd->e32, *r = hd->r32, *z = hd->z32, *dv = hd->d32, *q = hd->q32;
   int it = 0, nrep = 0, since = 0;
   mp_status st = MP_OK;
-  // deflated: every true residual is projected, r32 = fl32(P (bt - At p)), with
-  // Z^T (bt - At p) = Z^T bt - (At Z)^T p from FP64 p; the iteration uses P At
-  // in FP32; the exit adds Z E^-1 Z^T (bt - At p) to p
+  // deflated (A-DEF2 form): every true residual is projected, r32 = fl32(P (bt -
+  // At p)), with Z^T (bt - At p) = Z^T bt - (At Z)^T p from FP64 p; after every
+  // V-cycle z <- P^T z in FP32; the exit adds Z E^-1 Z^T (bt - At p) to p
   const bool defl = defl_active(hd);
   // the true residual is projected in FP64 and rounded afterwards: near the
   // components both bt - At p and A Z c are large, and rounding before the
@@ -669,20 +685,17 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
     if (since == 0 && rn <= tol_abs) break;  // converged on a true residual
     if (it >= maxit) { st = MP_ERR_NOT_CONVERGED; break; }
     CKS(run_vcycle<float>(hd, r, z));
-    LAUNCH(hd, K_DOT32, 0, 2.0 * nsz, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, z, n, hd->partial);
+    if (defl)
+      CKS((defl_rz<float, float>(hd, r, z, l0.bx32, l0.by32, l0.bz32)));
+    else
+      LAUNCH(hd, K_DOT32, 0, 2.0 * nsz, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, z, n,
+             hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
     LAUNCH(hd, K_XPBY32, 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<float>, VEC_BLOCKS, VEC_THREADS,
            dv, z, n, hd->scal, it == 0);
     LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot<float>, zgrid(l0.d), kBlock, dv, q, l0.bx32,
            l0.by32, l0.bz32, (float *)nullptr, l0.d, zper_of(l0.d), hd->partial);
-    if (defl) {  // q <- P q; alpha = rz / (d . P q)
-      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_DQ));
-      CKS((defl_coef<float, float>(hd, dv, l0.bx32, l0.by32, l0.bz32, false)));
-      CKS((defl_sub<float, float>(hd, q, dv, l0.bx32, l0.by32, l0.bz32)));
-      CKS(reduce(hd, VEC_BLOCKS, OP_ALPHA_DEFL, 0));
-    } else {
-      CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
-    }
+    CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
     LAUNCH(hd, K_AXPY32, 0, 6.0 * nsz, k_axpy2<float>, VEC_BLOCKS, VEC_THREADS, e, r, dv, q, n,
            hd->scal, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
@@ -1054,6 +1067,7 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
   CKS(dalloc(hd, &hd->roots, (size_t)DEFL_MAX));
   CKS(dalloc(hd, &hd->einv, (size_t)DEFL_MAX));
   CKS(dalloc(hd, &hd->coef, (size_t)DEFL_MAX));
+  CKS(dalloc(hd, &hd->coef32, (size_t)DEFL_MAX));
   CKS(dalloc(hd, &hd->dscale, 4));
   CKS(dalloc(hd, &hd->acc_a, (size_t)DEFL_MAX * DEFL_REP * 2));
   CKS(dalloc(hd, &hd->acc_b, (size_t)DEFL_MAX * DEFL_REP * 2));
@@ -1088,6 +1102,9 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
                           (int)std::max<size_t>(hd->tail64_bytes, 1)));
   CK(cudaFuncSetAttribute(k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)std::max<size_t>(hd->tail32_bytes, 1)));
+  // the zero fills of dalloc run on the legacy default stream, which a
+  // non-blocking caller stream does not wait for: finish them here
+  CK(cudaDeviceSynchronize());
   return MP_OK;
 }
 

@@ -382,3 +382,35 @@ def test_deflation_same_answer_fewer_iterations(precision):
     assert it1 < it0, (it1, it0)
     assert float(torch.linalg.norm(p1 - p0) / torch.linalg.norm(p0)) < 1e-7
     s.close()
+
+
+def test_fresh_handles_on_nonblocking_streams():
+    """A handle created and used at once on a non-blocking caller stream gives
+    bitwise the answer of one on the legacy default stream: the zero fills of
+    the new buffers are complete before the first geometry setup (they once
+    were not, and an early solve could read half-cleared work arrays)."""
+    n = 128
+    h = 1.0 / n
+    shape = (n, n, n)
+    bubbles = synth.random_bubbles(21, 16, 0.03, 0.08, n)
+    phi = dev(synth.level_set(shape, h, bubbles))
+    u = [dev(c) for c in synth.velocity(22, shape, h)]
+    prm = dict(h=h, bc=(P, P, N), rho_l=1.0, rho_g=1e-3, sigma=0.07)
+    ref = Poisson(phi, h, prm["bc"], prm["rho_l"], prm["rho_g"], prm["sigma"], precision=0)
+    rhs = ref.divergence(*u)
+    p_ref, it_ref, _ = ref.solve(rhs, tol=TOL)
+    ref.close()
+    for precision in (0, 1, 0):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            s = Poisson(phi, h, prm["bc"], prm["rho_l"], prm["rho_g"], prm["sigma"],
+                        precision=precision, stream=st)
+            p, it, _ = s.solve(rhs, tol=TOL)
+            stats = s.stats()
+        st.synchronize()
+        assert stats["relres"] <= TOL and stats["components"] == 16
+        if precision == 0:
+            assert it == it_ref and torch.equal(p, p_ref)
+        else:
+            assert float(torch.linalg.norm(p - p_ref) / torch.linalg.norm(p_ref)) < 1e-7
+        s.close()
