@@ -696,49 +696,69 @@ __global__ void k_restrict_fields(const double *__restrict__ phi, const double *
   }
 }
 
-// p_fine = s * (q - mean q) interpolated trilinearly from the network grid to
-// the grid twice as fine (cell-centred weights 3/4, 1/4 per axis; periodic
-// axes wrap, wall axes clamp)
-__global__ void k_prolong_tri(const float *__restrict__ q, const double *__restrict__ sum_q,
-                              int nxc, int nyc, int nzc, int per, double s,
-                              double *__restrict__ p) {
-  const size_t nc = (size_t)nxc * nyc * nzc;
-  const double m = *sum_q / (double)nc;
+// qc = q - mean(q) on the network grid: centred in FP64, rounded once to FP32
+__global__ void k_center_q(const float *__restrict__ q, const double *__restrict__ sum_q,
+                           size_t nc, float *__restrict__ qc) {
+  __shared__ double mean;
+  if (threadIdx.x == 0) mean = *sum_q / (double)nc;
+  __syncthreads();
+  const double m = mean;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nc;
+       v += (size_t)gridDim.x * blockDim.x)
+    qc[v] = (float)((double)q[v] - m);
+}
+
+// coarse neighbours l0, l1 of fine cell c along one axis and the weight w1 of
+// l1 (cell-centred: 3/4 for the nearer coarse cell, 1/4 for the farther one;
+// periodic axes wrap, wall axes clamp)
+__device__ __forceinline__ void tri_axis(int c, int nc, bool per, int &l0, int &l1, float &w1) {
+  const int lo = (c - 1) >> 1;  // coarse cell below the fine centre
+  w1 = (c & 1) ? 0.25f : 0.75f;
+  l0 = lo;
+  l1 = lo + 1;
+  if (per) {
+    l0 = l0 < 0 ? l0 + nc : l0;
+    l1 = l1 >= nc ? l1 - nc : l1;
+  } else {
+    l0 = l0 < 0 ? 0 : l0;
+    l1 = l1 > nc - 1 ? nc - 1 : l1;
+  }
+}
+
+// p_fine = s * qc interpolated trilinearly from the network grid to the grid
+// twice as fine.  The weights and their products are exact in FP32 and qc is
+// already centred, so the separable FP32 interpolation loses only a few FP32
+// ulps of the centred field; one FP64 multiply per fine cell.
+__global__ void k_prolong_tri(const float *__restrict__ qc, int nxc, int nyc, int nzc, int per,
+                              double s, double *__restrict__ p) {
   const int nx = 2 * nxc, ny = 2 * nyc, nz = 2 * nzc;
-  const size_t n = (size_t)nx * ny * nz;
-  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n;
-       v += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((size_t)nx * ny));
-    int I[2], J[2], K[2];
-    float wi[2], wj[2], wk[2];
-    const int c[3] = {i, j, k}, nn[3] = {nxc, nyc, nzc};
-    int *idx[3] = {I, J, K};
-    float *w[3] = {wi, wj, wk};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int lo = (c[a] - 1) >> 1;  // coarse cell below the fine centre
-      const float w1 = (c[a] & 1) ? 0.25f : 0.75f;
-      int l0 = lo, l1 = lo + 1;
-      if (per & (1 << a)) {
-        l0 = (l0 + nn[a]) % nn[a];
-        l1 = l1 % nn[a];
-      } else {
-        l0 = l0 < 0 ? 0 : l0;
-        l1 = l1 > nn[a] - 1 ? nn[a] - 1 : l1;
-      }
-      idx[a][0] = l0;
-      idx[a][1] = l1;
-      w[a][0] = 1.f - w1;
-      w[a][1] = w1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  int i0, i1;
+  float wi1;
+  tri_axis(i, nxc, per & 1, i0, i1, wi1);
+  const float wi0 = 1.f - wi1;
+  for (int k = blockIdx.z; k < nz; k += gridDim.z) {
+    int k0, k1;
+    float wk1;
+    tri_axis(k, nzc, per & 4, k0, k1, wk1);
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+      int j0, j1;
+      float wj1;
+      tri_axis(j, nyc, per & 2, j0, j1, wj1);
+      const float *r00 = qc + ((size_t)k0 * nyc + j0) * nxc;
+      const float *r01 = qc + ((size_t)k0 * nyc + j1) * nxc;
+      const float *r10 = qc + ((size_t)k1 * nyc + j0) * nxc;
+      const float *r11 = qc + ((size_t)k1 * nyc + j1) * nxc;
+      const float x00 = wi0 * r00[i0] + wi1 * r00[i1];
+      const float x01 = wi0 * r01[i0] + wi1 * r01[i1];
+      const float x10 = wi0 * r10[i0] + wi1 * r10[i1];
+      const float x11 = wi0 * r11[i0] + wi1 * r11[i1];
+      const float y0 = (1.f - wj1) * x00 + wj1 * x01;
+      const float y1 = (1.f - wj1) * x10 + wj1 * x11;
+      const float v = (1.f - wk1) * y0 + wk1 * y1;
+      p[((size_t)k * ny + j) * nx + i] = s * (double)v;
     }
-    double acc = 0.0;
-#pragma unroll
-    for (int q8 = 0; q8 < 8; ++q8) {
-      const int a = q8 & 1, bq = (q8 >> 1) & 1, cq = q8 >> 2;
-      const double wt = (double)wi[a] * wj[bq] * wk[cq];
-      acc += wt * ((double)q[((size_t)K[cq] * nyc + J[bq]) * nxc + I[a]] - m);
-    }
-    p[v] = s * acc;
   }
 }
 
@@ -1042,6 +1062,7 @@ struct mp_net {
   bf16 *gz = nullptr;             // ReLU-masked gradient (largest size)
   bf16 *gx = nullptr;             // input gradient of a layer (largest size)
   float *q = nullptr, *gq = nullptr;
+  float *qc = nullptr;  // centred output (prolongation to the solver grid)
   float *wpart = nullptr;         // weight-gradient split-K partials
   size_t wpart_n = 0;
   float *cpart = nullptr;         // per-channel partial sums
@@ -1483,6 +1504,7 @@ mp_status mp_net_create(mp_net_handle *out, int nx, int ny, int nz, void *stream
   if (s == MP_OK) s = nalloc(net, &net->gz, maxact);
   if (s == MP_OK) s = nalloc(net, &net->gx, maxact);
   if (s == MP_OK) s = nalloc(net, &net->q, net->nv[0]);
+  if (s == MP_OK) s = nalloc(net, &net->qc, net->nv[0]);
   if (s == MP_OK) s = nalloc(net, &net->gq, net->nv[0]);
   if (s == MP_OK) s = nalloc(net, &net->wpart, wpart);
   if (s == MP_OK) s = nalloc(net, &net->cpart, (net->nv[0] / 1024 + 64) * 130);
@@ -1623,10 +1645,13 @@ mp_status mp_net_pressure_at(mp_net_handle net, int factor, const mp_bc bc[3], d
   const size_t n = net->nv[0];
   k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, n, 0, net->dpart);
   k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
-  k_prolong_tri<<<grid_for(8 * n), 256, 0, net->st>>>(net->q, net->dscal, net->nx[0], net->ny[0],
-                                                      net->nz[0], per, s, p_dev);
+  k_center_q<<<grid_for(n), 256, 0, net->st>>>(net->q, net->dscal, n, net->qc);
+  const dim3 pg((2 * net->nx[0] + 255) / 256, std::min(2 * net->ny[0], 65535),
+                std::min(2 * net->nz[0], 65535));
+  k_prolong_tri<<<pg, 256, 0, net->st>>>(net->qc, net->nx[0], net->ny[0], net->nz[0], per, s,
+                                         p_dev);
   NCK(cudaGetLastError());
-  net->launches += 3;
+  net->launches += 4;
   NCK(cudaStreamSynchronize(net->st));
   return MP_OK;
 }
