@@ -7,6 +7,7 @@
 //   At e = bt,  (At e)_c = sum_f beta_f e_nb - diag_c e_c,  bt = h^2 b,
 // so no kernel multiplies by 1/h^2; diag_c = sum of the six face betas.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -181,12 +182,15 @@ __global__ void k_jump(const double *__restrict__ phi, const double *__restrict_
   Jt[c] = s;
 }
 
-// diag = sum of the six face betas, idiag = 1/diag; f64 and f32 copies
+// diag = sum of the six face betas, idiag = 1/diag; f64 and f32 copies, and
+// the FP16 faces of the FP32 V-cycle, stored as beta * fs
 __global__ void k_diag(const double *__restrict__ bx, const double *__restrict__ by,
                        const double *__restrict__ bz, double *__restrict__ diag,
                        double *__restrict__ idiag, float *__restrict__ bx32,
                        float *__restrict__ by32, float *__restrict__ bz32,
-                       float *__restrict__ diag32, float *__restrict__ idiag32, Dims d) {
+                       float *__restrict__ diag32, float *__restrict__ idiag32,
+                       __half *__restrict__ bx16, __half *__restrict__ by16,
+                       __half *__restrict__ bz16, float fs, Dims d) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
@@ -198,11 +202,15 @@ __global__ void k_diag(const double *__restrict__ bx, const double *__restrict__
   is = is * fma(-s, is, 2.0);
   diag[c] = s;
   idiag[c] = is;
-  bx32[c] = (float)bx[c];
-  by32[c] = (float)by[c];
-  bz32[c] = (float)bz[c];
+  const float fx = (float)bx[c], fy = (float)by[c], fz = (float)bz[c];
+  bx32[c] = fx;
+  by32[c] = fy;
+  bz32[c] = fz;
   diag32[c] = (float)s;
   idiag32[c] = (float)is;
+  bx16[c] = __float2half_rn(fx * fs);
+  by16[c] = __float2half_rn(fy * fs);
+  bz16[c] = __float2half_rn(fz * fs);
 }
 
 // ------------------------------------------- A5: coarse face coefficients
@@ -536,6 +544,91 @@ __device__ __forceinline__ void resid_restrict_cell(const T *__restrict__ x,
     s += resid_at(x, b, bx, by, bz, diag, df, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1),
                   2 * K + (q >> 2));
   bc[at(dc, I, J, K)] = (T)0.5 * s;
+}
+
+// ------------------------- FP32 V-cycle sweeps on FP16 face coefficients
+// The finest levels of the FP32 V-cycle read their face coefficients as FP16
+// copies scaled by a power of two fs (the largest coefficient lands just below
+// 2^14, the smallest of a 1e8 density ratio stays a normal number): 6 instead
+// of 12 bytes of coefficients per cell, the largest stream of a half-sweep.
+// FP16 keeps 11 bits; the V-cycle is only the preconditioner, and its smoother
+// and residual/restriction use the same rounded coefficients on every level
+// they run on, so it stays one fixed symmetric operator.  The CG operator and
+// every true residual keep the FP32/FP64 faces.
+__device__ __forceinline__ float hf(const __half *__restrict__ p, size_t i) {
+  return __half2float(p[i]);
+}
+
+// new value of one cell of a red-black half-sweep (loads only):
+// x_c = (sum_f w_f x_nb - fs bt_c) / sum_f w_f with w = fs beta
+__device__ __forceinline__ float rbgs_h_val(const float *__restrict__ x,
+                                            const float *__restrict__ b,
+                                            const __half *__restrict__ hx,
+                                            const __half *__restrict__ hy,
+                                            const __half *__restrict__ hz, const Dims &d, int i,
+                                            int j, int k, int zero, float fs) {
+  const size_t c = at(d, i, j, k);
+  const size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
+  const size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
+  const size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+  const float wxl = hf(hx, c), wxh = hf(hx, xh), wyl = hf(hy, c), wyh = hf(hy, yh),
+              wzl = hf(hz, c), wzh = hf(hz, zh);
+  float s = -b[c] * fs;
+  if (!zero) {
+    s = fmaf(wxl, x[xl], s);
+    s = fmaf(wxh, x[xh], s);
+    s = fmaf(wyl, x[yl], s);
+    s = fmaf(wyh, x[yh], s);
+    s = fmaf(wzl, x[zl], s);
+    s = fmaf(wzh, x[zh], s);
+  }
+  return __fdividef(s, ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh));
+}
+
+// red-black half-sweep on the FP16 faces (one cell of the colour per thread;
+// two planes per thread measured slower: fewer resident warps)
+__global__ void k_rbgs_h(float *__restrict__ x, const float *__restrict__ b,
+                         const __half *__restrict__ hx, const __half *__restrict__ hy,
+                         const __half *__restrict__ hz, Dims d, int colour, int zero, float fs) {
+  const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (t >= (d.nx >> 1) || j >= d.ny) return;
+  const int i = 2 * t + ((j + k + colour) & 1);
+  x[at(d, i, j, k)] = rbgs_h_val(x, b, hx, hy, hz, d, i, j, k, zero, fs);
+}
+
+// bt_c - (At x)_c with the FP16 faces (difference form, as the FP32 operator)
+__device__ __forceinline__ float resid_h(const float *__restrict__ x, const float *__restrict__ b,
+                                         const __half *__restrict__ hx,
+                                         const __half *__restrict__ hy,
+                                         const __half *__restrict__ hz, float inv_fs,
+                                         const Dims &d, int i, int j, int k) {
+  const size_t c = at(d, i, j, k);
+  const size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
+  const size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
+  const size_t zl = at(d, i, j, wlo(k, d.nz)), zh = at(d, i, j, whi(k, d.nz));
+  const float xc = x[c];
+  float s = hf(hx, c) * (x[xl] - xc);
+  s = fmaf(hf(hx, xh), x[xh] - xc, s);
+  s = fmaf(hf(hy, c), x[yl] - xc, s);
+  s = fmaf(hf(hy, yh), x[yh] - xc, s);
+  s = fmaf(hf(hz, c), x[zl] - xc, s);
+  s = fmaf(hf(hz, zh), x[zh] - xc, s);
+  return b[c] - s * inv_fs;
+}
+
+// residual + restriction (half the sum of the 8 children) on the FP16 faces
+__global__ void k_resid_restrict_h(const float *__restrict__ x, const float *__restrict__ b,
+                                   const __half *__restrict__ hx, const __half *__restrict__ hy,
+                                   const __half *__restrict__ hz, float inv_fs, Dims df,
+                                   float *__restrict__ bc, Dims dc) {
+  const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+  if (I >= dc.nx || J >= dc.ny) return;
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    s += resid_h(x, b, hx, hy, hz, inv_fs, df, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1),
+                 2 * K + (q >> 2));
+  bc[at(dc, I, J, K)] = 0.5f * s;
 }
 
 template <typename T>

@@ -34,6 +34,7 @@ struct Level {
   int nu1 = 2, nu2 = 2;
   double *bx = nullptr, *by = nullptr, *bz = nullptr, *diag = nullptr, *idiag = nullptr;
   float *bx32 = nullptr, *by32 = nullptr, *bz32 = nullptr, *diag32 = nullptr, *idiag32 = nullptr;
+  __half *bx16 = nullptr, *by16 = nullptr, *bz16 = nullptr;  // FP32 V-cycle faces, x fs16
   double *b = nullptr, *e = nullptr;   // coarse-level rhs / correction (levels >= 1)
   float *b32 = nullptr, *e32 = nullptr;
 };
@@ -97,6 +98,7 @@ struct mp_poisson {
   int *roots = nullptr;
   int defl_m = 0, defl_nband = 0;
   double beta_max = 1.0, ztb_scale = 1.0;
+  float fs16 = 1.f;  // scale of the FP16 faces (a power of two)
   double *einv = nullptr, *coef = nullptr, *dscale = nullptr;
   float *coef32 = nullptr;
   unsigned long long *acc_a = nullptr, *acc_b = nullptr, *acc_ztb = nullptr, *dmax = nullptr;
@@ -317,17 +319,29 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
   {
     dim3 hg = half_grid(lv.d);
     const int krb = kid<T>(K_RBGS64, K_RBGS32);
-    // FP32 forms 1/diag from the faces (no idiag read); FP64 reads the
-    // stored 1/diag (FP64 division is costly on this part)
-    const double per = sizeof(T) == 8 ? 5.0 : 4.5;
+    // FP64 reads the stored 1/diag (FP64 division is costly on this part);
+    // FP32 sweeps read FP16 faces and form 1/diag from them
+    const double per = sizeof(T) == 8 ? 5.0 : 3.0;
+    auto sweep = [&](int colour, int zero) -> mp_status {
+      const double bytes = (zero ? per - 0.5 : per) * nl * sz;
+      if constexpr (sizeof(T) == 4)
+        LAUNCH(hd, krb, l, bytes, k_rbgs_h, hg, kBlock, x, rhs, lv.bx16, lv.by16, lv.bz16, lv.d,
+               colour, zero, hd->fs16);
+      else
+        LAUNCH(hd, krb, l, bytes, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, colour,
+               zero);
+      return MP_OK;
+    };
     for (int s = 0; s < lv.nu1; ++s) {
-      LAUNCH(hd, krb, l, (s == 0 ? per - 0.5 : per) * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx,
-             by, bz, idiag, lv.d, 0, s == 0);
-      LAUNCH(hd, krb, l, per * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1,
-             0);
+      CKS(sweep(0, s == 0));
+      CKS(sweep(1, 0));
     }
-    LAUNCH(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
-           cell_grid(lc.d), kBlock, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
+    if constexpr (sizeof(T) == 4)
+      LAUNCH(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h, cell_grid(lc.d), kBlock, x,
+             rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d, LV<T>::b(lc), lc.d);
+    else
+      LAUNCH(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
+             cell_grid(lc.d), kBlock, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
     CKS(launch_ok());
     CKS(vcycle<T>(hd, l + 1, LV<T>::b(lc), LV<T>::e(lc)));
     constexpr int W = 16 / sizeof(T);
@@ -339,10 +353,8 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
       LAUNCH(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong<T>, cell_grid(lv.d),
              kBlock, x, LV<T>::e(lc), lv.d, lc.d);
     for (int s = 0; s < lv.nu2; ++s) {
-      LAUNCH(hd, krb, l, per * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 1,
-             0);
-      LAUNCH(hd, krb, l, per * nl * sz, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, 0,
-             0);
+      CKS(sweep(1, 0));
+      CKS(sweep(0, 0));
     }
   }
   return launch_ok();
@@ -951,6 +963,9 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
   LAUNCH(hd, K_JUMP, 0, n0 * 48.0, k_jump, cell_grid(l0.d), kBlock, hd->phi, hd->kap, l0.bx,
          l0.by, l0.bz, hd->Jt, l0.d, sigma);
   CKS(launch_ok());
+  // faces never exceed 1 / min(rho): scale them so the largest sits in (2^13, 2^14]
+  hd->beta_max = std::max(1.0 / rho_l, 1.0 / rho_g);
+  hd->fs16 = (float)std::ldexp(1.0, 14 - (int)std::ceil(std::log2(hd->beta_max)));
   for (size_t l = 0; l < hd->L.size(); ++l) {
     Level &lv = hd->L[l];
     if (l > 0) {
@@ -958,8 +973,9 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
       LAUNCH(hd, K_COARSEN, (int)l, lv.n * 120.0, k_coarsen_faces, cell_grid(lv.d), kBlock, lf.bx,
              lf.by, lf.bz, lf.d, lv.bx, lv.by, lv.bz, lv.d);
     }
-    LAUNCH(hd, K_DIAG, (int)l, lv.n * 60.0, k_diag, cell_grid(lv.d), kBlock, lv.bx, lv.by, lv.bz,
-           lv.diag, lv.idiag, lv.bx32, lv.by32, lv.bz32, lv.diag32, lv.idiag32, lv.d);
+    LAUNCH(hd, K_DIAG, (int)l, lv.n * 66.0, k_diag, cell_grid(lv.d), kBlock, lv.bx, lv.by, lv.bz,
+           lv.diag, lv.idiag, lv.bx32, lv.by32, lv.bz32, lv.diag32, lv.idiag32, lv.bx16, lv.by16,
+           lv.bz16, hd->fs16, lv.d);
     CKS(launch_ok());
   }
   Level &lc = hd->L.back();
@@ -969,7 +985,6 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
          lc.by, lc.bz, lc.diag, hd->Maug, lc.d);
   LAUNCH(hd, K_GJ, lcl, nc * 3.0 * nc * 8.0, k_gauss_jordan, 1, 1024, hd->Maug, hd->Minv, hd->nc);
   CKS(launch_ok());
-  hd->beta_max = std::max(1.0 / rho_l, 1.0 / rho_g);
   CKS(deflation_setup(hd));
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);
@@ -1022,6 +1037,9 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
     CKS(dalloc(hd, &lv.bz32, lv.n));
     CKS(dalloc(hd, &lv.diag32, lv.n));
     CKS(dalloc(hd, &lv.idiag32, lv.n));
+    CKS(dalloc(hd, &lv.bx16, lv.n));
+    CKS(dalloc(hd, &lv.by16, lv.n));
+    CKS(dalloc(hd, &lv.bz16, lv.n));
     if (l > 0) {
       CKS(dalloc(hd, &lv.b, lv.n));
       CKS(dalloc(hd, &lv.e, lv.n));

@@ -173,8 +173,11 @@ def test_project_step_matches_oracle(precision):
     ux, uy, uz = [dev(c) for c in u]
     p = torch.zeros_like(ux)
     s.project_step(ux, uy, uz, p, tol=TOL)
+    # the velocity error is the pressure's A-norm error (||u - u_ref||_beta =
+    # ||p - p_ref||_A), which a solve stopped below relative residual 1e-10
+    # bounds only to ~1e-9: the same parity bar as the pressure
     for g, o in zip((ux, uy, uz), (fx[:, :, :-1], fy[:, :-1, :], fz[:-1, :, :])):
-        assert rel_l2(host(g), o) < 1e-9
+        assert rel_l2(host(g), o) < PARITY
     # div u = b - A p on every cell: bounded by the solve's relative residual times ||b||
     div = oracle.divergence(host(ux), host(uy), host(uz), h)
     assert np.linalg.norm(div) <= 2 * TOL * np.linalg.norm(ref["b"])
