@@ -596,6 +596,73 @@ __global__ void k_rbgs_h(float *__restrict__ x, const float *__restrict__ b,
   x[at(d, i, j, k)] = rbgs_h_val(x, b, hx, hy, hz, d, i, j, k, zero, fs);
 }
 
+// The same half-sweep with 16-byte rows (nx a multiple of 4, 16-byte aligned
+// x and b): a thread owns the 4-cell x-chunk [4q, 4q + 4) of a row and
+// updates its two cells of the colour, loading x, b and the faces of the
+// chunk as vectors (14 loads for two cells instead of 26).  Each cell's
+// arithmetic is that of rbgs_h_val, operation for operation in the same order.
+struct __align__(8) H4 {
+  __half2 a, b;
+};
+__device__ __forceinline__ float h4_at(const H4 &v, int q) {
+  const __half2 p = q < 2 ? v.a : v.b;
+  return (q & 1) ? __high2float(p) : __low2float(p);
+}
+__device__ __forceinline__ float f4_at(const float4 &v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+__global__ void k_rbgs_h4(float *__restrict__ x, const float *__restrict__ b,
+                          const __half *__restrict__ hx, const __half *__restrict__ hy,
+                          const __half *__restrict__ hz, Dims d, int colour, int zero, float fs) {
+  const int qx = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (qx >= (d.nx >> 2) || j >= d.ny) return;
+  const int i0 = 4 * qx;
+  const int o = (j + k + colour) & 1;  // the chunk's cells of the colour: i0 + o, i0 + o + 2
+  const size_t c0 = at(d, i0, j, k);
+  const size_t cyl = at(d, i0, wlo(j, d.ny), k), cyh = at(d, i0, whi(j, d.ny), k);
+  const size_t czl = at(d, i0, j, wlo(k, d.nz)), czh = at(d, i0, j, whi(k, d.nz));
+  const float4 bb = *reinterpret_cast<const float4 *>(b + c0);
+  const H4 fx = *reinterpret_cast<const H4 *>(hx + c0);
+  const H4 fy = *reinterpret_cast<const H4 *>(hy + c0);
+  const H4 fyh = *reinterpret_cast<const H4 *>(hy + cyh);
+  const H4 fz = *reinterpret_cast<const H4 *>(hz + c0);
+  const H4 fzh = *reinterpret_cast<const H4 *>(hz + czh);
+  const float fxe = hf(hx, at(d, whi(i0 + 3, d.nx), j, k));  // high x face of cell i0 + 3
+  float4 xc = make_float4(0.f, 0.f, 0.f, 0.f), xyl = xc, xyh = xc, xzl = xc, xzh = xc;
+  float xm = 0.f, xp = 0.f;  // x[i0 - 1], x[i0 + 4] (wrapped)
+  if (!zero) {
+    xc = *reinterpret_cast<const float4 *>(x + c0);
+    xyl = *reinterpret_cast<const float4 *>(x + cyl);
+    xyh = *reinterpret_cast<const float4 *>(x + cyh);
+    xzl = *reinterpret_cast<const float4 *>(x + czl);
+    xzh = *reinterpret_cast<const float4 *>(x + czh);
+    xm = x[at(d, wlo(i0, d.nx), j, k)];
+    xp = x[at(d, whi(i0 + 3, d.nx), j, k)];
+  }
+  float v[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int q = o + 2 * e;  // position in the chunk
+    const float wxl = h4_at(fx, q), wxh = q < 3 ? h4_at(fx, q + 1) : fxe;
+    const float wyl = h4_at(fy, q), wyh = h4_at(fyh, q), wzl = h4_at(fz, q),
+                wzh = h4_at(fzh, q);
+    float s = -f4_at(bb, q) * fs;
+    if (!zero) {
+      const float x_l = q > 0 ? f4_at(xc, q - 1) : xm, x_h = q < 3 ? f4_at(xc, q + 1) : xp;
+      s = fmaf(wxl, x_l, s);
+      s = fmaf(wxh, x_h, s);
+      s = fmaf(wyl, f4_at(xyl, q), s);
+      s = fmaf(wyh, f4_at(xyh, q), s);
+      s = fmaf(wzl, f4_at(xzl, q), s);
+      s = fmaf(wzh, f4_at(xzh, q), s);
+    }
+    v[e] = __fdividef(s, ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh));
+  }
+  x[c0 + o] = v[0];
+  x[c0 + o + 2] = v[1];
+}
+
 // bt_c - (At x)_c with the FP16 faces (difference form, as the FP32 operator)
 __device__ __forceinline__ float resid_h(const float *__restrict__ x, const float *__restrict__ b,
                                          const __half *__restrict__ hx,

@@ -324,9 +324,15 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
     const double per = sizeof(T) == 8 ? 5.0 : 3.0;
     auto sweep = [&](int colour, int zero) -> mp_status {
       const double bytes = (zero ? per - 0.5 : per) * nl * sz;
-      if constexpr (sizeof(T) == 4)
-        LAUNCH(hd, krb, l, bytes, k_rbgs_h, hg, kBlock, x, rhs, lv.bx16, lv.by16, lv.bz16, lv.d,
-               colour, zero, hd->fs16);
+      if constexpr (sizeof(T) == 4) {
+        if (lv.d.nx % 4 == 0)  // 16-byte rows (level buffers are 256-byte aligned)
+          LAUNCH(hd, krb, l, bytes, k_rbgs_h4,
+                 dim3((lv.d.nx / 4 + BX - 1) / BX, (lv.d.ny + BY - 1) / BY, lv.d.nz), kBlock, x,
+                 rhs, lv.bx16, lv.by16, lv.bz16, lv.d, colour, zero, hd->fs16);
+        else
+          LAUNCH(hd, krb, l, bytes, k_rbgs_h, hg, kBlock, x, rhs, lv.bx16, lv.by16, lv.bz16,
+                 lv.d, colour, zero, hd->fs16);
+      }
       else
         LAUNCH(hd, krb, l, bytes, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, colour,
                zero);
