@@ -698,6 +698,65 @@ __global__ void k_resid_restrict_h(const float *__restrict__ x, const float *__r
   bc[at(dc, I, J, K)] = 0.5f * s;
 }
 
+// Residuals bt - At x of the 4-cell x-chunk [i0, i0 + 4) of fine row (j, k),
+// with the FP16 faces and 16-byte loads (resid_h's arithmetic per cell)
+__device__ __forceinline__ void resid_h4(const float *__restrict__ x, const float *__restrict__ b,
+                                         const __half *__restrict__ hx,
+                                         const __half *__restrict__ hy,
+                                         const __half *__restrict__ hz, float inv_fs,
+                                         const Dims &d, int i0, int j, int k, float r[4]) {
+  const size_t c0 = at(d, i0, j, k);
+  const size_t cyl = at(d, i0, wlo(j, d.ny), k), cyh = at(d, i0, whi(j, d.ny), k);
+  const size_t czl = at(d, i0, j, wlo(k, d.nz)), czh = at(d, i0, j, whi(k, d.nz));
+  const float4 bb = *reinterpret_cast<const float4 *>(b + c0);
+  const float4 xc = *reinterpret_cast<const float4 *>(x + c0);
+  const float4 xyl = *reinterpret_cast<const float4 *>(x + cyl);
+  const float4 xyh = *reinterpret_cast<const float4 *>(x + cyh);
+  const float4 xzl = *reinterpret_cast<const float4 *>(x + czl);
+  const float4 xzh = *reinterpret_cast<const float4 *>(x + czh);
+  const H4 fx = *reinterpret_cast<const H4 *>(hx + c0);
+  const H4 fy = *reinterpret_cast<const H4 *>(hy + c0);
+  const H4 fyh = *reinterpret_cast<const H4 *>(hy + cyh);
+  const H4 fz = *reinterpret_cast<const H4 *>(hz + c0);
+  const H4 fzh = *reinterpret_cast<const H4 *>(hz + czh);
+  const size_t ce = at(d, whi(i0 + 3, d.nx), j, k);
+  const float fxe = hf(hx, ce), xp = x[ce], xm = x[at(d, wlo(i0, d.nx), j, k)];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float v = f4_at(xc, q);
+    const float x_l = q > 0 ? f4_at(xc, q - 1) : xm, x_h = q < 3 ? f4_at(xc, q + 1) : xp;
+    float s = h4_at(fx, q) * (x_l - v);
+    s = fmaf(q < 3 ? h4_at(fx, q + 1) : fxe, x_h - v, s);
+    s = fmaf(h4_at(fy, q), f4_at(xyl, q) - v, s);
+    s = fmaf(h4_at(fyh, q), f4_at(xyh, q) - v, s);
+    s = fmaf(h4_at(fz, q), f4_at(xzl, q) - v, s);
+    s = fmaf(h4_at(fzh, q), f4_at(xzh, q) - v, s);
+    r[q] = f4_at(bb, q) - s * inv_fs;
+  }
+}
+
+// residual + restriction with 16-byte fine rows (fine nx a multiple of 4): a
+// thread owns coarse cells (2m, 2m + 1) of a coarse row, i.e. one 4-cell chunk
+// of each of its four fine rows; children summed in k_resid_restrict_h's order
+__global__ void k_resid_restrict_h4(const float *__restrict__ x, const float *__restrict__ b,
+                                    const __half *__restrict__ hx, const __half *__restrict__ hy,
+                                    const __half *__restrict__ hz, float inv_fs, Dims df,
+                                    float *__restrict__ bc, Dims dc) {
+  const int m = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+  if (m >= (df.nx >> 2) || J >= dc.ny) return;
+  float s0 = 0.f, s1 = 0.f, r[4];
+#pragma unroll
+  for (int row = 0; row < 4; ++row) {  // (dj, dk) = (0,0), (1,0), (0,1), (1,1)
+    resid_h4(x, b, hx, hy, hz, inv_fs, df, 4 * m, 2 * J + (row & 1), 2 * K + (row >> 1), r);
+    s0 += r[0];
+    s0 += r[1];
+    s1 += r[2];
+    s1 += r[3];
+  }
+  bc[at(dc, 2 * m, J, K)] = 0.5f * s0;
+  bc[at(dc, 2 * m + 1, J, K)] = 0.5f * s1;
+}
+
 template <typename T>
 __global__ void k_resid_restrict(const T *__restrict__ x, const T *__restrict__ b,
                                  const T *__restrict__ bx, const T *__restrict__ by,
@@ -770,6 +829,54 @@ __global__ void k_apply_dot(const T *__restrict__ dv, T *__restrict__ q, const T
     }
   double t = block_sum((double)acc);
   if (thread0()) partial[block_linear_id()] = t;
+}
+
+// q = At d (FP32 difference form, op_at's arithmetic per cell) and per-block
+// partials of d.q, with 16-byte rows (nx a multiple of 4): a thread owns a
+// 4-cell x-chunk in each of its zper planes and loads it as vectors
+__global__ void __launch_bounds__(BX * BY)
+k_apply_dot4(const float *__restrict__ dv, float *__restrict__ q, const float *__restrict__ bx,
+             const float *__restrict__ by, const float *__restrict__ bz, Dims d, int zper,
+             double *__restrict__ partial) {
+  const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
+  float acc = 0.f;
+  if (t < (d.nx >> 2) && j < d.ny)
+    for (int k = k0; k < k1; ++k) {
+      const int i0 = 4 * t;
+      const size_t c0 = at(d, i0, j, k);
+      const size_t cyl = at(d, i0, wlo(j, d.ny), k), cyh = at(d, i0, whi(j, d.ny), k);
+      const size_t czl = at(d, i0, j, wlo(k, d.nz)), czh = at(d, i0, j, whi(k, d.nz));
+      const size_t ce = at(d, whi(i0 + 3, d.nx), j, k);
+      const float4 xc = *reinterpret_cast<const float4 *>(dv + c0);
+      const float4 xyl = *reinterpret_cast<const float4 *>(dv + cyl);
+      const float4 xyh = *reinterpret_cast<const float4 *>(dv + cyh);
+      const float4 xzl = *reinterpret_cast<const float4 *>(dv + czl);
+      const float4 xzh = *reinterpret_cast<const float4 *>(dv + czh);
+      const float4 fx = *reinterpret_cast<const float4 *>(bx + c0);
+      const float4 fy = *reinterpret_cast<const float4 *>(by + c0);
+      const float4 fyh = *reinterpret_cast<const float4 *>(by + cyh);
+      const float4 fz = *reinterpret_cast<const float4 *>(bz + c0);
+      const float4 fzh = *reinterpret_cast<const float4 *>(bz + czh);
+      const float fxe = bx[ce], xp = dv[ce], xm = dv[at(d, wlo(i0, d.nx), j, k)];
+      float4 out;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float v = f4_at(xc, e);
+        const float x_l = e > 0 ? f4_at(xc, e - 1) : xm, x_h = e < 3 ? f4_at(xc, e + 1) : xp;
+        float s = f4_at(fx, e) * (x_l - v);
+        s = fmaf(e < 3 ? f4_at(fx, e + 1) : fxe, x_h - v, s);
+        s = fmaf(f4_at(fy, e), f4_at(xyl, e) - v, s);
+        s = fmaf(f4_at(fyh, e), f4_at(xyh, e) - v, s);
+        s = fmaf(f4_at(fz, e), f4_at(xzl, e) - v, s);
+        s = fmaf(f4_at(fzh, e), f4_at(xzh, e) - v, s);
+        if (e == 0) out.x = s; else if (e == 1) out.y = s; else if (e == 2) out.z = s; else out.w = s;
+        acc = fmaf(s, v, acc);
+      }
+      *reinterpret_cast<float4 *>(q + c0) = out;
+    }
+  const double tot = block_sum((double)acc);
+  if (thread0()) partial[block_linear_id()] = tot;
 }
 
 // r = b - At x (scaled), per-block partial of r.r; zero != 0: x = 0, r = b.

@@ -163,6 +163,12 @@ dim3 zgrid(const Dims &d) {
   int zp = zper_of(d);
   return dim3((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + zp - 1) / zp);
 }
+// the same decomposition for kernels that own 4-cell x-chunks (nx % 4 == 0)
+Dims chunk_dims(const Dims &d) {
+  Dims q = d;
+  q.nx = d.nx / 4;
+  return q;
+}
 int zblocks(const Dims &d) {
   dim3 g = zgrid(d);
   return (int)(g.x * g.y * g.z);
@@ -342,10 +348,15 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
       CKS(sweep(0, s == 0));
       CKS(sweep(1, 0));
     }
-    if constexpr (sizeof(T) == 4)
-      LAUNCH(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h, cell_grid(lc.d), kBlock, x,
-             rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d, LV<T>::b(lc), lc.d);
-    else
+    if constexpr (sizeof(T) == 4) {
+      if (lv.d.nx % 4 == 0)
+        LAUNCH(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h4,
+               dim3((lv.d.nx / 4 + BX - 1) / BX, (lc.d.ny + BY - 1) / BY, lc.d.nz), kBlock, x,
+               rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d, LV<T>::b(lc), lc.d);
+      else
+        LAUNCH(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h, cell_grid(lc.d), kBlock,
+               x, rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d, LV<T>::b(lc), lc.d);
+    } else
       LAUNCH(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
              cell_grid(lc.d), kBlock, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
     CKS(launch_ok());
@@ -711,9 +722,16 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
     CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
     LAUNCH(hd, K_XPBY32, 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<float>, VEC_BLOCKS, VEC_THREADS,
            dv, z, n, hd->scal, it == 0);
-    LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot<float>, zgrid(l0.d), kBlock, dv, q, l0.bx32,
-           l0.by32, l0.bz32, (float *)nullptr, l0.d, zper_of(l0.d), hd->partial);
-    CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
+    if (l0.d.nx % 4 == 0) {  // 16-byte rows
+      const Dims dq = chunk_dims(l0.d);
+      LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot4, zgrid(dq), kBlock, dv, q, l0.bx32,
+             l0.by32, l0.bz32, l0.d, zper_of(dq), hd->partial);
+      CKS(reduce(hd, zblocks(dq), OP_ALPHA, 0));
+    } else {
+      LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot<float>, zgrid(l0.d), kBlock, dv, q,
+             l0.bx32, l0.by32, l0.bz32, (float *)nullptr, l0.d, zper_of(l0.d), hd->partial);
+      CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
+    }
     LAUNCH(hd, K_AXPY32, 0, 6.0 * nsz, k_axpy2<float>, VEC_BLOCKS, VEC_THREADS, e, r, dv, q, n,
            hd->scal, hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
