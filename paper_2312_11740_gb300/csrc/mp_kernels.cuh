@@ -19,6 +19,12 @@ struct Dims {
 
 constexpr int BX = 32, BY = 8;  // per-cell launch tile (x fastest)
 
+// First statement of the V-cycle kernels: they are launched with programmatic
+// stream serialization (their blocks may be scheduled while the previous
+// kernel finishes) and read nothing before the previous kernel has completed
+// and its writes are visible.  A no-op for an ordinary launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ size_t at(const Dims &d, int i, int j, int k) {
   return (size_t)i + (size_t)d.nx * ((size_t)j + (size_t)d.ny * (size_t)k);
 }
@@ -281,6 +287,7 @@ __global__ void k_gauss_jordan(double *__restrict__ M, double *__restrict__ Minv
 template <typename T>
 __global__ void k_coarse_solve(const double *__restrict__ Minv, const T *__restrict__ b,
                                T *__restrict__ e, int n) {
+  griddep_wait();
   __shared__ double sb[512];
   __shared__ double mean;
   int t = threadIdx.x;
@@ -333,6 +340,7 @@ template <typename T>
 __global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__restrict__ bx,
                        const T *__restrict__ by, const T *__restrict__ bz,
                        const T *__restrict__ idiag, Dims d, int colour, int zero) {
+  griddep_wait();
   int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (t >= (d.nx >> 1) || j >= d.ny) return;
   rbgs_cell<T>(x, b, bx, by, bz, idiag, d, t, j, k, colour, zero);
@@ -450,6 +458,7 @@ __device__ __forceinline__ void tail_halfsweep(const TailView<T> &v, const Dims 
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS)
 k_tail(TailArgs a, const T *__restrict__ rhs, T *__restrict__ xout) {
+  griddep_wait();
   extern __shared__ __align__(16) unsigned char tail_smem[];
   T *base = reinterpret_cast<T *>(tail_smem);
   for (int l = 0; l < a.nlev; ++l) {
@@ -590,6 +599,7 @@ __device__ __forceinline__ float rbgs_h_val(const float *__restrict__ x,
 __global__ void k_rbgs_h(float *__restrict__ x, const float *__restrict__ b,
                          const __half *__restrict__ hx, const __half *__restrict__ hy,
                          const __half *__restrict__ hz, Dims d, int colour, int zero, float fs) {
+  griddep_wait();
   const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (t >= (d.nx >> 1) || j >= d.ny) return;
   const int i = 2 * t + ((j + k + colour) & 1);
@@ -615,6 +625,7 @@ __device__ __forceinline__ float f4_at(const float4 &v, int q) {
 __global__ void k_rbgs_h4(float *__restrict__ x, const float *__restrict__ b,
                           const __half *__restrict__ hx, const __half *__restrict__ hy,
                           const __half *__restrict__ hz, Dims d, int colour, int zero, float fs) {
+  griddep_wait();
   const int qx = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (qx >= (d.nx >> 2) || j >= d.ny) return;
   const int i0 = 4 * qx;
@@ -688,6 +699,7 @@ __global__ void k_resid_restrict_h(const float *__restrict__ x, const float *__r
                                    const __half *__restrict__ hx, const __half *__restrict__ hy,
                                    const __half *__restrict__ hz, float inv_fs, Dims df,
                                    float *__restrict__ bc, Dims dc) {
+  griddep_wait();
   const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
   if (I >= dc.nx || J >= dc.ny) return;
   float s = 0.f;
@@ -742,6 +754,7 @@ __global__ void k_resid_restrict_h4(const float *__restrict__ x, const float *__
                                     const __half *__restrict__ hx, const __half *__restrict__ hy,
                                     const __half *__restrict__ hz, float inv_fs, Dims df,
                                     float *__restrict__ bc, Dims dc) {
+  griddep_wait();
   const int m = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
   if (m >= (df.nx >> 2) || J >= dc.ny) return;
   float s0 = 0.f, s1 = 0.f, r[4];
@@ -762,6 +775,7 @@ __global__ void k_resid_restrict(const T *__restrict__ x, const T *__restrict__ 
                                  const T *__restrict__ bx, const T *__restrict__ by,
                                  const T *__restrict__ bz, const T *__restrict__ diag, Dims df,
                                  T *__restrict__ bc, Dims dc) {
+  griddep_wait();
   int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
   if (I >= dc.nx || J >= dc.ny) return;
   resid_restrict_cell<T>(x, b, bx, by, bz, diag, df, bc, dc, I, J, K);
@@ -771,6 +785,7 @@ __global__ void k_resid_restrict(const T *__restrict__ x, const T *__restrict__ 
 // piecewise-constant: each fine cell adds its parent's correction
 template <typename T>
 __global__ void k_prolong(T *__restrict__ x, const T *__restrict__ ec, Dims df, Dims dc) {
+  griddep_wait();
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= df.nx || j >= df.ny) return;
   x[at(df, i, j, k)] += ec[at(dc, i >> 1, j >> 1, k >> 1)];
@@ -781,6 +796,7 @@ __global__ void k_prolong(T *__restrict__ x, const T *__restrict__ ec, Dims df, 
 // rows stay 16-byte aligned).  The scalar form is latency-bound at ~21% of HBM.
 template <typename T>
 __global__ void k_prolong_vec(T *__restrict__ x, const T *__restrict__ ec, Dims df, Dims dc) {
+  griddep_wait();
   constexpr int W = 16 / sizeof(T);  // cells per thread (FP32: 4, FP64: 2)
   const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (t >= df.nx / W || j >= df.ny) return;

@@ -238,6 +238,38 @@ void prof_end(mp_poisson *hd, int id, int level, double bytes) {
     kern<<<(grid), (block), 0, (hd)->st>>>(__VA_ARGS__);          \
     prof_end((hd), (id), (level), (double)(bytes));               \
   } while (0)
+// Launch with programmatic stream serialization: the kernel's blocks may be
+// scheduled while the previous kernel on the stream finishes (hiding the
+// launch gap of the small coarse-level kernels); the kernel must begin with
+// griddep_wait().  Falls back to an ordinary launch if the attribute is refused.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...) != cudaSuccess) {
+    cudaGetLastError();
+    kern<<<grid, block, smem, st>>>(static_cast<KArgs>(args)...);
+  }
+}
+// LAUNCH for the V-cycle kernels (eager and profiled: an ordinary launch)
+#define LAUNCH_PDL(hd, id, level, bytes, kern, grid, block, smem, ...)       \
+  do {                                                                      \
+    prof_begin((hd), (id), (level));                                        \
+    if ((hd)->prof_on)                                                      \
+      kern<<<(grid), (block), (smem), (hd)->st>>>(__VA_ARGS__);             \
+    else                                                                    \
+      launch_pdl(kern, (grid), (block), (smem), (hd)->st, __VA_ARGS__);     \
+    prof_end((hd), (id), (level), (double)(bytes));                         \
+  } while (0)
 // the same with dynamic shared memory
 #define LAUNCH_SMEM(hd, id, level, bytes, kern, grid, block, smem, ...) \
   do {                                                                  \
@@ -310,12 +342,12 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
     }
     size_t smem = sizeof(T) == 8 ? hd->tail64_bytes : hd->tail32_bytes;
     auto ktail = k_tail<T>;
-    LAUNCH_SMEM(hd, kid<T>(K_TAIL64, K_TAIL32), l, bytes, ktail, 1, TAIL_THREADS, smem, a, rhs, x);
+    LAUNCH_PDL(hd, kid<T>(K_TAIL64, K_TAIL32), l, bytes, ktail, 1, TAIL_THREADS, smem, a, rhs, x);
     return launch_ok();
   }
   if (l == (int)hd->L.size() - 1) {
-    LAUNCH(hd, kid<T>(K_COARSE64, K_COARSE32), l, lv.n * (lv.n * 8.0 + 2.0 * sizeof(T)),
-           k_coarse_solve<T>, 1, 512, hd->Minv, rhs, x, (int)lv.n);
+    LAUNCH_PDL(hd, kid<T>(K_COARSE64, K_COARSE32), l, lv.n * (lv.n * 8.0 + 2.0 * sizeof(T)),
+               k_coarse_solve<T>, 1, 512, 0, hd->Minv, rhs, x, (int)lv.n);
     return launch_ok();
   }
   Level &lc = hd->L[l + 1];
@@ -332,16 +364,16 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
       const double bytes = (zero ? per - 0.5 : per) * nl * sz;
       if constexpr (sizeof(T) == 4) {
         if (lv.d.nx % 4 == 0)  // 16-byte rows (level buffers are 256-byte aligned)
-          LAUNCH(hd, krb, l, bytes, k_rbgs_h4,
-                 dim3((lv.d.nx / 4 + BX - 1) / BX, (lv.d.ny + BY - 1) / BY, lv.d.nz), kBlock, x,
-                 rhs, lv.bx16, lv.by16, lv.bz16, lv.d, colour, zero, hd->fs16);
+          LAUNCH_PDL(hd, krb, l, bytes, k_rbgs_h4,
+                     dim3((lv.d.nx / 4 + BX - 1) / BX, (lv.d.ny + BY - 1) / BY, lv.d.nz), kBlock,
+                     0, x, rhs, lv.bx16, lv.by16, lv.bz16, lv.d, colour, zero, hd->fs16);
         else
-          LAUNCH(hd, krb, l, bytes, k_rbgs_h, hg, kBlock, x, rhs, lv.bx16, lv.by16, lv.bz16,
-                 lv.d, colour, zero, hd->fs16);
+          LAUNCH_PDL(hd, krb, l, bytes, k_rbgs_h, hg, kBlock, 0, x, rhs, lv.bx16, lv.by16,
+                     lv.bz16, lv.d, colour, zero, hd->fs16);
       }
       else
-        LAUNCH(hd, krb, l, bytes, k_rbgs<T>, hg, kBlock, x, rhs, bx, by, bz, idiag, lv.d, colour,
-               zero);
+        LAUNCH_PDL(hd, krb, l, bytes, k_rbgs<T>, hg, kBlock, 0, x, rhs, bx, by, bz, idiag, lv.d,
+                   colour, zero);
       return MP_OK;
     };
     for (int s = 0; s < lv.nu1; ++s) {
@@ -350,25 +382,27 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
     }
     if constexpr (sizeof(T) == 4) {
       if (lv.d.nx % 4 == 0)
-        LAUNCH(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h4,
-               dim3((lv.d.nx / 4 + BX - 1) / BX, (lc.d.ny + BY - 1) / BY, lc.d.nz), kBlock, x,
-               rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d, LV<T>::b(lc), lc.d);
+        LAUNCH_PDL(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h4,
+                   dim3((lv.d.nx / 4 + BX - 1) / BX, (lc.d.ny + BY - 1) / BY, lc.d.nz), kBlock,
+                   0, x, rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d, LV<T>::b(lc),
+                   lc.d);
       else
-        LAUNCH(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h, cell_grid(lc.d), kBlock,
-               x, rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d, LV<T>::b(lc), lc.d);
+        LAUNCH_PDL(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h, cell_grid(lc.d),
+                   kBlock, 0, x, rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d,
+                   LV<T>::b(lc), lc.d);
     } else
-      LAUNCH(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
-             cell_grid(lc.d), kBlock, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
+      LAUNCH_PDL(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
+                 cell_grid(lc.d), kBlock, 0, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
     CKS(launch_ok());
     CKS(vcycle<T>(hd, l + 1, LV<T>::b(lc), LV<T>::e(lc)));
     constexpr int W = 16 / sizeof(T);
     if (lv.d.nx % (2 * W) == 0)
-      LAUNCH(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong_vec<T>,
-             dim3((lv.d.nx / W + BX - 1) / BX, (lv.d.ny + BY - 1) / BY, lv.d.nz), kBlock, x,
-             LV<T>::e(lc), lv.d, lc.d);
+      LAUNCH_PDL(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong_vec<T>,
+                 dim3((lv.d.nx / W + BX - 1) / BX, (lv.d.ny + BY - 1) / BY, lv.d.nz), kBlock, 0,
+                 x, LV<T>::e(lc), lv.d, lc.d);
     else
-      LAUNCH(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong<T>, cell_grid(lv.d),
-             kBlock, x, LV<T>::e(lc), lv.d, lc.d);
+      LAUNCH_PDL(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong<T>,
+                 cell_grid(lv.d), kBlock, 0, x, LV<T>::e(lc), lv.d, lc.d);
     for (int s = 0; s < lv.nu2; ++s) {
       CKS(sweep(1, 0));
       CKS(sweep(0, 0));
@@ -655,9 +689,9 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
 // true FP64 residual bt - At p (rounded to FP32).  The search direction is
 // kept across replacements (no restart), so the iteration count stays close
 // to that of FP64 PCG while every stencil sweep moves 4-byte values.
-// On entry r32 holds the true residual of p with norm rn.
+// On entry r32 holds the true residual of p with norm rn; p_zero: p is zero.
 mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int maxit, int *iters,
-                    int *outer, std::vector<double> *hist, double inv_b) {
+                    int *outer, std::vector<double> *hist, double inv_b, bool p_zero) {
   Level &l0 = hd->L[0];
   const mp_opts &o = hd->opts;
   const size_t n = hd->n;
@@ -672,10 +706,12 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
   // the true residual is projected in FP64 and rounded afterwards: near the
   // components both bt - At p and A Z c are large, and rounding before the
   // subtraction would leave their FP32 rounding error in the projected residual
-  auto project_true = [&](double &rnorm) -> mp_status {
+  // (p_is_zero: p = 0, so bt - At p = bt off the band without the FP64 stencil)
+  auto project_true = [&](double &rnorm, int p_is_zero) -> mp_status {
     CKS((defl_coef<double, double>(hd, p, l0.bx, l0.by, l0.bz, true)));
-    LAUNCH(hd, K_RESIDMIX, 0, n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b, r,
-           l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+    LAUNCH(hd, K_RESIDMIX, 0, n * (p_is_zero ? 12.0 : 52.0), k_residual_mixed, zgrid(l0.d),
+           kBlock, p, hd->b, r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial,
+           p_is_zero);
     const int nb = hd->defl_nband;
     LAUNCH(hd, K_DEFL, 0, nb * 120.0, k_defl_resid_band, VEC_BLOCKS, VEC_THREADS, hd->band, nb,
            hd->comp, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->coef, p, hd->b, r);
@@ -687,7 +723,7 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
   };
   if (defl) {
     CKS(defl_ztb(hd));
-    CKS(project_true(rn));
+    CKS(project_true(rn, p_zero ? 1 : 0));
   }
   double rn_rep = rn, rec = rn;
   CK(cudaMemsetAsync(e, 0, n * sizeof(float), hd->st));
@@ -697,7 +733,7 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
       // reliable update: p += e32 (e32 = 0), r32 = bt - At p from FP64
       LAUNCH(hd, K_ADDF32, 0, n * 24.0, k_add_f32, VEC_BLOCKS, VEC_THREADS, p, e, n);
       if (defl) {
-        CKS(project_true(rn));
+        CKS(project_true(rn, 0));
       } else {
         LAUNCH(hd, K_RESIDMIX, 0, n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b, r,
                l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
@@ -919,7 +955,7 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
       if (o.method == 0) {
         // PCG with reliable updates (replaces the refinement loop)
         int pit = 0, pout = 0;
-        st = pcg_mixed(hd, p, rn, tol_abs, o.max_iters, &pit, &pout, hist, inv_b);
+        st = pcg_mixed(hd, p, rn, tol_abs, o.max_iters, &pit, &pout, hist, inv_b, zero != 0);
         total = pit;
         outer = pout;
         if (st != MP_OK && st != MP_ERR_NOT_CONVERGED && st != MP_ERR_DIVERGED) return st;
