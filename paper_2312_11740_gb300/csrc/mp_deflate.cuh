@@ -495,7 +495,8 @@ __global__ void k_defl_sub_aw(const int *__restrict__ band, int nband, const int
 // The projected true residual on the band, formed in FP64 and rounded once:
 // r32_c = fl32((bt - At p)_c - (At Z coef)_c).  Off the band (At Z coef)_c = 0
 // and r32 already holds fl32(bt - At p).  Near a component both terms are
-// large and nearly cancel, so they must not be rounded separately.
+// large and nearly cancel, so they must not be rounded separately.  p may be
+// null: p = 0.
 __global__ void k_defl_resid_band(const int *__restrict__ band, int nband,
                                   const int *__restrict__ comp, const double *__restrict__ bx,
                                   const double *__restrict__ by, const double *__restrict__ bz,
@@ -506,7 +507,7 @@ __global__ void k_defl_resid_band(const int *__restrict__ band, int nband,
     const size_t c = (size_t)band[e];
     int i, j, k;
     cell_ijk(d, c, i, j, k);
-    const double res = resid_at<double>(p, b, bx, by, bz, diag, d, i, j, k);
+    const double res = p ? resid_at<double>(p, b, bx, by, bz, diag, d, i, j, k) : b[c];
     r32[c] = (float)(res - band_aw(bx, by, bz, comp, d, c, i, j, k, coef));
   }
 }

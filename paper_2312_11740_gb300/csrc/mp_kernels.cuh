@@ -282,6 +282,52 @@ __global__ void k_gauss_jordan(double *__restrict__ M, double *__restrict__ Minv
   }
 }
 
+// Inverse of the SPD coarsest matrix M (left half of [M | I]) by columns, for
+// n <= GJ_SMEM_MAX: block j factors M = L L^T in shared memory (every block the
+// same factor) and solves L L^T x = e_j into column j.  The n blocks run on n
+// SMs at once; one block's Gauss-Jordan elimination is bound by a single SM's
+// FP64 rate, which is low on this part.
+constexpr int GJ_SMEM_MAX = 112;
+__global__ void k_inverse_cols(const double *__restrict__ Maug, double *__restrict__ Minv, int n) {
+  extern __shared__ double L[];  // n x n, then the right-hand side / solution (n)
+  __shared__ double inv_d[GJ_SMEM_MAX];
+  double *y = L + n * n;
+  const int w = 2 * n, j = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) L[e] = Maug[(size_t)(e / n) * w + (e % n)];
+  for (int e = tid; e < n; e += nt) y[e] = e == j ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {  // right-looking Cholesky, lower triangle
+    if (tid == 0) {
+      const double dkk = sqrt(L[k * n + k]);
+      L[k * n + k] = dkk;
+      inv_d[k] = 1.0 / dkk;
+    }
+    __syncthreads();
+    const double id = inv_d[k];
+    for (int r = k + 1 + tid; r < n; r += nt) L[r * n + k] *= id;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int r = k + 1 + e / m, c = k + 1 + e % m;
+      if (c <= r) L[r * n + c] -= L[r * n + k] * L[c * n + k];
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < n; ++c) {  // L y = e_j (column-oriented)
+    if (tid == 0) y[c] *= inv_d[c];
+    __syncthreads();
+    for (int r = c + 1 + tid; r < n; r += nt) y[r] -= L[r * n + c] * y[c];
+    __syncthreads();
+  }
+  for (int c = n - 1; c >= 0; --c) {  // L^T x = y
+    if (tid == 0) y[c] *= inv_d[c];
+    __syncthreads();
+    for (int r = tid; r < c; r += nt) y[r] -= L[c * n + r] * y[c];
+    __syncthreads();
+  }
+  for (int r = tid; r < n; r += nt) Minv[(size_t)r * n + j] = y[r];
+}
+
 // e = M^-1 (-(b - mean b)), FP64 internally for any storage type T.
 // One block of 512 threads; n <= 512.
 template <typename T>

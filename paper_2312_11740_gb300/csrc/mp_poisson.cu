@@ -681,6 +681,36 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
   return st;
 }
 
+// r32 = fl32(P (bt - At p)) and its norm, deflation active.  The projection
+// is formed in FP64 and rounded afterwards: near the components both bt - At p
+// and A Z c are large, and rounding before the subtraction would leave their
+// FP32 rounding error in the projected residual.  p_is_zero: p is taken as
+// zero (not read), so bt - At p = bt off the band without the FP64 stencil.
+// Needs defl_ztb of the current right-hand side.
+mp_status defl_true_residual32(mp_poisson *hd, const double *p, int p_is_zero, double *rnorm) {
+  Level &l0 = hd->L[0];
+  const size_t n = hd->n;
+  const int m = hd->defl_m, nb = hd->defl_nband;
+  if (p_is_zero)  // coef = E^-1 Z^T bt
+    LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, hd->acc_ztb,
+           (const double *)nullptr, hd->ztb_scale, 0, (unsigned long long *)nullptr,
+           (const double *)nullptr, hd->einv, hd->coef, hd->coef32, hd->dmax);
+  else
+    CKS((defl_coef<double, double>(hd, p, l0.bx, l0.by, l0.bz, true)));
+  LAUNCH(hd, K_RESIDMIX, 0, n * (p_is_zero ? 12.0 : 52.0), k_residual_mixed, zgrid(l0.d), kBlock,
+         p, hd->b, hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial,
+         p_is_zero);
+  LAUNCH(hd, K_DEFL, 0, nb * 120.0, k_defl_resid_band, VEC_BLOCKS, VEC_THREADS, hd->band, nb,
+         hd->comp, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->coef,
+         p_is_zero ? (const double *)nullptr : p, hd->b, hd->r32);
+  LAUNCH(hd, K_DOT32, 0, 4.0 * n, k_dot<float>, VEC_BLOCKS, VEC_THREADS, hd->r32, hd->r32, n,
+         hd->partial);
+  CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
+  CKS(read_scalars(hd));
+  *rnorm = std::sqrt(hd->scal_h[S_RR]);
+  return MP_OK;
+}
+
 // Mixed-precision PCG with reliable updates.  The Krylov iteration (V-cycle
 // preconditioner, operator, vector updates) runs in FP32 on a correction e32
 // and residual r32.  Whenever the recurrence residual has fallen by
@@ -703,23 +733,8 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
   // At p)), with Z^T (bt - At p) = Z^T bt - (At Z)^T p from FP64 p; after every
   // V-cycle z <- P^T z in FP32; the exit adds Z E^-1 Z^T (bt - At p) to p
   const bool defl = defl_active(hd);
-  // the true residual is projected in FP64 and rounded afterwards: near the
-  // components both bt - At p and A Z c are large, and rounding before the
-  // subtraction would leave their FP32 rounding error in the projected residual
-  // (p_is_zero: p = 0, so bt - At p = bt off the band without the FP64 stencil)
   auto project_true = [&](double &rnorm, int p_is_zero) -> mp_status {
-    CKS((defl_coef<double, double>(hd, p, l0.bx, l0.by, l0.bz, true)));
-    LAUNCH(hd, K_RESIDMIX, 0, n * (p_is_zero ? 12.0 : 52.0), k_residual_mixed, zgrid(l0.d),
-           kBlock, p, hd->b, r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial,
-           p_is_zero);
-    const int nb = hd->defl_nband;
-    LAUNCH(hd, K_DEFL, 0, nb * 120.0, k_defl_resid_band, VEC_BLOCKS, VEC_THREADS, hd->band, nb,
-           hd->comp, l0.bx, l0.by, l0.bz, l0.diag, l0.d, hd->coef, p, hd->b, r);
-    LAUNCH(hd, K_DOT32, 0, 4.0 * n, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, r, n, hd->partial);
-    CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
-    CKS(read_scalars(hd));
-    rnorm = std::sqrt(hd->scal_h[S_RR]);
-    return MP_OK;
+    return defl_true_residual32(hd, p, p_is_zero, &rnorm);
   };
   if (defl) {
     CKS(defl_ztb(hd));
@@ -892,17 +907,27 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     double alpha = hd->scal_h[S_RZ] / hd->scal_h[S_TMP];
     if (!std::isfinite(alpha)) alpha = 0.0;
     LAUNCH(hd, K_SCALE, 0, hd->n * 16.0, k_scale, VEC_BLOCKS, VEC_THREADS, p, p, hd->n, alpha);
-    if (o.precision == 0)
-      LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b,
-             hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
-    else
-      LAUNCH(hd, K_RESIDMIX, 0, hd->n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p, hd->b,
-             hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
-    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
-    CKS(read_scalars(hd));
-    double rnet = std::sqrt(hd->scal_h[S_RR]), rzero = hd->bnorm;
-    if (defl_active(hd) && o.net_check == 0 && std::isfinite(rnet))
-      CKS(defl_guess_residuals(hd, p, &rnet, &rzero));
+    double rnet = 0.0, rzero = hd->bnorm;
+    const bool defl_mixed = defl_active(hd) && o.net_check == 0 && o.precision == 1;
+    if (defl_mixed) {
+      // deflated residuals of the zero guess and of the guess (mixed PCG forms
+      // the guess's again at its start when the guess is kept)
+      CKS(defl_ztb(hd));
+      CKS(defl_true_residual32(hd, p, 1, &rzero));
+      CKS(defl_true_residual32(hd, p, 0, &rnet));
+    } else {
+      if (o.precision == 0)
+        LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b,
+               hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+      else
+        LAUNCH(hd, K_RESIDMIX, 0, hd->n * 52.0, k_residual_mixed, zgrid(l0.d), kBlock, p,
+               hd->b, hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
+      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_RR));
+      CKS(read_scalars(hd));
+      rnet = std::sqrt(hd->scal_h[S_RR]);
+      if (defl_active(hd) && o.net_check == 0 && std::isfinite(rnet))
+        CKS(defl_guess_residuals(hd, p, &rnet, &rzero));
+    }
     hd->stats.net_relres = rnet / rzero;
     const bool keep = o.net_check == 0 ? rnet < rzero : alpha != 0.0;
     if (keep && std::isfinite(rnet)) {
@@ -1043,7 +1068,12 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
   const double nc = (double)hd->nc;
   LAUNCH(hd, K_DENSE, lcl, nc * 2.0 * nc * 8.0, k_dense_build, (hd->nc + 127) / 128, 128, lc.bx,
          lc.by, lc.bz, lc.diag, hd->Maug, lc.d);
-  LAUNCH(hd, K_GJ, lcl, nc * 3.0 * nc * 8.0, k_gauss_jordan, 1, 1024, hd->Maug, hd->Minv, hd->nc);
+  if (hd->nc <= GJ_SMEM_MAX)
+    LAUNCH_SMEM(hd, K_GJ, lcl, nc * 3.0 * nc * 8.0, k_inverse_cols, hd->nc, 256,
+                (size_t)(hd->nc + 1) * hd->nc * sizeof(double), hd->Maug, hd->Minv, hd->nc);
+  else
+    LAUNCH(hd, K_GJ, lcl, nc * 3.0 * nc * 8.0, k_gauss_jordan, 1, 1024, hd->Maug, hd->Minv,
+           hd->nc);
   CKS(launch_ok());
   CKS(deflation_setup(hd));
   CK(cudaStreamSynchronize(hd->st));
@@ -1176,6 +1206,8 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
       hd->tail32_bytes = bytes;
     }
   }
+  CK(cudaFuncSetAttribute(k_inverse_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)((GJ_SMEM_MAX + 1) * GJ_SMEM_MAX * sizeof(double))));
   CK(cudaFuncSetAttribute(k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)std::max<size_t>(hd->tail64_bytes, 1)));
   CK(cudaFuncSetAttribute(k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
