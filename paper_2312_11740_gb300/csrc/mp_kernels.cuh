@@ -188,35 +188,39 @@ __global__ void k_jump(const double *__restrict__ phi, const double *__restrict_
   Jt[c] = s;
 }
 
-// diag = sum of the six face betas, idiag = 1/diag; f64 and f32 copies, and
-// the FP16 faces of the FP32 V-cycle, stored as beta * fs
+// diag = sum of the six face betas (always); MODE & 1: idiag = 1/diag (the
+// FP64 smoother); MODE & 2: FP32 faces and 1/diag (CG operator, one-CTA tail)
+// and the FP16 faces of the FP32 V-cycle, stored as beta * fs
+template <int MODE>
 __global__ void k_diag(const double *__restrict__ bx, const double *__restrict__ by,
                        const double *__restrict__ bz, double *__restrict__ diag,
                        double *__restrict__ idiag, float *__restrict__ bx32,
                        float *__restrict__ by32, float *__restrict__ bz32,
-                       float *__restrict__ diag32, float *__restrict__ idiag32,
-                       __half *__restrict__ bx16, __half *__restrict__ by16,
-                       __half *__restrict__ bz16, float fs, Dims d) {
+                       float *__restrict__ idiag32, __half *__restrict__ bx16,
+                       __half *__restrict__ by16, __half *__restrict__ bz16, float fs, Dims d) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
   double s = bx[c] + bx[at(d, whi(i, d.nx), j, k)] + by[c] + by[at(d, i, whi(j, d.ny), k)] + bz[c] +
              bz[at(d, i, j, whi(k, d.nz))];
-  // 1/s: FP32 reciprocal refined by one Newton step in FP64 (relative error
-  // ~1e-14, two FP64 operations instead of a full FP64 division)
-  double is = (double)(1.0f / (float)s);
-  is = is * fma(-s, is, 2.0);
   diag[c] = s;
-  idiag[c] = is;
-  const float fx = (float)bx[c], fy = (float)by[c], fz = (float)bz[c];
-  bx32[c] = fx;
-  by32[c] = fy;
-  bz32[c] = fz;
-  diag32[c] = (float)s;
-  idiag32[c] = (float)is;
-  bx16[c] = __float2half_rn(fx * fs);
-  by16[c] = __float2half_rn(fy * fs);
-  bz16[c] = __float2half_rn(fz * fs);
+  if (MODE & 1) {
+    // 1/s: FP32 reciprocal refined by one Newton step in FP64 (relative error
+    // ~1e-14, two FP64 operations instead of a full FP64 division)
+    double is = (double)(1.0f / (float)s);
+    is = is * fma(-s, is, 2.0);
+    idiag[c] = is;
+  }
+  if (MODE & 2) {
+    const float fx = (float)bx[c], fy = (float)by[c], fz = (float)bz[c];
+    bx32[c] = fx;
+    by32[c] = fy;
+    bz32[c] = fz;
+    idiag32[c] = 1.0f / (float)s;
+    bx16[c] = __float2half_rn(fx * fs);
+    by16[c] = __float2half_rn(fy * fs);
+    bz16[c] = __float2half_rn(fz * fs);
+  }
 }
 
 // ------------------------------------------- A5: coarse face coefficients

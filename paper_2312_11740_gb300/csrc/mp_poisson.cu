@@ -33,7 +33,7 @@ struct Level {
   size_t n = 0;
   int nu1 = 2, nu2 = 2;
   double *bx = nullptr, *by = nullptr, *bz = nullptr, *diag = nullptr, *idiag = nullptr;
-  float *bx32 = nullptr, *by32 = nullptr, *bz32 = nullptr, *diag32 = nullptr, *idiag32 = nullptr;
+  float *bx32 = nullptr, *by32 = nullptr, *bz32 = nullptr, *idiag32 = nullptr;
   __half *bx16 = nullptr, *by16 = nullptr, *bz16 = nullptr;  // FP32 V-cycle faces, x fs16
   double *b = nullptr, *e = nullptr;   // coarse-level rhs / correction (levels >= 1)
   float *b32 = nullptr, *e32 = nullptr;
@@ -99,6 +99,7 @@ struct mp_poisson {
   int defl_m = 0, defl_nband = 0;
   double beta_max = 1.0, ztb_scale = 1.0;
   float fs16 = 1.f;  // scale of the FP16 faces (a power of two)
+  int diag_mode = 0;  // per-level arrays formed by k_diag for this geometry (bits: 1 FP64, 2 FP32)
   double *einv = nullptr, *coef = nullptr, *dscale = nullptr;
   float *coef32 = nullptr;
   unsigned long long *acc_a = nullptr, *acc_b = nullptr, *acc_ztb = nullptr, *dmax = nullptr;
@@ -312,7 +313,7 @@ template <> struct LV<float> {
   static float *bx(Level &l) { return l.bx32; }
   static float *by(Level &l) { return l.by32; }
   static float *bz(Level &l) { return l.bz32; }
-  static float *diag(Level &l) { return l.diag32; }
+  static float *diag(Level &) { return nullptr; }  // FP32 operators use the difference form
   static float *idiag(Level &l) { return l.idiag32; }
   static float *b(Level &l) { return l.b32; }
   static float *e(Level &l) { return l.e32; }
@@ -863,6 +864,8 @@ mp_status assemble_rhs_u(mp_poisson *hd, const double *ux, const double *uy, con
   return finish_rhs(hd, zblocks(l0.d));
 }
 
+mp_status diag_fields(mp_poisson *hd, int mode);
+
 // Solve At p = bt (bt in hd->b, S_BB set).  p: device FP64, in/out.
 mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<double> *hist) {
   Level &l0 = hd->L[0];
@@ -874,6 +877,8 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
   hd->stats.coarse_n = hd->nc;
   hd->stats.components = defl_active(hd) ? hd->defl_m : 0;
   if (o.initial_guess == 2 && !hd->net) return MP_ERR_NO_NET;
+  const int need = o.precision == 0 ? 1 : 2;
+  if ((hd->diag_mode & need) != need) CKS(diag_fields(hd, need));
   int zero = o.initial_guess == 0;
   if (zero) CK(cudaMemsetAsync(p, 0, hd->n * sizeof(double), hd->st));
   if (hd->bnorm == 0.0) {
@@ -1031,6 +1036,22 @@ void apply_nu(mp_poisson *hd) {
   }
 }
 
+// Per-level diagonal and face copies for the precisions in mode (bits: 1 = the
+// FP64 smoother's 1/diag, 2 = the FP32 faces, 1/diag and FP16 faces); a solve
+// in a precision whose arrays this geometry has not formed yet adds them.
+mp_status diag_fields(mp_poisson *hd, int mode) {
+  for (size_t l = 0; l < hd->L.size(); ++l) {
+    Level &lv = hd->L[l];
+    auto kd = mode == 1 ? k_diag<1> : (mode == 2 ? k_diag<2> : k_diag<3>);
+    LAUNCH(hd, K_DIAG, (int)l, lv.n * (mode == 1 ? 48.0 : (mode == 2 ? 58.0 : 66.0)), kd,
+           cell_grid(lv.d), kBlock, lv.bx, lv.by, lv.bz, lv.diag, lv.idiag, lv.bx32, lv.by32,
+           lv.bz32, lv.idiag32, lv.bx16, lv.by16, lv.bz16, hd->fs16, lv.d);
+    CKS(launch_ok());
+  }
+  hd->diag_mode |= mode;
+  return MP_OK;
+}
+
 mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g, double sigma) {
   if (!phi || !(rho_l > 0.0) || !(rho_g > 0.0) || !(sigma >= 0.0) || !std::isfinite(rho_l) ||
       !std::isfinite(rho_g) || !std::isfinite(sigma))
@@ -1058,11 +1079,9 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
       LAUNCH(hd, K_COARSEN, (int)l, lv.n * 120.0, k_coarsen_faces, cell_grid(lv.d), kBlock, lf.bx,
              lf.by, lf.bz, lf.d, lv.bx, lv.by, lv.bz, lv.d);
     }
-    LAUNCH(hd, K_DIAG, (int)l, lv.n * 66.0, k_diag, cell_grid(lv.d), kBlock, lv.bx, lv.by, lv.bz,
-           lv.diag, lv.idiag, lv.bx32, lv.by32, lv.bz32, lv.diag32, lv.idiag32, lv.bx16, lv.by16,
-           lv.bz16, hd->fs16, lv.d);
-    CKS(launch_ok());
   }
+  hd->diag_mode = 0;
+  CKS(diag_fields(hd, hd->opts.precision == 0 ? 1 : 2));
   Level &lc = hd->L.back();
   const int lcl = (int)hd->L.size() - 1;
   const double nc = (double)hd->nc;
@@ -1125,7 +1144,6 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
     CKS(dalloc(hd, &lv.bx32, lv.n));
     CKS(dalloc(hd, &lv.by32, lv.n));
     CKS(dalloc(hd, &lv.bz32, lv.n));
-    CKS(dalloc(hd, &lv.diag32, lv.n));
     CKS(dalloc(hd, &lv.idiag32, lv.n));
     CKS(dalloc(hd, &lv.bx16, lv.n));
     CKS(dalloc(hd, &lv.by16, lv.n));

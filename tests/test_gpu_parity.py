@@ -417,3 +417,26 @@ def test_fresh_handles_on_nonblocking_streams():
         else:
             assert float(torch.linalg.norm(p - p_ref) / torch.linalg.norm(p_ref)) < 1e-7
         s.close()
+
+
+def test_precision_switch_after_geometry():
+    """The per-precision arrays (FP64 1/diag; FP32 and FP16 faces) are formed
+    for the precision the geometry was set in, and added at the first solve in
+    the other precision: switching after set_geometry gives bitwise the answer
+    of a handle created in that precision."""
+    phi, u, prm = case("ragged")
+    rhs = dev(oracle.divergence(*u, prm["h"]))
+    results = {}
+    for first, second in ((0, 1), (1, 0)):
+        s = make(phi, prm, precision=first)
+        s.set_geometry(dev(phi), prm["rho_l"], prm["rho_g"], prm["sigma"])
+        s.solve(rhs)
+        s.set_opts(precision=second)
+        p, it, _ = s.solve(rhs)
+        results[second] = (p, it)
+        s.close()
+    for prec in (0, 1):
+        s = make(phi, prm, precision=prec)
+        p, it, _ = s.solve(rhs)
+        assert it == results[prec][1] and torch.equal(p, results[prec][0]), prec
+        s.close()
