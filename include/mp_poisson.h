@@ -73,7 +73,7 @@ typedef struct {
   double inner_rtol; /* mixed: the FP32 recurrence residual must fall by this factor below the
                         last true residual before the FP32 correction is folded into the FP64
                         solution and the residual replaced by the true FP64 one (reliable
-                        update; the CG direction is kept).  Default 1e-4. */
+                        update; the CG direction is kept).  Default 3e-3. */
   int inner_max;     /* mixed: at most this many FP32 iterations between true residuals.
                         Default 12. */
   int net_check;     /* learned guess p0 = alpha q (alpha energy-optimal) is kept when

@@ -160,15 +160,19 @@ __device__ __forceinline__ bool band_flag(const int *__restrict__ comp, const Di
          comp[at(d, i, j, wlo(k, d.nz))] != m || comp[at(d, i, j, whi(k, d.nz))] != m;
 }
 
-// number of band cells in each block of BAND_CELLS consecutive cells
+// number of band cells in each block of BAND_CELLS consecutive cells; the
+// per-cell flags are kept (one byte each) for k_band_assign
 __global__ void __launch_bounds__(BAND_THREADS) k_band_count(const int *__restrict__ comp, Dims d,
-                                                             size_t n, int *__restrict__ cnt) {
+                                                             size_t n, int *__restrict__ cnt,
+                                                             unsigned char *__restrict__ flag) {
   const size_t base = (size_t)blockIdx.x * BAND_CELLS;
   int total = 0;
 #pragma unroll
   for (int r = 0; r < BAND_ROUNDS; ++r) {
     const size_t c = base + (size_t)r * BAND_THREADS + threadIdx.x;
-    total += __syncthreads_count(c < n && band_flag(comp, d, c));
+    const bool f = c < n && band_flag(comp, d, c);
+    if (c < n) flag[c] = f ? 1 : 0;
+    total += __syncthreads_count(f);
   }
   if (threadIdx.x == 0) cnt[blockIdx.x] = total;
 }
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_counts(int *cnt, int nb, 
 }
 
 // band[id] = c for the band cells, in cell order (off: the scanned counts)
-__global__ void __launch_bounds__(BAND_THREADS) k_band_assign(const int *__restrict__ comp, Dims d,
+__global__ void __launch_bounds__(BAND_THREADS) k_band_assign(const unsigned char *__restrict__ flag,
                                                               size_t n, const int *__restrict__ off,
                                                               int *__restrict__ band) {
   __shared__ int wcount[BAND_THREADS / 32];
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_band_assign(const int *__restr
   int run = off[blockIdx.x];
   for (int r = 0; r < BAND_ROUNDS; ++r) {
     const size_t c = base + (size_t)r * BAND_THREADS + threadIdx.x;
-    const bool f = c < n && band_flag(comp, d, c);
+    const bool f = c < n && flag[c] != 0;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (lane == 0) wcount[w] = __popc(bal);
     __syncthreads();
