@@ -7,12 +7,14 @@
 // no longer resolved by the coarse grids.  CG is therefore deflated by the
 // indicator vectors z_j of the connected gas components (Tang & Vuik's
 // deflated PCG for bubbly flows): with Z = [z_1 .. z_m], E = Z^T A Z and
-// P = I - A Z E^-1 Z^T, CG solves P A x = P b and the solution is
+// P = I - A Z E^-1 Z^T, CG starts from the residual P r0, projects every
+// preconditioned residual, z <- P^T z (the A-DEF2 form of Tang, Nabben, Vuik
+// and Erlangga, which tolerates rounding), and the solution is
 // x + Z E^-1 Z^T (b - A x).  Components never share a face, so E is diagonal
 // (E_jj = -sum of the face coefficients on component j's boundary), and for
 // any v the products Z^T A v and A Z c are nonzero only on the band of cells
 // with a face to another component (or to liquid): the per-iteration work is a
-// few passes over that band, not over the grid.
+// few passes over that band and one fused pass over the grid.
 //
 // Components come from a union-find labelling of the gas cells (lowest cell
 // index as root); ids follow the roots' cell order, and every sum over cells
@@ -473,26 +475,17 @@ __device__ __forceinline__ double band_aw(const F *__restrict__ bx, const F *__r
   return aw;
 }
 
-// v_c -= (A w)_c on the band, w = coef[comp] (0 in liquid); optional per-block
-// partial sums of u_c (A w)_c (the change of u.v)
+// v_c -= (A w)_c on the band, w = coef[comp] (0 in liquid)
 template <typename T, typename F>
 __global__ void k_defl_sub_aw(const int *__restrict__ band, int nband, const int *__restrict__ comp,
                               const F *__restrict__ bx, const F *__restrict__ by,
                               const F *__restrict__ bz, Dims d, const double *__restrict__ coef,
-                              T *__restrict__ v, const T *__restrict__ u,
-                              double *__restrict__ partial) {
-  double acc = 0.0;
+                              T *__restrict__ v) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nband; e += gridDim.x * blockDim.x) {
     const size_t c = (size_t)band[e];
     int i, j, k;
     cell_ijk(d, c, i, j, k);
-    const double aw = band_aw(bx, by, bz, comp, d, c, i, j, k, coef);
-    v[c] = (T)((double)v[c] - aw);
-    if (u) acc += (double)u[c] * aw;
-  }
-  if (partial) {
-    const double t = block_sum(acc);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    v[c] = (T)((double)v[c] - band_aw(bx, by, bz, comp, d, c, i, j, k, coef));
   }
 }
 

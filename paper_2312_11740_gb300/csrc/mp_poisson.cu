@@ -557,15 +557,14 @@ mp_status defl_coef(mp_poisson *hd, const T *v, const F *bx, const F *by, const 
   return launch_ok();
 }
 
-// v -= A Z coef on the band; with u, per-block partials of u.(A Z coef) in hd->partial
+// v -= A Z coef on the band
 template <typename T, typename F>
-mp_status defl_sub(mp_poisson *hd, T *v, const T *u, const F *bx, const F *by, const F *bz) {
+mp_status defl_sub(mp_poisson *hd, T *v, const F *bx, const F *by, const F *bz) {
   Level &l0 = hd->L[0];
   const int nb = hd->defl_nband;
   auto ksub = k_defl_sub_aw<T, F>;
-  LAUNCH(hd, K_DEFL, 0, nb * (3.0 * sizeof(T) + 3.0 * sizeof(F) + 28.0), ksub, VEC_BLOCKS,
-         VEC_THREADS, hd->band, nb, hd->comp, bx, by, bz, l0.d, hd->coef, v, u,
-         u ? hd->partial : (double *)nullptr);
+  LAUNCH(hd, K_DEFL, 0, nb * (2.0 * sizeof(T) + 3.0 * sizeof(F) + 28.0), ksub, VEC_BLOCKS,
+         VEC_THREADS, hd->band, nb, hd->comp, bx, by, bz, l0.d, hd->coef, v);
   return launch_ok();
 }
 
@@ -588,7 +587,7 @@ mp_status defl_guess_residuals(mp_poisson *hd, const double *p, double *rguess, 
   LAUNCH(hd, K_RESID64, 0, n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b, hd->z,
          l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
   CKS((defl_coef<double, double>(hd, p, l0.bx, l0.by, l0.bz, true)));
-  CKS((defl_sub<double, double>(hd, hd->z, (const double *)nullptr, l0.bx, l0.by, l0.bz)));
+  CKS((defl_sub<double, double>(hd, hd->z, l0.bx, l0.by, l0.bz)));
   LAUNCH(hd, K_DOT64, 0, n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, hd->z, hd->z, n,
          hd->partial);
   CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_TMP));
@@ -600,7 +599,7 @@ mp_status defl_guess_residuals(mp_poisson *hd, const double *p, double *rguess, 
          (const double *)nullptr, hd->ztb_scale, 0, (unsigned long long *)nullptr,
          (const double *)nullptr, hd->einv, hd->coef, hd->coef32, hd->dmax);
   CK(cudaMemcpyAsync(hd->z, hd->b, n * sizeof(double), cudaMemcpyDeviceToDevice, hd->st));
-  CKS((defl_sub<double, double>(hd, hd->z, (const double *)nullptr, l0.bx, l0.by, l0.bz)));
+  CKS((defl_sub<double, double>(hd, hd->z, l0.bx, l0.by, l0.bz)));
   LAUNCH(hd, K_DOT64, 0, n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, hd->z, hd->z, n,
          hd->partial);
   CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_TMP));
@@ -642,7 +641,7 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
   if (defl) {
     CKS(defl_ztb(hd));
     CKS((defl_coef<T, T>(hd, x, bx, by, bz, true)));
-    CKS((defl_sub<T, T>(hd, r, (const T *)nullptr, bx, by, bz)));
+    CKS((defl_sub<T, T>(hd, r, bx, by, bz)));
     LAUNCH(hd, kid<T>(K_DOT64, K_DOT32), 0, 2.0 * nsz, k_dot<T>, VEC_BLOCKS, VEC_THREADS, r, r, n,
            hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
