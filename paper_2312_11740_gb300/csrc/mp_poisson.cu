@@ -903,9 +903,20 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
                           (hd->per & 2) ? MP_BC_PERIODIC : MP_BC_NEUMANN,
                           (hd->per & 4) ? MP_BC_PERIODIC : MP_BC_NEUMANN};
     CKS(mp_net_pressure_at(hd->net, hd->net_factor, nbc, 1.0, p));
-    LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, p, hd->q,
-           l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial);
-    CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_TMP));
+    if (o.precision == 1 && l0.d.nx % 4 == 0) {
+      // q . At q from the FP32 operator on fl32(q): alpha is a scale factor,
+      // and 1e-7 relative is ample (an FP64 operator pass is FP64-rate bound)
+      LAUNCH(hd, K_RESIDMIX, 0, hd->n * 12.0, k_to_f32_norm, VEC_BLOCKS, VEC_THREADS, p, hd->z32,
+             hd->n, hd->partial);
+      const Dims dq = chunk_dims(l0.d);
+      LAUNCH(hd, K_APPLY32, 0, hd->n * 20.0, k_apply_dot4, zgrid(dq), kBlock, hd->z32, hd->q32,
+             l0.bx32, l0.by32, l0.bz32, l0.d, zper_of(dq), hd->partial);
+      CKS(reduce(hd, zblocks(dq), OP_STORE, S_TMP));
+    } else {
+      LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, p, hd->q,
+             l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial);
+      CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_TMP));
+    }
     LAUNCH(hd, K_DOT64, 0, hd->n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, p, hd->b, hd->n,
            hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RZ));
