@@ -440,3 +440,22 @@ def test_precision_switch_after_geometry():
         p, it, _ = s.solve(rhs)
         assert it == results[prec][1] and torch.equal(p, results[prec][0]), prec
         s.close()
+
+
+@pytest.mark.parametrize("rho_g", [1e-5, 10.0])
+def test_mixed_extreme_density_ratios(rho_g):
+    """The FP16 face copies of the FP32 V-cycle are scaled by a power of two
+    set from 1/min(rho): at density ratio 1e5 (faces up to 1e5) and with the
+    gas heavier than the liquid (faces down to 0.1) the mixed solve still
+    reaches 1e-10 and agrees with the FP64 one."""
+    phi, u, prm = case("bubble32")
+    prm = dict(prm, rho_g=rho_g)
+    rhs = dev(oracle.divergence(*u, prm["h"]))
+    out = {}
+    for prec in (0, 1):
+        s = make(phi, prm, precision=prec, max_iters=400)
+        p, it, _ = s.solve(rhs, tol=TOL)
+        assert s.stats()["relres"] <= TOL
+        out[prec] = host(p)
+        s.close()
+    assert rel_l2(out[1], out[0]) < 1e-7
