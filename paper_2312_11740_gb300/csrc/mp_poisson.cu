@@ -56,6 +56,7 @@ const char *const kKernelNames[K_COUNT] = {
   "sub_mean", "reduce", "assemble", "assemble_u", "project", "divergence", "scale",
   "deflation"};
 constexpr int MAX_LEVELS = 16;
+constexpr int TAIL32_NU_MAX = 4;  // sweeps per level in the one-CTA FP32 tail
 constexpr int EVENT_POOL = 4096;
 
 struct ProfEntry {
@@ -335,10 +336,15 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
     a.Minv = hd->Minv;
     double bytes = 0.0;
     int off = 0;
+    // the FP32 tail (levels <= 16^3, latency-bound at about a microsecond per
+    // half-sweep) caps its sweeps at TAIL32_NU_MAX: measured, the deflated mixed
+    // solve needs no more there (FP64 keeps the level's sweeps; the same cap
+    // cost it iterations)
+    const int cap = sizeof(T) == 4 ? TAIL32_NU_MAX : 1 << 20;
     for (int q = 0; q < a.nlev; ++q) {
       Level &t = hd->L[l + q];
-      a.lv[q] = TailLevel{t.d, (int)t.n, t.nu1, t.nu2, off, LV<T>::bx(t), LV<T>::by(t),
-                          LV<T>::bz(t), LV<T>::idiag(t)};
+      a.lv[q] = TailLevel{t.d, (int)t.n, std::min(t.nu1, cap), std::min(t.nu2, cap), off,
+                          LV<T>::bx(t), LV<T>::by(t), LV<T>::bz(t), LV<T>::idiag(t)};
       off += 6 * (int)t.n;
       bytes += 4.0 * t.n * sizeof(T);
     }
