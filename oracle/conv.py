@@ -220,3 +220,114 @@ def adam(param, grad, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1.0 - b1 ** step)
     vh = v / (1.0 - b2 ** step)
     return param - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ------------------------------------------- learned guess on a coarser grid
+def restrict8(a):
+    """Grid half as fine in every axis: each coarse cell takes the mean of its
+    8 children (2 x 2 x 2 blocks of the fine grid), arrays (nz, ny, nx)."""
+    a = np.asarray(a, dtype=np.float64)
+    nz, ny, nx = a.shape
+    return a.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).mean(axis=(1, 3, 5))
+
+
+def features(phi, b, h):
+    """The two network input channels on a grid of cell size h:
+    f0 = clip(phi / (4h), -1, 1) (the level set in units of 4 cells, cut off
+    away from the interface) and f1 = b / rms(b) (rms 1; b = 0 gives 0).
+    Returns (f0, f1), each (nz, ny, nx) float64."""
+    phi = np.asarray(phi, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    f0 = np.clip(phi / (4.0 * h), -1.0, 1.0)
+    rms = np.sqrt(np.mean(b * b))
+    f1 = b / rms if rms > 0.0 else b.copy()
+    return f0, f1
+
+
+def half_res_features(phi, b, h):
+    """Input of a network whose grid is half as fine as the solver's (cell
+    size 2h): the features of the child means of phi and of b."""
+    return features(restrict8(phi), restrict8(b), 2.0 * h)
+
+
+def _interp_matrix(n, periodic):
+    """(2n, n) matrix of linear interpolation from n cell centres to the 2n
+    cell centres of the grid twice as fine along one axis.  Fine centre f sits
+    at coarse coordinate x = (f + 1/2)/2 - 1/2 (coarse centres at integers);
+    it takes (1 - w) of coarse cell floor(x) and w of floor(x) + 1, w = x -
+    floor(x).  Out-of-range coarse cells wrap on a periodic axis and are
+    replaced by the nearest end cell on a wall axis."""
+    P = np.zeros((2 * n, n))
+    for f in range(2 * n):
+        x = (f + 0.5) / 2.0 - 0.5
+        lo = int(np.floor(x))
+        w = x - lo
+        for idx, wt in ((lo, 1.0 - w), (lo + 1, w)):
+            idx = idx % n if periodic else min(max(idx, 0), n - 1)
+            P[f, idx] += wt
+    return P
+
+
+def prolong_trilinear2(q, periodic):
+    """Cell-centred trilinear interpolation of q (nz, ny, nx) onto the grid
+    twice as fine: the 1-D interpolation of _interp_matrix applied along
+    x, y and z in turn.  periodic = (x, y, z) booleans."""
+    out = np.asarray(q, dtype=np.float64)
+    for ax_np, per in ((2, periodic[0]), (1, periodic[1]), (0, periodic[2])):
+        P = _interp_matrix(out.shape[ax_np], per)
+        out = np.moveaxis(np.tensordot(P, out, axes=([1], [ax_np])), 0, ax_np)
+    return out
+
+
+def prolong_trilinear2_adjoint(g, periodic):
+    """Adjoint of prolong_trilinear2, written as a scatter: every fine value
+    g[f] is distributed to the coarse cells it was interpolated from, with the
+    same weights (one axis at a time)."""
+    out = np.asarray(g, dtype=np.float64)
+    for ax_np, per in ((2, periodic[0]), (1, periodic[1]), (0, periodic[2])):
+        m = np.moveaxis(out, ax_np, 0)
+        n = m.shape[0] // 2
+        acc = np.zeros((n,) + m.shape[1:])
+        for f in range(2 * n):
+            x = (f + 0.5) / 2.0 - 0.5
+            lo = int(np.floor(x))
+            w = x - lo
+            for idx, wt in ((lo, 1.0 - w), (lo + 1, w)):
+                idx = idx % n if per else min(max(idx, 0), n - 1)
+                acc[idx] += wt * m[f]
+        out = np.moveaxis(acc, 0, ax_np)
+    return out
+
+
+# ------------------------------------------------------- energy-norm loss
+def energy_loss(q, t, f0, rho_l, rho_g, bc):
+    """Energy-norm training loss of a predicted pressure shape q for the
+    target t, and its gradient with respect to q.
+
+    A is the positive semidefinite ghost-fluid operator, minus the C oracle's
+    operator, with the face coefficients that the oracle builds from the
+    level set f0 (the network's input channel phi / 4h: the interface
+    fraction theta = |f0_a| / (|f0_a| + |f0_b|) does not depend on the scale
+    of phi, and the scale of A cancels in the loss).  With a = q.At,
+    c = q.Aq, d = t.At:
+
+        L = 1 - a^2 / (c d),
+
+    the squared A-norm error of the best multiple alpha q (alpha = a / c),
+    relative to the A-norm of t.  A is symmetric, so
+
+        dL/dq = -2 a At / (c d) + 2 a^2 Aq / (c^2 d).
+
+    Returns (L, dL/dq)."""
+    from . import apply, faces
+    q = np.asarray(q, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    f = faces(np.asarray(f0, dtype=np.float64), rho_l, rho_g, bc)
+    Aq = -apply(f, q, 1.0, bc)
+    At = -apply(f, t, 1.0, bc)
+    a = float(np.sum(q * At))
+    c = float(np.sum(q * Aq))
+    d = float(np.sum(t * At))
+    L = 1.0 - a * a / (c * d)
+    grad = -2.0 * a * At / (c * d) + 2.0 * a * a * Aq / (c * c * d)
+    return L, grad

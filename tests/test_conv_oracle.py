@@ -125,3 +125,165 @@ def test_gauge_mse_and_adam():
     p, m, v = conv.adam(np.array([1.0]), np.array([0.5]), np.zeros(1), np.zeros(1), 1, lr=0.1)
     # first bias-corrected step moves by lr * sign(grad)
     assert p[0] == pytest.approx(0.9, rel=1e-6)
+
+
+# ------------------------------------------- learned guess on a coarser grid
+def test_restrict8_matches_uniform_filter():
+    """Mean of the 8 children = scipy's 2-wide box mean sampled at the odd
+    cells (an independent library routine)."""
+    a = rng(11).standard_normal((6, 8, 10))
+    ref = scipy_ndimage.uniform_filter(a, size=2, mode="constant")[1::2, 1::2, 1::2]
+    assert np.allclose(conv.restrict8(a), ref, rtol=0, atol=1e-14)
+
+
+def test_features_closed_form():
+    """A linear level set restricts exactly to its value at the coarse
+    centres; f0 is that value over 4 coarse cells, clipped to [-1, 1]; f1 has
+    rms 1, keeps the sign of b and ignores its scale."""
+    n, h = 16, 1.0 / 16
+    c = (np.arange(n) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    phi = 0.3 * x - 0.2 * y + 0.9 * z - 0.41
+    b = rng(12).standard_normal((n, n, n))
+    f0, f1 = conv.half_res_features(phi, b, h)
+    H = 2.0 * h
+    cc = (np.arange(n // 2) + 0.5) * H
+    Z, Y, X = np.meshgrid(cc, cc, cc, indexing="ij")
+    phic = 0.3 * X - 0.2 * Y + 0.9 * Z - 0.41
+    assert np.allclose(f0, np.clip(phic / (4 * H), -1, 1), rtol=0, atol=1e-14)
+    assert 0 < np.mean(np.abs(f0) == 1.0) < 1  # both clipped and unclipped cells
+    assert np.sqrt(np.mean(f1 * f1)) == pytest.approx(1.0, rel=1e-14)
+    g0, g1 = conv.half_res_features(phi, -7.5 * b, h)
+    assert np.allclose(g1, -f1, rtol=0, atol=1e-14) and np.array_equal(g0, f0)
+    assert np.all(conv.features(phi, np.zeros_like(b), h)[1] == 0)
+
+
+@pytest.mark.parametrize("per", [(True, True, False), (False, False, False), (True, True, True),
+                                 (False, True, False)])
+def test_prolongation_matches_scipy_zoom(per):
+    """Cell-centred linear interpolation onto the grid twice as fine is
+    scipy's order-1 zoom with grid-aligned cells, wrapping periodic axes and
+    repeating the end cell of wall axes; axes taken one at a time."""
+    q = rng(13).standard_normal((4, 6, 8))
+    ref = q
+    for ax_np, p in ((2, per[0]), (1, per[1]), (0, per[2])):
+        zf = [1, 1, 1]
+        zf[ax_np] = 2
+        ref = scipy_ndimage.zoom(ref, zf, order=1, grid_mode=True,
+                                 mode="grid-wrap" if p else "nearest")
+    out = conv.prolong_trilinear2(q, per)
+    assert out.shape == (8, 12, 16)
+    assert np.allclose(out, ref, rtol=0, atol=1e-13)
+
+
+def test_prolongation_exact_on_linear_fields_and_constants():
+    """Away from wall ends the interpolation reproduces any linear field at
+    the fine centres; every row's weights sum to 1 (constants are kept)."""
+    n, H = 8, 1.0 / 8
+    c = (np.arange(n) + 0.5) * H
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    q = 1.5 * X - 0.25 * Y + 2.0 * Z + 0.125
+    out = conv.prolong_trilinear2(q, (False, False, False))
+    f = (np.arange(2 * n) + 0.5) * (H / 2)
+    z, y, x = np.meshgrid(f, f, f, indexing="ij")
+    exact = 1.5 * x - 0.25 * y + 2.0 * z + 0.125
+    inner = (slice(1, -1),) * 3
+    assert np.allclose(out[inner], exact[inner], rtol=0, atol=1e-13)
+    assert np.allclose(conv.prolong_trilinear2(np.full((4, 4, 4), 2.5), (True, False, True)), 2.5,
+                       rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("per", [(True, True, False), (False, False, False)])
+def test_prolongation_adjoint_identity(per):
+    g = rng(14)
+    q = g.standard_normal((4, 6, 8))
+    v = g.standard_normal((8, 12, 16))
+    lhs = np.sum(conv.prolong_trilinear2(q, per) * v)
+    assert lhs == pytest.approx(np.sum(q * conv.prolong_trilinear2_adjoint(v, per)), rel=1e-12)
+
+
+def _energy_case(seed, n=8, bc=(0, 0, 1)):
+    import synth
+    h = 1.0 / n
+    phi = synth.level_set((n, n, n), h, [((0.5, 0.45, 0.4), 0.27)], pool_z0=0.8, bc=bc)
+    f0 = np.clip(phi / (4 * h), -1, 1)
+    g = rng(seed)
+    return g.standard_normal((n, n, n)), g.standard_normal((n, n, n)), f0, bc
+
+
+def test_energy_loss_invariants():
+    """0 <= L <= 1 (A is positive semidefinite); L = 0 when q is a multiple
+    of t; L does not change when q is scaled (by either sign), so the
+    gradient is orthogonal to q; L is unchanged when a constant is added
+    (constants are the operator's null space with periodic and wall axes)."""
+    q, t, f0, bc = _energy_case(15)
+    L, gq = conv.energy_loss(q, t, f0, 1.0, 1e-3, bc)
+    assert 0.0 < L < 1.0
+    for lam in (3.0, -0.5):
+        L2, g2 = conv.energy_loss(lam * q, t, f0, 1.0, 1e-3, bc)
+        assert L2 == pytest.approx(L, rel=1e-12)
+        assert np.allclose(lam * g2, gq, rtol=1e-10, atol=1e-14 * np.abs(gq).max())
+    assert abs(np.sum(gq * q)) <= 1e-12 * np.linalg.norm(gq) * np.linalg.norm(q)
+    assert conv.energy_loss(q + 4.0, t, f0, 1.0, 1e-3, bc)[0] == pytest.approx(L, rel=1e-10)
+    L0, g0 = conv.energy_loss(-2.0 * t, t, f0, 1.0, 1e-3, bc)
+    assert abs(L0) < 1e-14 and np.abs(g0).max() < 1e-12 * np.abs(gq).max() * 1e3
+
+
+def test_energy_loss_is_best_multiple_error():
+    """L is the squared A-norm error of the best multiple of q relative to
+    the A-norm of t: the quadratic N(alpha) = |alpha q - t|_A^2, fitted
+    through three values, has minimum L * |t|_A^2.  |x|_A^2 here comes from a
+    dense matrix assembled column by column from the oracle's operator."""
+    import oracle
+    q, t, f0, bc = _energy_case(16, n=6)
+    n = q.size
+    f = oracle.faces(f0, 1.0, 1e-3, bc)
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = -oracle.apply(f, e.reshape(q.shape), 1.0, bc).ravel()
+
+    def N(alpha):
+        e = (alpha * q - t).ravel()
+        return e @ A @ e
+
+    fit = np.polyfit([-1.0, 0.0, 1.0], [N(-1.0), N(0.0), N(1.0)], 2)
+    nmin = fit[2] - fit[1] ** 2 / (4.0 * fit[0])
+    L, _ = conv.energy_loss(q, t, f0, 1.0, 1e-3, bc)
+    assert L == pytest.approx(nmin / N(0.0), rel=1e-10)
+
+
+def test_energy_gradient_finite_difference():
+    """Central differences of L along random directions and single entries;
+    q is t plus noise so that L sits well inside (0, 1) and its derivatives
+    stand clear of the rounding of L itself."""
+    q, t, f0, bc = _energy_case(17)
+    q = t + 0.5 * q
+    L, gq = conv.energy_loss(q, t, f0, 1.0, 1e-3, bc)
+    assert 0.05 < L < 0.95
+    eps = 1e-5
+    g = rng(18)
+    for _ in range(3):
+        d = g.standard_normal(q.shape)
+        fd = (conv.energy_loss(q + eps * d, t, f0, 1.0, 1e-3, bc)[0] -
+              conv.energy_loss(q - eps * d, t, f0, 1.0, 1e-3, bc)[0]) / (2 * eps)
+        assert fd == pytest.approx(np.sum(gq * d), rel=1e-6)
+    for idx in [(0, 0, 0), (3, 4, 5), (7, 7, 7)]:
+        e = np.zeros_like(q)
+        e[idx] = eps
+        fd = (conv.energy_loss(q + e, t, f0, 1.0, 1e-3, bc)[0] -
+              conv.energy_loss(q - e, t, f0, 1.0, 1e-3, bc)[0]) / (2 * eps)
+        assert fd == pytest.approx(gq[idx], rel=1e-5, abs=1e-9)
+
+
+def test_adam_two_steps_closed_form():
+    """Two bias-corrected Adam steps written out for scalars: after the
+    first, m = 0.1 g1, v = 0.001 g1^2; the second combines both gradients."""
+    p0, g1, g2, lr = 0.7, 0.3, -0.05, 0.01
+    p1, m1, v1 = conv.adam(np.array([p0]), np.array([g1]), np.zeros(1), np.zeros(1), 1, lr=lr)
+    p2, _, _ = conv.adam(p1, np.array([g2]), m1, v1, 2, lr=lr)
+    mhat = (0.9 * 0.1 * g1 + 0.1 * g2) / (1 - 0.81)
+    vhat = (0.999 * 0.001 * g1 * g1 + 0.001 * g2 * g2) / (1 - 0.999 ** 2)
+    assert p1[0] == pytest.approx(p0 - lr * g1 / (abs(g1) + 1e-8), rel=1e-14)
+    assert p2[0] == pytest.approx(p1[0] - lr * mhat / (np.sqrt(vhat) + 1e-8), rel=1e-14)
