@@ -35,6 +35,9 @@ extern "C" {
 typedef struct mp_net *mp_net_handle;
 
 /*
+ * Defines: no paper passage (the paper has no learned component); the 3x3x3 convolution
+ * layer of the learned initial guess for Grid_solvePoisson (Section 3).
+ *
  * Single 3x3x3 convolution (zero padding), for tests and building blocks.
  * y[v, co] = bias[co] + sum_{t, ci} x[v + off_t, ci] w[co, t, ci], ReLU if
  * relu != 0.  The input is the channel concatenation of xa (ca channels,
@@ -50,6 +53,9 @@ mp_status mp_conv3d_fwd(int nx, int ny, int nz, const void *xa, int ca, int up_a
                         float *y32, void *stream);
 
 /*
+ * Defines: no paper passage (the paper has no learned component); the weight gradient
+ * of the convolution, for training the network on the GPU.
+ *
  * Weight gradient of mp_conv3d_fwd: dw[co, t, ci] = sum_v x[v + off_t, ci] g[v, co],
  * x as in mp_conv3d_fwd (concatenation of xa/xb), g (BF16, cout channels).
  * dw: FP32 [cout][27][ca+cb], overwritten.  Deterministic (fixed-order
@@ -59,27 +65,34 @@ mp_status mp_conv3d_wgrad(int nx, int ny, int nz, const void *xa, int ca, int up
                           const void *xb, int cb, const void *g, int cout, float *dw,
                           void *stream);
 
-/* Create a network for an nx x ny x nz grid (multiples of 32).  All device
+/* Defines: no paper passage (the paper has no learned component); the 4-level U-Net.
+ * Create a network for an nx x ny x nz grid (multiples of 32).  All device
  * memory it needs is allocated here.  Parameters start at zero: set them
  * with mp_net_set_params (the caller draws the initial values). */
 mp_status mp_net_create(mp_net_handle *out, int nx, int ny, int nz, void *stream);
 
-/* Grid of the network. */
+/* Defines: no paper passage (the paper has no learned component); handle query.
+ * Grid of the network. */
 mp_status mp_net_dims(mp_net_handle net, int *nx, int *ny, int *nz);
 
-/* Number of FP32 parameters (all conv weights and biases, then the head). */
+/* Defines: no paper passage (the paper has no learned component); handle query.
+ * Number of FP32 parameters (all conv weights and biases, then the head). */
 size_t mp_net_param_count(mp_net_handle net);
 
-/* Kernels the network has launched on inference paths (features, forward,
+/* Defines: no paper passage (the paper has no learned component); measurement.
+ * Kernels the network has launched on inference paths (features, forward,
  * pressure) since creation. */
 unsigned long long mp_net_launches(mp_net_handle net);
 
-/* Copy the FP32 master parameters in or out (device pointers, param_count
+/* Defines: no paper passage (the paper has no learned component); parameter transfer.
+ * Copy the FP32 master parameters in or out (device pointers, param_count
  * floats); setting them also refreshes the BF16 copies the kernels use. */
 mp_status mp_net_set_params(mp_net_handle net, const float *params_dev);
 mp_status mp_net_get_params(mp_net_handle net, float *params_dev);
 
-/* Input features from phi (FP64) and the mean-free right-hand side b
+/* Defines: no paper passage (the paper has no learned component); the network input,
+ * the level set phi (Section 2, Fig. 2 caption sign) and the right-hand side.
+ * Input features from phi (FP64) and the mean-free right-hand side b
  * (FP64) with bt = b_scale * b the h^2-scaled one (b_scale = h^2 for the
  * unscaled b of mp_poisson_rhs, 1 for the solver's scaled b): writes the
  * network input (16-channel BF16, internal buffer) and returns
@@ -87,29 +100,37 @@ mp_status mp_net_get_params(mp_net_handle net, float *params_dev);
 mp_status mp_net_features(mp_net_handle net, const double *phi_dev, const double *b_dev, double h,
                           double b_scale, double *s_out);
 
-/* mp_net_features for fields on a grid `factor` (1 or 2) times finer than the
+/* Defines: no paper passage (the paper has no learned component); the input of a network
+ * run on a grid half as fine as the solver's.
+ * mp_net_features for fields on a grid `factor` (1 or 2) times finer than the
  * network's in every dimension (phi, b: device FP64 on that grid; h its cell
  * size): with factor 2 the features are formed from the means of the 8
  * children of every network cell (cell size 2h). */
 mp_status mp_net_features_at(mp_net_handle net, int factor, const double *phi_dev,
                              const double *b_dev, double h, double b_scale, double *s_out);
 
-/* mp_net_pressure onto a grid `factor` (1 or 2) times finer: with factor 2,
+/* Defines: no paper passage (the paper has no learned component); the initial guess
+ * interpolated from the network's grid onto the solver's.
+ * mp_net_pressure onto a grid `factor` (1 or 2) times finer: with factor 2,
  * p = s (q - mean q) interpolated trilinearly (cell-centred weights 3/4 and
  * 1/4 per axis; periodic axes wrap, wall axes clamp). p_dev: device FP64 on
  * the fine grid. */
 mp_status mp_net_pressure_at(mp_net_handle net, int factor, const mp_bc bc[3], double s,
                              double *p_dev);
 
-/* The two used input channels (f0, f1) as a compact BF16 array (N*2), out
+/* Defines: no paper passage (the paper has no learned component); input transfer.
+ * The two used input channels (f0, f1) as a compact BF16 array (N*2), out
  * of or into the network input; set_input2 zero-fills the other 14. */
 mp_status mp_net_get_input2(mp_net_handle net, void *x2_dev);
 mp_status mp_net_set_input2(mp_net_handle net, const void *x2_dev);
 
-/* Forward pass on the current input features; q_dev: FP32 output (N). */
+/* Defines: no paper passage (the paper has no learned component); inference.
+ * Forward pass on the current input features; q_dev: FP32 output (N). */
 mp_status mp_net_forward(mp_net_handle net, float *q_dev);
 
-/* One training step on (features already set by mp_net_features or
+/* Defines: no paper passage (the paper has no learned component); training on the GPU
+ * on solutions the plain solver produces.
+ * One training step on (features already set by mp_net_features or
  * mp_net_set_input, target q_target_dev FP32 N): forward, gauge-free MSE
  * loss, backward through every layer, Adam (lr, beta1 0.9, beta2 0.999,
  * eps 1e-8, bias correction with step >= 1).  loss_out (host) gets the
@@ -118,6 +139,10 @@ mp_status mp_net_train_step(mp_net_handle net, const float *q_target_dev, float 
                             double *loss_out);
 
 /*
+ * Defines: no paper passage (the paper has no learned component); the training loss;
+ * the energy norm uses the ghost-fluid operator of the solve (varDens,
+ * Section 3).
+ *
  * Loss of mp_net_train_step.  kind 0: gauge-free mean squared error against
  * the target (default).  kind 1: energy norm,
  *   L = 1 - (q.A t)^2 / ((q.A q)(t.A t)),
@@ -131,27 +156,49 @@ mp_status mp_net_train_step(mp_net_handle net, const float *q_target_dev, float 
 mp_status mp_net_set_loss(mp_net_handle net, int kind, double rho_l, double rho_g,
                           const mp_bc bc[3]);
 
-/* Set the 16-channel BF16 input directly (device pointer, N*16 bf16). */
+/* Defines: no paper passage (the paper has no learned component); the loss gradient
+ * that training feeds to the backward pass.
+ * Forward pass on the current input and the loss of mp_net_train_step
+ * (mp_net_set_loss) against q_target_dev (FP32, N) with its gradient with
+ * respect to the network output q, without the backward pass or an update:
+ * gq_dev (device FP32 N, may be NULL) gets dL/dq, loss_out (host, may be
+ * NULL) the loss.  The gradient is the one mp_net_train_step feeds to the
+ * backward pass, for tests and for callers who form their own updates. */
+mp_status mp_net_loss_grad(mp_net_handle net, const float *q_target_dev, float *gq_dev,
+                           double *loss_out);
+
+/* Defines: no paper passage (the paper has no learned component); input transfer.
+ * Set the 16-channel BF16 input directly (device pointer, N*16 bf16). */
 mp_status mp_net_set_input(mp_net_handle net, const void *x16_dev);
 
-/* Gradients of sum(q * gq) w.r.t. all parameters for the current input
+/* Defines: no paper passage (the paper has no learned component); the backward pass.
+ * Gradients of sum(q * gq) w.r.t. all parameters for the current input
  * (no update): grad_dev gets param_count floats.  For tests. */
 mp_status mp_net_backward(mp_net_handle net, const float *gq_dev, float *grad_dev);
 
-/* Pressure shape from the last forward pass: p = s (q - mean q) (device,
+/* Defines: no paper passage (the paper has no learned component); the initial guess on
+ * the network's own grid.
+ * Pressure shape from the last forward pass: p = s (q - mean q) (device,
  * N f64). */
 mp_status mp_net_pressure(mp_net_handle net, double s, double *p_dev);
 
-/* Training target from a pressure field: q = (p - mean p) / rms(p - mean p)
+/* Defines: no paper passage (the paper has no learned component); the training target
+ * from a pressure the plain solver produced.
+ * Training target from a pressure field: q = (p - mean p) / rms(p - mean p)
  * (p: device N f64; q: device N f32). */
 mp_status mp_net_make_target(mp_net_handle net, const double *p_dev, float *q_dev);
 
-/* Stream for the network's work (cudaStream_t; NULL = legacy default). */
+/* Defines: no paper passage (the paper has no learned component); configuration.
+ * Stream for the network's work (cudaStream_t; NULL = legacy default). */
 mp_status mp_net_set_stream(mp_net_handle net, void *stream);
 
+/* Defines: no paper passage (the paper has no learned component); resource release. */
 void mp_net_destroy(mp_net_handle net);
 
-/* Use `net` (or NULL to detach) for initial_guess = 2 in mp_poisson_solve.
+/* Defines: no paper passage (the paper has no learned component); the learned initial
+ * guess of the multigrid solve (Grid_solvePoisson, Section 3), with the
+ * residual check that falls back to the zero guess.
+ * Use `net` (or NULL to detach) for initial_guess = 2 in mp_poisson_solve.
  * The network grid equals the solver grid, or is half of it in every
  * dimension (the guess is then formed on the coarser grid from restricted
  * features and interpolated, see mp_net_features_at / mp_net_pressure_at).

@@ -114,6 +114,7 @@ SIGNATURES = {
     "mp_net_set_input2": (_I, [_P, _P]),
     "mp_net_forward": (_I, [_P, _P]),
     "mp_net_train_step": (_I, [_P, _P, ctypes.c_float, _I, _DP]),
+    "mp_net_loss_grad": (_I, [_P, _P, _P, _DP]),
     "mp_net_set_input": (_I, [_P, _P]),
     "mp_net_backward": (_I, [_P, _P, _P]),
     "mp_net_pressure": (_I, [_P, _D, _P]),

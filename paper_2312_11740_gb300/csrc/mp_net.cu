@@ -1386,6 +1386,33 @@ mp_status backward(mp_net *net) {
   return MP_OK;
 }
 
+// Loss of the last forward pass against target and its gradient w.r.t. q
+// into net->gq; the loss value lands in net->dscal[2] (MSE: the sum of
+// squared errors, divided by n on the host).
+mp_status loss_and_grad(mp_net *net, const float *target) {
+  const size_t n = net->nv[0];
+  // means of prediction and target, then loss and its gradient
+  k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, n, 0, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
+  k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(target, n, 0, net->dpart);
+  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 1);
+  if (net->loss_kind == 0) {
+    k_loss<<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, target, n, net->dscal, net->gq,
+                                                   net->dpart);
+    k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 2);
+  } else {
+    k_energy_apply<<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, target, net->in16, net->eg, n,
+                                                           net->e_aq, net->e_at, net->dpart);
+    for (int q = 0; q < 3; ++q)
+      k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart + q * RED_BLOCKS, RED_BLOCKS,
+                                               net->dscal + 8 + q);
+    k_energy_grad<<<grid_for(n), 256, 0, net->st>>>(net->e_aq, net->e_at, n, net->dscal + 8,
+                                                    net->gq, net->dscal + 2);
+  }
+  NCK(cudaGetLastError());
+  return MP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1718,29 +1745,28 @@ mp_status mp_net_backward(mp_net_handle net, const float *gq, float *grad_dev) {
   return check_err(net);
 }
 
+mp_status mp_net_loss_grad(mp_net_handle net, const float *target, float *gq_dev,
+                           double *loss_out) {
+  if (!net || !target) return MP_ERR_INVALID_ARG;
+  NCKS(forward(net));
+  NCKS(loss_and_grad(net, target));
+  if (gq_dev)
+    NCK(cudaMemcpyAsync(gq_dev, net->gq, net->nv[0] * sizeof(float), cudaMemcpyDeviceToDevice,
+                        net->st));
+  NCK(cudaMemcpyAsync(net->hscal, net->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                      net->st));
+  NCKS(check_err(net));
+  if (loss_out)
+    *loss_out = net->loss_kind == 0 ? net->hscal[0] / (double)net->nv[0] : net->hscal[0];
+  return MP_OK;
+}
+
 mp_status mp_net_train_step(mp_net_handle net, const float *target, float lr, int step,
                             double *loss_out) {
   if (!net || !target || step < 1 || !(lr > 0.f)) return MP_ERR_INVALID_ARG;
   const size_t n = net->nv[0];
   NCKS(forward(net));
-  // means of prediction and target, then loss and its gradient
-  k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, n, 0, net->dpart);
-  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal);
-  k_psum<float><<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(target, n, 0, net->dpart);
-  k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 1);
-  if (net->loss_kind == 0) {
-    k_loss<<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, target, n, net->dscal, net->gq,
-                                                   net->dpart);
-    k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart, RED_BLOCKS, net->dscal + 2);
-  } else {
-    k_energy_apply<<<RED_BLOCKS, RED_THREADS, 0, net->st>>>(net->q, target, net->in16, net->eg, n,
-                                                           net->e_aq, net->e_at, net->dpart);
-    for (int q = 0; q < 3; ++q)
-      k_pfinal<<<1, RED_THREADS, 0, net->st>>>(net->dpart + q * RED_BLOCKS, RED_BLOCKS,
-                                               net->dscal + 8 + q);
-    k_energy_grad<<<grid_for(n), 256, 0, net->st>>>(net->e_aq, net->e_at, n, net->dscal + 8,
-                                                    net->gq, net->dscal + 2);
-  }
+  NCKS(loss_and_grad(net, target));
   NCKS(backward(net));
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);

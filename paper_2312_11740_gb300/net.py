@@ -164,6 +164,16 @@ class Net:
         _check(_lib_().mp_net_set_loss(self.handle, int(kind), float(rho_l), float(rho_g), arr),
                "mp_net_set_loss")
 
+    def loss_grad(self, target):
+        """Forward pass, the training loss against target and dL/dq (no
+        update); returns (loss, gq) with gq FP32 on the device."""
+        loss = ctypes.c_double(0.0)
+        gq = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        _check(_lib_().mp_net_loss_grad(self.handle, _ptr(target, torch.float32, self.n),
+                                        _ptr(gq, torch.float32), ctypes.byref(loss)),
+               "mp_net_loss_grad")
+        return loss.value, gq
+
     def train_step(self, target, lr, step):
         loss = ctypes.c_double(0.0)
         _check(_lib_().mp_net_train_step(self.handle, _ptr(target, torch.float32, self.n),
