@@ -107,10 +107,21 @@ typedef struct {
 
 typedef struct mp_poisson *mp_handle;
 
-/* Fill *opts with the defaults documented in mp_opts. */
+/* Fill *opts with the defaults documented in mp_opts.
+ * Defines: the options of the multigrid Poisson solve (Grid_solvePoisson,
+ * Section 3); the paper gives no solver settings, each default is a stated,
+ * measured choice. */
 void mp_opts_default(mp_opts *opts);
 
 /*
+ * Defines: the variable-density pressure problem of the fractional-step
+ * projection on the staggered grid (Section 2, Fig. 2 caption: phi > 0 in
+ * air/gas), with the properties of each cell taken from phi (varDens and
+ * MultiphaseMain, Section 3) through ghost-fluid face coefficients and the
+ * surface-tension jump [p] = sigma*kappa (published ghost-fluid method,
+ * Liu-Fedkiw-Kang 2000), and the multigrid hierarchy of Grid_solvePoisson
+ * (Section 3).
+ *
  * Allocate a solver for grid g (cell edge h > 0, boundary bc[axis] per axis)
  * and set its geometry from phi_dev (device, nx*ny*nz f64, phi > 0 gas),
  * liquid density rho_l > 0, gas density rho_g > 0, surface tension sigma >= 0.
@@ -125,6 +136,9 @@ mp_status mp_poisson_setup(mp_handle *out, mp_grid g, double h, const mp_bc bc[3
                            const mp_opts *opts);
 
 /*
+ * Defines: as mp_poisson_setup, for a level set that has moved (the level
+ * set is advected every step, MultiphaseMain, Section 3).
+ *
  * Recompute the geometry-dependent data (curvature, face coefficients, jump
  * source, coarse hierarchy, coarsest inverse) for a new phi on the same grid.
  * No allocation.
@@ -132,10 +146,14 @@ mp_status mp_poisson_setup(mp_handle *out, mp_grid g, double h, const mp_bc bc[3
 mp_status mp_poisson_set_geometry(mp_handle hd, const double *phi_dev, double rho_l, double rho_g,
                                   double sigma);
 
-/* Replace the options (stream, precision, method, ...). */
+/* Defines: no paper passage (solver configuration, see mp_opts).
+ * Replace the options (stream, precision, method, ...). */
 mp_status mp_poisson_set_opts(mp_handle hd, const mp_opts *opts);
 
 /*
+ * Defines: the pressure Poisson solve of the projection step
+ * (Grid_solvePoisson, Section 3; fractional-step projection, Section 2).
+ *
  * Solve A p = b with b = rhs + J - mean, to ||b - A p|| <= tol ||b||.
  * rhs_dev: device, N f64 (e.g. div u*).  p_dev: device, N f64, in/out
  * (read only if initial_guess = 1), mean-free on exit.  iterations (may be
@@ -150,6 +168,11 @@ mp_status mp_poisson_solve(mp_handle hd, const double *rhs_dev, double *p_dev, d
                            int *iterations, double *res_hist, int res_hist_cap, int *res_hist_len);
 
 /*
+ * Defines: the pressure-projection part of one step of the fractional-step
+ * method on the staggered grid (Section 2: velocities on faces, pressure at
+ * cell centres; the predicted velocity u* comes from IncompNS_predictor in
+ * the Driver_evolveAll listing, Section 3).
+ *
  * One projection step on device data: rhs = div_h u*, solve as
  * mp_poisson_solve, then correct the face velocities in place,
  * u = u* - beta (grad_h p - [p]).  ux/uy/uz_dev: device, N f64 each
@@ -159,6 +182,9 @@ mp_status mp_poisson_project_step(mp_handle hd, double *ux_dev, double *uy_dev, 
                                   double *p_dev, double tol, int *iterations);
 
 /*
+ * Defines: as mp_poisson_project_step (Section 2), for callers whose fields
+ * live in host memory.
+ *
  * The same step on HOST buffers: copies u* (3N f64) and, for
  * initial_guess = 1, p (N f64) to the device, runs mp_poisson_project_step
  * and copies the corrected velocities and p back.  Uses device staging
@@ -168,21 +194,36 @@ mp_status mp_poisson_project_step_host(mp_handle hd, double *ux_host, double *uy
                                        double *uz_host, double *p_host, double tol,
                                        int *iterations);
 
-/* y = A x (unscaled operator, device N f64 each). */
+/* Defines: the variable-coefficient operator div((1/rho) grad) on the
+ * staggered stencil (Section 2; varDens, Section 3), ghost-fluid faces.
+ * y = A x (unscaled operator, device N f64 each). */
 mp_status mp_poisson_apply(mp_handle hd, const double *x_dev, double *y_dev);
 
-/* div_dev = div_h u (device, N f64). */
+/* Defines: the cell-centred divergence of face velocities on the staggered
+ * grid (Section 2).
+ * div_dev = div_h u (device, N f64). */
 mp_status mp_poisson_divergence(mp_handle hd, const double *ux_dev, const double *uy_dev,
                                 const double *uz_dev, double *div_dev);
 
-/* b_dev = rhs + J - mean(rhs + J), the right-hand side the solve uses. */
+/* Defines: the right-hand side with the surface-tension jump source
+ * (reading: ghost-fluid method, Kang-Fedkiw-Liu 2000; [p] = sigma*kappa,
+ * sigma the paper's mph_invWeber, runtime-parameter TOML figure,
+ * Section 4), mean-projected for the singular
+ * periodic/wall problem.
+ * b_dev = rhs + J - mean(rhs + J), the right-hand side the solve uses. */
 mp_status mp_poisson_rhs(mp_handle hd, const double *rhs_dev, double *b_dev);
 
-/* u -= beta (grad_h p - [p]) on every face, in place. */
+/* Defines: the velocity correction of the fractional-step projection
+ * (Section 2), with the pressure jump removed from the gradient on faces
+ * that cross the interface (ghost-fluid reading).
+ * u -= beta (grad_h p - [p]) on every face, in place. */
 mp_status mp_poisson_project(mp_handle hd, const double *p_dev, double *ux_dev, double *uy_dev,
                              double *uz_dev);
 
-/* Copy setup fields out (device pointers, each N f64; any may be NULL):
+/* Defines: the fields derived from phi (curvature and fluid properties,
+ * MultiphaseMain and StencilsLevelSet, Section 3; jump source, ghost-fluid
+ * reading).
+ * Copy setup fields out (device pointers, each N f64; any may be NULL):
  * curvature kappa (evaluated in the interface band -- cells with a face
  * neighbour of the other fluid -- and 0 elsewhere), face coefficients
  * beta_x/y/z (low-face ownership, wall faces 0), jump source J (unscaled,
@@ -190,10 +231,14 @@ mp_status mp_poisson_project(mp_handle hd, const double *p_dev, double *ux_dev, 
 mp_status mp_poisson_get_fields(mp_handle hd, double *kappa_dev, double *bx_dev, double *by_dev,
                                 double *bz_dev, double *J_dev);
 
-/* Statistics of the last solve. */
+/* Defines: no paper passage (solver diagnostics).
+ * Statistics of the last solve. */
 mp_status mp_poisson_get_stats(mp_handle hd, mp_stats *st);
 
-/* Connected gas components of the current geometry (face neighbours, periodic
+/* Defines: no paper passage; the gas regions phi > 0 (Fig. 2 caption) split
+ * into connected components, the deflation vectors of the solve (reading:
+ * deflated CG for bubbly flows, Tang & Vuik).
+ * Connected gas components of the current geometry (face neighbours, periodic
  * axes wrapped): comp_dev (device, N int32, may be NULL) gets each cell's
  * component id (0..m-1 in the order of each component's lowest cell index,
  * -1 for liquid); m (host) gets the count.  m = 0 when deflation is off for
@@ -211,13 +256,17 @@ typedef struct {
 } mp_kernel_prof;
 
 /*
+ * Defines: no paper passage (measurement: per-kernel launch counts, event
+ * times and algorithmic bytes for the roofline).
+ *
  * Launch accounting.  Every kernel launch is counted per (kernel, level).
  * enable = 1 also brackets every launch with CUDA events on the handle's
  * stream (host-side cost ~1 us per launch).  Resets all counters.
  */
 mp_status mp_poisson_set_profiling(mp_handle hd, int enable);
 
-/* Copy up to cap records to out (host memory); *count (may be NULL) gets
+/* Defines: no paper passage (measurement, see mp_poisson_set_profiling).
+ * Copy up to cap records to out (host memory); *count (may be NULL) gets
  * the number of records available. */
 mp_status mp_poisson_get_profile(mp_handle hd, mp_kernel_prof *out, int cap, int *count);
 
@@ -230,7 +279,9 @@ mp_status mp_poisson_get_profile(mp_handle hd, mp_kernel_prof *out, int cap, int
  * cudaMalloc because it can block on or synchronise the device.  It needs
  * no handle: the caller passes ncells (number of cells), rhs_dev and J_dev
  * (device, ncells f64 each; J as returned by mp_poisson_get_fields) and
- * b_dev (device, ncells f64, output).
+ * b_dev (device, ncells f64, output).  The call works on the CURRENT device
+ * (its scratch and its launches): the three pointers must be memory of that
+ * device.
  *
  * Scratch: a fixed array of about 512 KB in device memory that every GPU
  * loading this library holds until the process exits; it bounds ncells to
@@ -249,10 +300,12 @@ mp_status mp_poisson_get_profile(mp_handle hd, mp_kernel_prof *out, int cap, int
 mp_status mp_poisson_rhs_noalloc(long long ncells, const double *rhs_dev, const double *J_dev,
                                  double *b_dev, void *stream);
 
-/* Free everything the handle owns.  NULL is ignored. */
+/* Defines: no paper passage (resource release).
+ * Free everything the handle owns.  NULL is ignored. */
 void mp_poisson_destroy(mp_handle hd);
 
-/* Static text for a status code. */
+/* Defines: no paper passage (error reporting).
+ * Static text for a status code. */
 const char *mp_status_str(mp_status s);
 
 #ifdef __cplusplus

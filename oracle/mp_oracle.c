@@ -56,7 +56,8 @@ static int is_gas(double phi) { return phi > 0.0; } /* phi = 0 counts as liquid 
  * |grad phi| floored at 1e-12, result clamped to |kappa| <= 1/h.
  * With phi > 0 in gas a spherical bubble of radius R has kappa = +2/R.
  * Surface tension enters through the jump [p] = sigma kappa (the paper's
- * mph_invWeber parameter, Fig. 14; MultiphaseMain, Section 3).
+ * mph_invWeber parameter of the runtime-parameter TOML figure, Section 4;
+ * MultiphaseMain, Section 3).
  */
 void oracle_curvature(int nx, int ny, int nz, double h, const int periodic[3],
                       const double *phi, double *kappa) {

@@ -126,11 +126,16 @@ def mp_poisson_rhs(handle, rhs, b):
 
 def mp_poisson_rhs_noalloc(rhs, J, b, stream=None):
     """b = rhs + J - mean(rhs + J) without any device allocation (enqueued on
-    `stream`; the call does not wait for the work)."""
+    `stream`; the call does not wait for the work).  The library uses the
+    current device's scratch and launches there, so the three tensors must
+    share one device, which is made current for the call."""
     n = rhs.numel()
-    return _check(_lib_().mp_poisson_rhs_noalloc(n, _ptr(rhs, numel=n), _ptr(J, numel=n),
-                                                 _ptr(b, numel=n), _stream_ptr(stream)),
-                  "mp_poisson_rhs_noalloc")
+    if not (rhs.device == J.device == b.device):
+        raise ValueError("rhs, J and b must be on one device")
+    with torch.cuda.device(rhs.device):
+        return _check(_lib_().mp_poisson_rhs_noalloc(n, _ptr(rhs, numel=n), _ptr(J, numel=n),
+                                                     _ptr(b, numel=n), _stream_ptr(stream)),
+                      "mp_poisson_rhs_noalloc")
 
 
 def mp_poisson_project(handle, p, ux, uy, uz):

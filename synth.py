@@ -24,7 +24,7 @@ NEUMANN = 1
 
 # Workload recipes (grid, geometry, fluid parameters) of the benchmark configs.
 # rho_g / rho_l = 0.001 is the paper's example gas/liquid density ratio
-# (Fig. 14 runtime parameters, mph_rhoGas); sigma is the surface tension.
+# (the runtime-parameter TOML figure of Section 4, mph_rhoGas); sigma is the surface tension.
 WORKLOADS = {
     "bubble32": dict(n=32, bubbles=[((0.5, 0.5, 0.4), 0.25)], pool_z0=None,
                      rho_l=1.0, rho_g=1e-3, sigma=0.01, useed=1),
