@@ -355,13 +355,21 @@ def test_energy_loss_backward_matches_oracle():
     p = oracle_params_from_vector(vec)
     _, cache = conv.unet_forward(p, x[..., :2], rnd=bf16_round)
     gref, _ = conv.unet_backward(p, cache, gref_q, rnd=bf16_round)
-    rows, tot, head = _compare_param_grads(grad, gref)
+    rows, tot, _ = _compare_param_grads(grad, gref)
     for name, cos, err, berr in rows:
         assert cos > 0.9995, (name, cos)
         assert err < 3e-2, (name, err)
         assert berr < 3e-2, (name, berr)
     assert tot < 2e-2
-    assert head < 1e-2
+    # head weights: dL/dw_c = sum_v gq_v d0_v,c.  The energy gradient sums to
+    # zero over the grid (A annihilates constants) and d0 is nearly constant
+    # in the linear regime, so this sum is a small residue of cancelling
+    # terms: bound its error by the mass of the terms, sum_v |gq_v d0_v,c|,
+    # times the FP32/BF16 rounding the two sides differ by
+    off = sum(co * 27 * (16 if name == "e0a" else ci) + co for name, co, ci in conv.layer_shapes())
+    gh = grad[off:off + conv.CH[0]]
+    mass = np.abs(gref_q.reshape(-1, 1) * cache["d0"].reshape(-1, conv.CH[0])).sum(axis=0)
+    assert np.all(np.abs(gh - gref["head.w"].ravel()) <= 2e-3 * mass), (gh, gref["head.w"], mass)
 
 
 def test_two_adam_steps_match_oracle_adam():
