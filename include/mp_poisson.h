@@ -87,6 +87,10 @@ typedef struct {
                         connected gas components (phi > 0), removing the bubbles' pressure
                         levels, which the V-cycle resolves poorly at density ratio 1000;
                         0 = plain MG-preconditioned CG.  Same converged answer. */
+  int smoother;      /* FP32 V-cycle levels (mixed precision) with nx a multiple of 8:
+                        1 (default) = one fused pass per red-black sweep (both colours,
+                        shared-memory halo staging, second iterate buffer); 0 = one
+                        in-place launch per colour.  Bitwise the same result. */
   void *stream;      /* cudaStream_t; NULL = legacy default stream. */
 } mp_opts;
 

@@ -43,6 +43,7 @@ class mp_opts(ctypes.Structure):
         ("inner_max", ctypes.c_int),
         ("net_check", ctypes.c_int),
         ("deflate", ctypes.c_int),
+        ("smoother", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 

@@ -19,6 +19,7 @@
 #include "../../include/mp_net.h"
 #include "../../include/mp_poisson.h"
 #include "mp_kernels.cuh"
+#include "mp_sweep.cuh"
 #include "mp_deflate.cuh"
 
 using namespace mp;
@@ -37,18 +38,20 @@ struct Level {
   __half *bx16 = nullptr, *by16 = nullptr, *bz16 = nullptr;  // FP32 V-cycle faces, x fs16
   double *b = nullptr, *e = nullptr;   // coarse-level rhs / correction (levels >= 1)
   float *b32 = nullptr, *e32 = nullptr;
+  float *t32 = nullptr;  // second FP32 iterate of the fused sweep (levels it runs on)
+  int ftx = 0, fty = 0, fchunk = 0;  // fused sweep grid: tiles in x, y; z-chunks
 };
 
 enum KernelId {
   K_CURV, K_FACES, K_JUMP, K_DIAG, K_COARSEN, K_DENSE, K_GJ,
-  K_RBGS64, K_RBGS32, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
+  K_RBGS64, K_RBGS32, K_RBGS32F, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
   K_APPLY64, K_APPLY32, K_RESID64, K_RESID32, K_RESIDMIX, K_DOT64, K_DOT32, K_AXPY64, K_AXPY32,
   K_XPBY64, K_XPBY32, K_ADD64, K_ADD32, K_ADDF32, K_SUM, K_SUBMEAN, K_REDUCE, K_ASSEMBLE,
   K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_DEFL, K_COUNT
 };
 const char *const kKernelNames[K_COUNT] = {
   "curvature", "gfm_faces", "jump", "diag", "coarsen_faces", "dense_build", "gauss_jordan",
-  "rbgs_f64", "rbgs_f32", "coarse_tail_f64", "coarse_tail_f32",
+  "rbgs_f64", "rbgs_f32", "rbgs_f32_fused", "coarse_tail_f64", "coarse_tail_f32",
   "resid_restrict_f64", "resid_restrict_f32", "prolong_f64",
   "prolong_f32", "coarse_solve_f64", "coarse_solve_f32io", "apply_dot_f64", "apply_dot_f32",
   "residual_f64", "residual_f32", "residual_mixed", "dot_f64", "dot_f32", "axpy2_f64",
@@ -384,10 +387,38 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
                    colour, zero);
       return MP_OK;
     };
-    for (int s = 0; s < lv.nu1; ++s) {
-      CKS(sweep(0, s == 0));
-      CKS(sweep(1, 0));
-    }
+    // FP32 levels with a fused-sweep grid: one launch per sweep, ping-pong
+    // between x and t32 (pairs of sweeps end in x); an odd last sweep, and
+    // every sweep of the other levels, is one in-place launch per colour
+    const bool fused = sizeof(T) == 4 && hd->opts.smoother == 1 && lv.fchunk > 0;
+    auto fsweep = [&](const float *xin, float *xout, int c0, int zero) -> mp_status {
+      FusedArgs fa{xin, xout, (const float *)rhs, lv.bx16, lv.by16, lv.bz16, lv.d, c0, zero,
+                   hd->fs16, lv.ftx, lv.fty, lv.fchunk};
+      // x, b and three face arrays read, x written (x not read by a first sweep)
+      const double bytes = (zero ? 20.0 : 24.0) * nl;
+      if (zero)
+        LAUNCH_PDL(hd, K_RBGS32F, l, bytes, k_rbgs_fused<true>, lv.ftx * lv.fty * lv.fchunk,
+                   FS_THREADS, FS_SMEM, fa);
+      else
+        LAUNCH_PDL(hd, K_RBGS32F, l, bytes, k_rbgs_fused<false>, lv.ftx * lv.fty * lv.fchunk,
+                   FS_THREADS, FS_SMEM, fa);
+      return MP_OK;
+    };
+    auto smooth = [&](int nu, int c0, int first_zero) -> mp_status {
+      int s = 0;
+      if (fused) {
+        for (; s + 1 < nu; s += 2) {
+          CKS(fsweep((const float *)x, lv.t32, c0, first_zero && s == 0));
+          CKS(fsweep(lv.t32, (float *)x, c0, 0));
+        }
+      }
+      for (; s < nu; ++s) {
+        CKS(sweep(c0, first_zero && s == 0));
+        CKS(sweep(1 - c0, 0));
+      }
+      return MP_OK;
+    };
+    CKS(smooth(lv.nu1, 0, 1));
     if constexpr (sizeof(T) == 4) {
       if (lv.d.nx % 4 == 0)
         LAUNCH_PDL(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h4,
@@ -411,10 +442,7 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
     else
       LAUNCH_PDL(hd, kid<T>(K_PROL64, K_PROL32), l, 2.125 * nl * sz, k_prolong<T>,
                  cell_grid(lv.d), kBlock, 0, x, LV<T>::e(lc), lv.d, lc.d);
-    for (int s = 0; s < lv.nu2; ++s) {
-      CKS(sweep(1, 0));
-      CKS(sweep(0, 0));
-    }
+    CKS(smooth(lv.nu2, 1, 0));
   }
   return launch_ok();
 }
@@ -1042,7 +1070,7 @@ bool valid_opts(const mp_opts &o) {
          o.initial_guess >= 0 && o.initial_guess <= 2 && o.max_iters >= 0 && o.nu1 >= 1 &&
          o.nu2 >= 1 && o.nu_growth >= 1 && o.nu_max >= 1 && o.inner_rtol > 0.0 &&
          o.inner_rtol < 1.0 && o.inner_max >= 1 && (o.net_check == 0 || o.net_check == 1) &&
-         (o.deflate == 0 || o.deflate == 1);
+         (o.deflate == 0 || o.deflate == 1) && (o.smoother == 0 || o.smoother == 1);
 }
 
 void apply_nu(mp_poisson *hd) {
@@ -1115,6 +1143,42 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
   CKS(deflation_setup(hd));
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);
+  return MP_OK;
+}
+
+// Grid of the fused sweep for every FP32 level it runs on (levels above the
+// one-CTA tail, nx a multiple of 8), and the second iterate buffer.  The
+// z-chunk count minimises (waves of resident CTAs) x (planes per chunk +
+// the ~3.5 planes a chunk stages beyond its own).
+mp_status fused_setup(mp_poisson *hd) {
+  CK(cudaFuncSetAttribute(k_rbgs_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          FS_SMEM));
+  CK(cudaFuncSetAttribute(k_rbgs_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          FS_SMEM));
+  int dev = 0, sms = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_fused<false>, FS_THREADS,
+                                                   FS_SMEM));
+  const long slots = (long)std::max(1, sms) * std::max(1, per_sm);
+  for (int l = 0; l < hd->tail32 && l < (int)hd->L.size() - 1; ++l) {
+    Level &lv = hd->L[l];
+    if (lv.d.nx % 8 != 0) continue;
+    lv.ftx = (lv.d.nx + FS_TX - 1) / FS_TX;
+    lv.fty = (lv.d.ny + FS_TY - 1) / FS_TY;
+    const long tiles = (long)lv.ftx * lv.fty;
+    double best = 0.0;
+    for (int c = 1; c <= lv.d.nz; ++c) {
+      if (tiles * c > (1L << 30)) break;
+      const long waves = (tiles * c + slots - 1) / slots;
+      const double cost = (double)waves * ((lv.d.nz + c - 1) / c + 3.5);
+      if (lv.fchunk == 0 || cost < best - 1e-9) {
+        best = cost;
+        lv.fchunk = c;
+      }
+    }
+    CKS(dalloc(hd, &lv.t32, lv.n));
+  }
   return MP_OK;
 }
 
@@ -1243,6 +1307,8 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
       hd->tail32_bytes = bytes;
     }
   }
+  // fused FP32 sweep: levels above the one-CTA tail with nx a multiple of 8
+  CKS(fused_setup(hd));
   CK(cudaFuncSetAttribute(k_inverse_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)((GJ_SMEM_MAX + 1) * GJ_SMEM_MAX * sizeof(double))));
   CK(cudaFuncSetAttribute(k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1273,6 +1339,7 @@ void mp_opts_default(mp_opts *o) {
   o->inner_max = 12;
   o->net_check = 0;
   o->deflate = 1;
+  o->smoother = 1;
   o->stream = nullptr;
 }
 

@@ -459,3 +459,62 @@ def test_mixed_extreme_density_ratios(rho_g):
         out[prec] = host(p)
         s.close()
     assert rel_l2(out[1], out[0]) < 1e-7
+
+
+def _pool_case(n, seed=5):
+    """Pool + 16 bubbles on an n^3 grid (several fused-sweep z-chunks)."""
+    h = 1.0 / n
+    bub = synth.random_bubbles(seed, 16, 0.03, 0.08, n, pool_z0=0.6)
+    phi = synth.level_set((n, n, n), h, bub, pool_z0=0.6)
+    u = synth.velocity(seed, (n, n, n), h)
+    return phi, u, dict(h=h, rho_l=1.0, rho_g=1e-3, sigma=0.07, bc=(P, P, N))
+
+
+@pytest.mark.parametrize("name,opts", [("ragged", {}), ("walls", {}), ("periodic", {}),
+                                       ("bubble32", {"nu1": 3, "nu2": 3}),
+                                       ("pool128", {}),
+                                       ("pool128", {"deflate": 0, "method": 1, "max_iters": 20})])
+def test_fused_sweep_bitwise_equals_per_colour_launches(name, opts):
+    """The fused red-black pass (both colours in one z-marching launch) and
+    the two in-place launches per sweep update every cell with the same
+    operands in the same order, so whole mixed-precision solves agree bit for
+    bit: pressure, iteration count and residual history.  The cases cover
+    tiles that overhang the grid (nx = 40 < 64, ny = 24 = 3 tiles), wall and
+    periodic axes in x, y and z, an odd number of sweeps (the last one per
+    colour), a 128^3 pool with many z-chunks per tile, and the stationary
+    V-cycle iteration."""
+    if name == "pool128":
+        phi, u, prm = _pool_case(128)
+    else:
+        phi, u, prm = case(name)
+    rhs = dev(oracle.divergence(*u, prm["h"]))
+    out = []
+    for smoother in (1, 0):
+        s = make(phi, prm, precision=1, smoother=smoother, **opts)
+        # (the stationary V-cycle is cut off after max_iters: same bits either way)
+        p, it, hist = s.solve(rhs, tol=TOL, allow_not_converged="max_iters" in opts)
+        out.append((host(p), it, list(hist), s.stats()["relres"]))
+        if smoother == 1:
+            prof = {(e["name"], e["level"]) for e in s.profile()}
+            assert any(k[0] == "rbgs_f32_fused" for k in prof), prof
+        s.close()
+    (p1, it1, h1, r1), (p0, it0, h0, r0) = out
+    assert it1 == it0 and h1 == h0 and r1 == r0
+    assert np.array_equal(p1.view(np.uint64), p0.view(np.uint64))
+
+
+def test_fused_sweep_bitwise_full_size_pool():
+    """The benchmark's 256^3 pool workload (7 z-chunks of 36-37 planes at the
+    finest level): fused and per-colour smoothing give the same bits."""
+    phi, u, prm = synth.workload("pool256")
+    d = [dev(c) for c in u]
+    out = []
+    for smoother in (1, 0):
+        s = Poisson(dev(phi), prm["h"], prm["bc"], prm["rho_l"], prm["rho_g"], prm["sigma"],
+                    precision=1, smoother=smoother)
+        rhs = s.divergence(*d)
+        p, it, hist = s.solve(rhs, tol=TOL)
+        out.append((p, it, list(hist)))
+        s.close()
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert torch.equal(out[0][0], out[1][0])
