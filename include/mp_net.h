@@ -192,6 +192,15 @@ mp_status mp_net_make_target(mp_net_handle net, const double *p_dev, float *q_de
  * Stream for the network's work (cudaStream_t; NULL = legacy default). */
 mp_status mp_net_set_stream(mp_net_handle net, void *stream);
 
+/* Defines: no paper passage (test support for the error path of the bounded
+ * waits).  Test only: the next n convolution launches of this process treat
+ * the first wait of every CTA on its shared-memory staging barrier as timed
+ * out.  That wait comes before any tensor-core instruction; the CTA then
+ * waits (bounded, as always) for the copies it has already started,
+ * releases its tensor memory and returns, and the call that launched it
+ * returns MP_ERR_TIMEOUT.  Handles stay usable.  n = 0 cancels. */
+mp_status mp_net_test_wait_timeout(int n);
+
 /* Defines: no paper passage (the paper has no learned component); resource release. */
 void mp_net_destroy(mp_net_handle net);
 

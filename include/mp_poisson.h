@@ -91,6 +91,10 @@ typedef struct {
                         1 (default) = one fused pass per red-black sweep (both colours,
                         shared-memory halo staging, second iterate buffer); 0 = one
                         in-place launch per colour.  Bitwise the same result. */
+  int label_limit;   /* bound on every find walk and union retry of the gas-component
+                        labelling (default 8192; walks are a few steps long in practice).
+                        A geometry whose labelling reaches it is solved without deflation
+                        (mp_stats.components = 0). */
   void *stream;      /* cudaStream_t; NULL = legacy default stream. */
 } mp_opts;
 

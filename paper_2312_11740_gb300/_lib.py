@@ -44,6 +44,7 @@ class mp_opts(ctypes.Structure):
         ("net_check", ctypes.c_int),
         ("deflate", ctypes.c_int),
         ("smoother", ctypes.c_int),
+        ("label_limit", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -116,6 +117,7 @@ SIGNATURES = {
     "mp_net_forward": (_I, [_P, _P]),
     "mp_net_train_step": (_I, [_P, _P, ctypes.c_float, _I, _DP]),
     "mp_net_loss_grad": (_I, [_P, _P, _P, _DP]),
+    "mp_net_test_wait_timeout": (_I, [_I]),
     "mp_net_set_input": (_I, [_P, _P]),
     "mp_net_backward": (_I, [_P, _P, _P]),
     "mp_net_pressure": (_I, [_P, _D, _P]),

@@ -25,8 +25,6 @@ namespace mp {
 
 constexpr int DEFL_MAX = 4096;          // components handled (more: deflation off)
 constexpr int DEFL_REP = 16;            // replicas of each accumulator (atomic contention)
-constexpr int CCL_FIND_LIMIT = 8192;    // bound on a find walk (path halving keeps walks short)
-constexpr int CCL_UNITE_LIMIT = 512;    // bound on the retries of one union
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_TILE = 8 * SCAN_THREADS;  // counts scanned per pass (in shared memory)
 constexpr int BAND_THREADS = 256;
@@ -51,8 +49,10 @@ __device__ __forceinline__ double warp_max(double v) {
 
 // root of x.  Labels only decrease (lab[x] <= x always), so walks end at a
 // root; path halving (lab[x] <- lab[lab[x]], by atomicMin) keeps them short.
-__device__ __forceinline__ int ccl_find(int *lab, int x, int *err) {
-  for (int it = 0; it < CCL_FIND_LIMIT; ++it) {
+// Every labelling loop stops after `limit` rounds (mp_opts.label_limit) and
+// raises *err, which turns deflation off for the geometry.
+__device__ __forceinline__ int ccl_find(int *lab, int x, int *err, int limit) {
+  for (int it = 0; it < limit; ++it) {
     const int p = ld_volatile(lab + x);
     if (p == x) return x;
     const int g = ld_volatile(lab + p);
@@ -65,10 +65,10 @@ __device__ __forceinline__ int ccl_find(int *lab, int x, int *err) {
 
 // union of the components of a and b: the larger root is hooked under the
 // smaller with atomicMin, retried on the new root if another thread got there
-__device__ void ccl_unite(int *lab, int a, int b, int *err) {
-  for (int it = 0; it < CCL_UNITE_LIMIT; ++it) {
-    a = ccl_find(lab, a, err);
-    b = ccl_find(lab, b, err);
+__device__ void ccl_unite(int *lab, int a, int b, int *err, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    a = ccl_find(lab, a, err, limit);
+    b = ccl_find(lab, b, err, limit);
     if (a == b) return;
     if (a < b) {
       const int old = atomicMin(lab + b, a);
@@ -83,40 +83,118 @@ __device__ void ccl_unite(int *lab, int a, int b, int *err) {
   atomicExch(err, 1);
 }
 
-__global__ void k_ccl_init(const double *__restrict__ phi, int *__restrict__ lab, size_t n) {
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x)
-    lab[c] = gas(phi[c]) ? (int)c : -1;
+// Two-pass labelling.  Pass 1 (k_ccl_tile): a 32 x 8 x 8 tile of cells is
+// labelled in shared memory (union-find on local indices, which order the
+// cells as their global indices do), and every gas cell gets the global index
+// of its local root -- the smallest cell of its local component, so labels
+// still only decrease.  Pass 2 (k_ccl_faces): only the cells on a tile's high
+// faces unite, globally, with their neighbour across the face (periodic axes
+// wrap), their finds one hop long.  The global unions drop from three per gas
+// cell to about one per four cells, which matters when one component fills
+// most of the grid (the gas above a liquid pool).
+constexpr int CT_X = 32, CT_Y = 8, CT_Z = 8, CT_CELLS = CT_X * CT_Y * CT_Z, CT_THREADS = 512;
+
+__device__ __forceinline__ int ct_find(int *L, int x, int *err, int limit) {
+  const volatile int *V = L;  // other threads hook and halve concurrently
+  for (int it = 0; it < limit; ++it) {
+    const int p = V[x];
+    if (p == x) return x;
+    const int g = V[p];
+    if (g < p) atomicMin(L + x, g);
+    x = p;
+  }
+  atomicExch(err, 1);
+  return x;
+}
+__device__ void ct_unite(int *L, int a, int b, int *err, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    a = ct_find(L, a, err, limit);
+    b = ct_find(L, b, err, limit);
+    if (a == b) return;
+    if (a < b) {
+      const int old = atomicMin(L + b, a);
+      if (old == b) return;
+      b = old;
+    } else {
+      const int old = atomicMin(L + a, b);
+      if (old == a) return;
+      a = old;
+    }
+  }
+  atomicExch(err, 1);
 }
 
-// unite every gas cell with its gas neighbours in +x, +y, +z (wrapping on
-// periodic axes only)
-__global__ void k_ccl_merge(int *lab, Dims d, int per, int *err) {
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-  if (i >= d.nx || j >= d.ny) return;
-  const int c = (int)at(d, i, j, k);
-  if (ld_volatile(lab + c) < 0) return;
-  if (i + 1 < d.nx || (per & 1)) {
-    const int nb = (int)at(d, whi(i, d.nx), j, k);
-    if (ld_volatile(lab + nb) >= 0) ccl_unite(lab, c, nb, err);
+__global__ void __launch_bounds__(CT_THREADS) k_ccl_tile(const double *__restrict__ phi,
+                                                         int *__restrict__ lab, Dims d, int *err,
+                                                         int limit) {
+  __shared__ int L[CT_CELLS];
+  const int tx = blockIdx.x * CT_X, ty = blockIdx.y * CT_Y, tz = blockIdx.z * CT_Z;
+  // local index li = x + CT_X (y + CT_Y z); cells outside the grid are liquid
+  for (int li = threadIdx.x; li < CT_CELLS; li += CT_THREADS) {
+    const int x = tx + li % CT_X, y = ty + (li / CT_X) % CT_Y, z = tz + li / (CT_X * CT_Y);
+    const bool in = x < d.nx && y < d.ny && z < d.nz;
+    L[li] = in && gas(phi[at(d, x, y, z)]) ? li : -1;
   }
-  if (j + 1 < d.ny || (per & 2)) {
-    const int nb = (int)at(d, i, whi(j, d.ny), k);
-    if (ld_volatile(lab + nb) >= 0) ccl_unite(lab, c, nb, err);
+  __syncthreads();
+  for (int li = threadIdx.x; li < CT_CELLS; li += CT_THREADS) {
+    if (L[li] < 0) continue;
+    const int lx = li % CT_X, ly = (li / CT_X) % CT_Y, lz = li / (CT_X * CT_Y);
+    if (lx + 1 < CT_X && L[li + 1] >= 0) ct_unite(L, li, li + 1, err, limit);
+    if (ly + 1 < CT_Y && L[li + CT_X] >= 0) ct_unite(L, li, li + CT_X, err, limit);
+    if (lz + 1 < CT_Z && L[li + CT_X * CT_Y] >= 0) ct_unite(L, li, li + CT_X * CT_Y, err, limit);
   }
-  if (k + 1 < d.nz || (per & 4)) {
-    const int nb = (int)at(d, i, j, whi(k, d.nz));
-    if (ld_volatile(lab + nb) >= 0) ccl_unite(lab, c, nb, err);
+  __syncthreads();
+  for (int li = threadIdx.x; li < CT_CELLS; li += CT_THREADS) {
+    const int x = tx + li % CT_X, y = ty + (li / CT_X) % CT_Y, z = tz + li / (CT_X * CT_Y);
+    if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
+    int v = -1;
+    if (L[li] >= 0) {
+      const int r = ct_find(L, li, err, limit);
+      v = (int)at(d, tx + r % CT_X, ty + (r / CT_X) % CT_Y, tz + r / (CT_X * CT_Y));
+    }
+    lab[at(d, x, y, z)] = v;
+  }
+}
+
+// unite the gas cells on the high faces of every tile with their gas
+// neighbour across the face (wrapping on periodic axes only)
+__global__ void __launch_bounds__(CT_THREADS) k_ccl_faces(int *lab, Dims d, int per, int *err,
+                                                          int limit) {
+  const int tx = blockIdx.x * CT_X, ty = blockIdx.y * CT_Y, tz = blockIdx.z * CT_Z;
+  const int xe = min(CT_X, d.nx - tx), ye = min(CT_Y, d.ny - ty), ze = min(CT_Z, d.nz - tz);
+  // the face cells of the tile: x = xe-1 (ye * ze), y = ye-1 (xe * ze), z = ze-1 (xe * ye)
+  const int nfx = ye * ze, nfy = xe * ze, nfz = xe * ye;
+  for (int e = threadIdx.x; e < nfx + nfy + nfz; e += CT_THREADS) {
+    int x, y, z, dir;
+    if (e < nfx) {
+      x = xe - 1; y = e % ye; z = e / ye; dir = 0;
+    } else if (e < nfx + nfy) {
+      const int f = e - nfx;
+      y = ye - 1; x = f % xe; z = f / xe; dir = 1;
+    } else {
+      const int f = e - nfx - nfy;
+      z = ze - 1; x = f % xe; y = f / xe; dir = 2;
+    }
+    x += tx;
+    y += ty;
+    z += tz;
+    const int c = (int)at(d, x, y, z);
+    if (ld_volatile(lab + c) < 0) continue;
+    int nb = -1;
+    if (dir == 0 && (x + 1 < d.nx || (per & 1))) nb = (int)at(d, whi(x, d.nx), y, z);
+    if (dir == 1 && (y + 1 < d.ny || (per & 2))) nb = (int)at(d, x, whi(y, d.ny), z);
+    if (dir == 2 && (z + 1 < d.nz || (per & 4))) nb = (int)at(d, x, y, whi(z, d.nz));
+    if (nb >= 0 && ld_volatile(lab + nb) >= 0) ccl_unite(lab, c, nb, err, limit);
   }
 }
 
 // lab[c] <- root of c for every gas cell; every root appends its index to
 // roots (first DEFL_MAX of them; *nroots counts all)
-__global__ void k_ccl_flatten(int *lab, size_t n, int *err, int *roots, int *nroots) {
+__global__ void k_ccl_flatten(int *lab, size_t n, int *err, int *roots, int *nroots, int limit) {
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
     if (lab[c] < 0) continue;
-    const int r = ccl_find(lab, (int)c, err);
+    const int r = ccl_find(lab, (int)c, err, limit);
     lab[c] = r;
     if (r == (int)c) {
       const int q = atomicAdd(nroots, 1);
@@ -320,12 +398,35 @@ __device__ __forceinline__ void band_row(const F *__restrict__ bx, const F *__re
   ws[6] = -self;
 }
 
+// A warp's running FP64 sum for one component, carried across grid-stride
+// chunks and added to the fixed-point accumulator when the component changes
+// (and by flush at the end): one atomic add per warp and component run.
+// Every lane holds the same state.
+struct FxCarry {
+  int cur = -1;
+  double run = 0.0;
+  __device__ __forceinline__ void add(unsigned long long *acc, int m, double s, double scale) {
+    if (m == cur) {
+      run += s;
+      return;
+    }
+    flush(acc, scale);
+    cur = m;
+    run = s;
+  }
+  __device__ __forceinline__ void flush(unsigned long long *acc, double scale) {
+    if (cur >= 0 && (threadIdx.x & 31) == 0 && run != 0.0) fx_add(acc, cur, run, scale);
+    cur = -1;
+    run = 0.0;
+  }
+};
+
 // Warp-aggregated fixed-point add of the (ks[f], vals[f]) pairs of every lane:
 // the contributions to the warp's leading component (the first one met in
-// lane order) are summed across the warp in a fixed shuffle tree and added
-// once; the others are added per lane.  Called by all 32 lanes.
+// lane order) are summed across the warp in a fixed shuffle tree and carried
+// in `carry`; the others are added per lane.  Called by all 32 lanes.
 __device__ __forceinline__ void fx_add_warp(unsigned long long *acc, const int ks[7],
-                                            const double vals[7], double scale) {
+                                            const double vals[7], double scale, FxCarry &carry) {
   int mine = -1;
 #pragma unroll
   for (int f = 0; f < 7; ++f)
@@ -343,7 +444,7 @@ __device__ __forceinline__ void fx_add_warp(unsigned long long *acc, const int k
       other = true;
   }
   s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0 && s != 0.0) fx_add(acc, mm, s, scale);
+  carry.add(acc, mm, s, scale);
   if (other) {
 #pragma unroll
     for (int f = 0; f < 7; ++f)
@@ -357,6 +458,7 @@ __global__ void k_defl_E(const int *__restrict__ band, int nband, const int *__r
                          const F *__restrict__ bx, const F *__restrict__ by,
                          const F *__restrict__ bz, Dims d, unsigned long long *acc, double scale) {
   const int stride = gridDim.x * blockDim.x;
+  FxCarry carry;
   for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < nband; e0 += stride) {
     const int e = e0 + (threadIdx.x & 31);
     int ks[7];
@@ -366,8 +468,9 @@ __global__ void k_defl_E(const int *__restrict__ band, int nband, const int *__r
     if (e < nband) band_row(bx, by, bz, comp, d, (size_t)band[e], ks, ws);
 #pragma unroll
     for (int f = 0; f < 6; ++f) ks[f] = -1;  // only the diagonal term z_j^T A z_j
-    fx_add_warp(acc, ks, ws, scale);
+    fx_add_warp(acc, ks, ws, scale, carry);
   }
+  carry.flush(acc, scale);
 }
 
 // max |v| over the band (as the ordered bits of a non-negative double)
@@ -395,6 +498,7 @@ __global__ void k_defl_azt(const int *__restrict__ band, int nband, const int *_
   const double scale = bound > 0.0 ? ldexp(1.0, 60) / bound : 1.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) *scale_out = scale;
   const int stride = gridDim.x * blockDim.x;
+  FxCarry carry;
   for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < nband; e0 += stride) {
     const int e = e0 + (threadIdx.x & 31);
     int ks[7];
@@ -408,29 +512,36 @@ __global__ void k_defl_azt(const int *__restrict__ band, int nband, const int *_
 #pragma unroll
       for (int f = 0; f < 7; ++f) ws[f] *= vc;
     }
-    fx_add_warp(acc, ks, ws, scale);
+    fx_add_warp(acc, ks, ws, scale, carry);
   }
+  carry.flush(acc, scale);
 }
 
-// sums[j] += sum of v over all cells of component j (|sum| bounded by the caller's scale)
+// sums[j] += sum of v over all cells of component j (|sum| bounded by the caller's scale).
+// A warp whose 32 cells hold one component sums them in a fixed shuffle tree
+// and carries that sum in FP64 across its grid-stride chunks while the
+// component stays the same, adding it to the fixed-point accumulator only
+// when the component changes and at the end: a large component (the gas
+// above a liquid pool) costs one atomic add per warp instead of one per 32
+// cells.  Fixed launch shape, fixed order: bitwise reproducible.
 template <typename T>
 __global__ void k_defl_zt(const int *__restrict__ comp, const T *__restrict__ v, size_t n,
                           unsigned long long *acc, double scale) {
+  FxCarry carry;
   for (size_t c0 = blockIdx.x * (size_t)blockDim.x; c0 < n; c0 += (size_t)gridDim.x * blockDim.x) {
     const size_t c = c0 + threadIdx.x;
     const int m = c < n ? comp[c] : -1;
     const double val = m >= 0 ? (double)v[c] : 0.0;
-    // a full warp whose gas cells all lie in one component adds its sum once
     const unsigned gasl = __ballot_sync(0xffffffffu, m >= 0);
     if (gasl == 0u) continue;
     const int mm = __shfl_sync(0xffffffffu, m, __ffs(gasl) - 1);
     if (__all_sync(0xffffffffu, m < 0 || m == mm)) {
-      const double s = warp_sum(val);
-      if ((threadIdx.x & 31) == 0) fx_add(acc, mm, s, scale);
+      carry.add(acc, mm, warp_sum(val), scale);
     } else if (m >= 0) {
       fx_add(acc, m, val, scale);
     }
   }
+  carry.flush(acc, scale);
 }
 
 // c_j = E_jj^-1 (s_j - t_j): s from the sum sa (scale *scale_a, or fixed_scale_a

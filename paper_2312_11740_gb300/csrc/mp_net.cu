@@ -175,6 +175,7 @@ struct HaloArgs {
   int nx, ny, nz;       // output grid
   int ca, up_a, cout, relu;
   int tiles_x, tiles_y, ntiles, nsplit, nchunk;
+  int fail_first;  // test: treat the first stage wait as timed out (before any MMA)
   int *err;
 };
 
@@ -352,7 +353,7 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     // one thread polls the barriers (127 pollers would load the shared-memory
     // pipe that feeds the tensor core); the others wait at the CTA barrier
     if (tid == 0) {
-      if (mbar_wait(&full[buf], (uint32_t)((s / NS) & 1)))
+      if (!(s == 0 && a.fail_first) && mbar_wait(&full[buf], (uint32_t)((s / NS) & 1)))
         waited_full = s + 1;
       else
         abort_flag = 1;
@@ -1013,6 +1014,7 @@ __global__ void k_to_pressure(const float *__restrict__ q, size_t n, const doubl
 
 // =================================================================== host side
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -1153,6 +1155,15 @@ int sm_count() {
   return n;
 }
 
+// Launches that are still to report a timed-out first wait (mp_net_test_wait_timeout).
+std::atomic<int> g_wait_failures{0};
+int take_wait_failure() {
+  int v = g_wait_failures.load();
+  while (v > 0 && !g_wait_failures.compare_exchange_weak(v, v - 1)) {
+  }
+  return v > 0 ? 1 : 0;
+}
+
 template <int NC>
 mp_status launch_halo(const ConvGeom &g, const CUtensorMap &ma, const CUtensorMap &mb,
                       const bf16 *xa, const bf16 *wimg, const float *bias, int cout, bf16 *y,
@@ -1183,6 +1194,7 @@ mp_status launch_halo(const ConvGeom &g, const CUtensorMap &ma, const CUtensorMa
   a.ntiles = a.tiles_x * a.tiles_y * tiles_z;
   a.nsplit = cout / NC;
   a.nchunk = g.cin / 16;
+  a.fail_first = take_wait_failure();
   a.err = err;
   const long items = (long)a.ntiles * a.nsplit;
   long grid = std::min<long>(items, (long)sm_count() * h_ctas_per_sm<NC>());
@@ -1778,6 +1790,12 @@ mp_status mp_net_train_step(mp_net_handle net, const float *target, float lr, in
                       net->st));
   NCKS(check_err(net));
   if (loss_out) *loss_out = net->loss_kind == 0 ? net->hscal[0] / (double)n : net->hscal[0];
+  return MP_OK;
+}
+
+mp_status mp_net_test_wait_timeout(int n) {
+  if (n < 0) return MP_ERR_INVALID_ARG;
+  g_wait_failures.store(n);
   return MP_OK;
 }
 

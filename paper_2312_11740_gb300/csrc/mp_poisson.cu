@@ -47,7 +47,7 @@ enum KernelId {
   K_RBGS64, K_RBGS32, K_RBGS32F, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
   K_APPLY64, K_APPLY32, K_RESID64, K_RESID32, K_RESIDMIX, K_DOT64, K_DOT32, K_AXPY64, K_AXPY32,
   K_XPBY64, K_XPBY32, K_ADD64, K_ADD32, K_ADDF32, K_SUM, K_SUBMEAN, K_REDUCE, K_ASSEMBLE,
-  K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_DEFL, K_COUNT
+  K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_DEFL, K_DEFL_LABEL, K_DEFL_DOT, K_COUNT
 };
 const char *const kKernelNames[K_COUNT] = {
   "curvature", "gfm_faces", "jump", "diag", "coarsen_faces", "dense_build", "gauss_jordan",
@@ -57,7 +57,7 @@ const char *const kKernelNames[K_COUNT] = {
   "residual_f64", "residual_f32", "residual_mixed", "dot_f64", "dot_f32", "axpy2_f64",
   "axpy2_f32", "xpby_f64", "xpby_f32", "add_f64", "add_f32", "add_f32_to_f64", "sum",
   "sub_mean", "reduce", "assemble", "assemble_u", "project", "divergence", "scale",
-  "deflation"};
+  "deflation_band", "deflation_label", "deflation_dot"};
 constexpr int MAX_LEVELS = 16;
 constexpr int TAIL32_NU_MAX = 4;  // sweeps per level in the one-CTA FP32 tail
 constexpr int EVENT_POOL = 4096;
@@ -513,22 +513,26 @@ mp_status deflation_setup(mp_poisson *hd) {
   const int nblk = (int)((n + BAND_CELLS - 1) / BAND_CELLS);
   // dint: [0] components (roots), [1] band cells, [2] labelling bound exceeded
   CK(cudaMemsetAsync(hd->dint, 0, 4 * sizeof(int), hd->st));
-  LAUNCH(hd, K_DEFL, 0, n * 12.0, k_ccl_init, VEC_BLOCKS, VEC_THREADS, hd->phi, hd->lab, n);
-  LAUNCH(hd, K_DEFL, 0, n * 16.0, k_ccl_merge, cell_grid(l0.d), kBlock, hd->lab, l0.d, hd->per,
-         hd->dint + 2);
-  LAUNCH(hd, K_DEFL, 0, n * 8.0, k_ccl_flatten, VEC_BLOCKS, VEC_THREADS, hd->lab, n, hd->dint + 2,
-         hd->roots, hd->dint);
-  LAUNCH(hd, K_DEFL, 0, DEFL_MAX * 8.0, k_rank_roots, 1, 1024, hd->roots, hd->dint, hd->comp);
-  LAUNCH(hd, K_DEFL, 0, n * 12.0, k_comp_from_roots, VEC_BLOCKS, VEC_THREADS, hd->lab, hd->comp,
+  const dim3 ct_grid((l0.d.nx + CT_X - 1) / CT_X, (l0.d.ny + CT_Y - 1) / CT_Y,
+                     (l0.d.nz + CT_Z - 1) / CT_Z);
+  const int lim = hd->opts.label_limit;
+  LAUNCH(hd, K_DEFL_LABEL, 0, n * 12.0, k_ccl_tile, ct_grid, CT_THREADS, hd->phi, hd->lab, l0.d,
+         hd->dint + 2, lim);
+  LAUNCH(hd, K_DEFL_LABEL, 0, n * 4.0, k_ccl_faces, ct_grid, CT_THREADS, hd->lab, l0.d, hd->per,
+         hd->dint + 2, lim);
+  LAUNCH(hd, K_DEFL_LABEL, 0, n * 8.0, k_ccl_flatten, VEC_BLOCKS, VEC_THREADS, hd->lab, n, hd->dint + 2,
+         hd->roots, hd->dint, lim);
+  LAUNCH(hd, K_DEFL_LABEL, 0, DEFL_MAX * 8.0, k_rank_roots, 1, 1024, hd->roots, hd->dint, hd->comp);
+  LAUNCH(hd, K_DEFL_LABEL, 0, n * 12.0, k_comp_from_roots, VEC_BLOCKS, VEC_THREADS, hd->lab, hd->comp,
          n);
   CK(cudaMemcpyAsync(hd->hint, hd->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost, hd->st));
   CK(cudaStreamSynchronize(hd->st));
   const int m = hd->hint[0];
   if (hd->hint[2] != 0 || m <= 0 || m > DEFL_MAX) return MP_OK;
-  LAUNCH(hd, K_DEFL, 0, n * 5.0, k_band_count, nblk, BAND_THREADS, hd->comp, l0.d, n, hd->cnt,
+  LAUNCH(hd, K_DEFL_LABEL, 0, n * 5.0, k_band_count, nblk, BAND_THREADS, hd->comp, l0.d, n, hd->cnt,
          hd->bflag);
-  LAUNCH(hd, K_DEFL, 0, nblk * 8.0, k_scan_counts, 1, SCAN_THREADS, hd->cnt, nblk, hd->dint + 1);
-  LAUNCH(hd, K_DEFL, 0, n * 1.0, k_band_assign, nblk, BAND_THREADS, hd->bflag, n, hd->cnt,
+  LAUNCH(hd, K_DEFL_LABEL, 0, nblk * 8.0, k_scan_counts, 1, SCAN_THREADS, hd->cnt, nblk, hd->dint + 1);
+  LAUNCH(hd, K_DEFL_LABEL, 0, n * 1.0, k_band_assign, nblk, BAND_THREADS, hd->bflag, n, hd->cnt,
          hd->band);
   CK(cudaMemcpyAsync(hd->hint, hd->dint, 4 * sizeof(int), cudaMemcpyDeviceToHost, hd->st));
   CK(cudaStreamSynchronize(hd->st));
@@ -561,7 +565,7 @@ mp_status defl_ztb(mp_poisson *hd) {
   CK(cudaMemsetAsync(hd->acc_a, 0, defl_acc_bytes(m), hd->st));
   CK(cudaMemsetAsync(hd->acc_b, 0, defl_acc_bytes(m), hd->st));
   CK(cudaMemsetAsync(hd->dmax, 0, sizeof(unsigned long long), hd->st));
-  LAUNCH(hd, K_DEFL, 0, hd->n * 12.0, k_defl_zt<double>, VEC_BLOCKS, VEC_THREADS, hd->comp, hd->b,
+  LAUNCH(hd, K_DEFL_DOT, 0, hd->n * 12.0, k_defl_zt<double>, VEC_BLOCKS, VEC_THREADS, hd->comp, hd->b,
          hd->n, hd->acc_ztb, hd->ztb_scale);
   return launch_ok();
 }
@@ -606,7 +610,7 @@ mp_status defl_sub(mp_poisson *hd, T *v, const F *bx, const F *by, const F *bz) 
 mp_status defl_finish(mp_poisson *hd, double *x) {
   Level &l0 = hd->L[0];
   CKS((defl_coef<double, double>(hd, x, l0.bx, l0.by, l0.bz, true)));
-  LAUNCH(hd, K_DEFL, 0, hd->n * 12.0, k_defl_add_z, VEC_BLOCKS, VEC_THREADS, x, hd->comp, hd->n,
+  LAUNCH(hd, K_DEFL_DOT, 0, hd->n * 12.0, k_defl_add_z, VEC_BLOCKS, VEC_THREADS, x, hd->comp, hd->n,
          hd->coef);
   return launch_ok();
 }
@@ -653,7 +657,7 @@ mp_status defl_rz(mp_poisson *hd, const T *r, T *z, const F *bx, const F *by, co
     coef = hd->coef;
   else
     coef = hd->coef32;
-  LAUNCH(hd, K_DEFL, 0, hd->n * (3.0 * sizeof(T) + 4.0), k_dot_zdefl<T>, VEC_BLOCKS, VEC_THREADS,
+  LAUNCH(hd, K_DEFL_DOT, 0, hd->n * (3.0 * sizeof(T) + 4.0), k_dot_zdefl<T>, VEC_BLOCKS, VEC_THREADS,
          r, z, hd->comp, coef, hd->n, hd->partial);
   return launch_ok();
 }
@@ -1070,7 +1074,8 @@ bool valid_opts(const mp_opts &o) {
          o.initial_guess >= 0 && o.initial_guess <= 2 && o.max_iters >= 0 && o.nu1 >= 1 &&
          o.nu2 >= 1 && o.nu_growth >= 1 && o.nu_max >= 1 && o.inner_rtol > 0.0 &&
          o.inner_rtol < 1.0 && o.inner_max >= 1 && (o.net_check == 0 || o.net_check == 1) &&
-         (o.deflate == 0 || o.deflate == 1) && (o.smoother == 0 || o.smoother == 1);
+         (o.deflate == 0 || o.deflate == 1) && (o.smoother == 0 || o.smoother == 1) &&
+         o.label_limit >= 1;
 }
 
 void apply_nu(mp_poisson *hd) {
@@ -1340,6 +1345,7 @@ void mp_opts_default(mp_opts *o) {
   o->net_check = 0;
   o->deflate = 1;
   o->smoother = 1;
+  o->label_limit = 8192;
   o->stream = nullptr;
 }
 

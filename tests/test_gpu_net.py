@@ -505,3 +505,25 @@ def test_trained_net_saves_iterations_on_held_out_seeds():
     print("deflated (zero its, learned its, kept, deflated residual ratio):", defl)
     assert sum(kept) == len(kept), kept
     assert np.mean(saved) >= 0.75, saved
+
+
+def test_conv_wait_timeout_is_reported_and_the_network_stays_usable():
+    """The bounded waits of the tcgen05 convolution: with the test switch the
+    first staging-barrier wait of every CTA of the next launch counts as timed
+    out (before any MMA is issued).  The CTAs wait for their copies in flight,
+    free their tensor memory and return; the forward pass reports
+    MP_ERR_TIMEOUT, and the next forward pass gives the same output as
+    before, bit for bit."""
+    from paper_2312_11740_gb300 import MPError, _lib
+    shape = (32, 32, 32)
+    net = Net(32, 32, 32)
+    net.set_params(to_f32(random_param_vector(net, 41)))
+    net.set_input(to_bf16(make_input(42, shape)))
+    q_ref = net.forward()
+    assert _lib.load().mp_net_test_wait_timeout(1) == _lib.MP_OK
+    with pytest.raises(MPError) as err:
+        net.forward()
+    assert err.value.status == _lib.MP_ERR_TIMEOUT
+    q = net.forward()
+    assert torch.equal(q, q_ref)
+    net.close()

@@ -362,6 +362,24 @@ def test_gas_components_match_scipy_labelling(bc):
     s.close()
 
 
+def test_gas_components_pool_layer_spans_every_tile():
+    """A gas layer above a liquid pool is one component crossing every
+    labelling tile (32 x 8 x 8 cells) and both periodic wraps; the bubbles
+    below it, some cut by the periodic boundaries, are separate components.
+    80 cells per axis: three tiles in x (the last one partial), ten in y."""
+    n = 80
+    h = 1.0 / n
+    bc = (P, P, N)
+    bub = [((0.02, 0.5, 0.3), 0.1), ((0.5, 0.97, 0.25), 0.08), ((0.6, 0.6, 0.2), 0.06)]
+    phi = synth.level_set((n, n, n), h, bub, pool_z0=0.55, bc=bc)
+    s = make(phi, dict(h=h, bc=bc, rho_l=1.0, rho_g=1e-3, sigma=0.07))
+    comp, m = s.components()
+    ref, mref = _components_reference(phi, bc)
+    assert m == mref == 4
+    assert np.array_equal(comp.cpu().numpy(), ref)
+    s.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_deflation_same_answer_fewer_iterations(precision):
     """Deflating CG by the bubbles' indicator vectors changes the iteration,
@@ -518,3 +536,27 @@ def test_fused_sweep_bitwise_full_size_pool():
         s.close()
     assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
     assert torch.equal(out[0][0], out[1][0])
+
+
+def test_labelling_bound_turns_deflation_off_and_the_solve_still_converges():
+    """When a find walk or union retry of the gas-component labelling reaches
+    mp_opts.label_limit (here 1, so any walk longer than a step does), the
+    geometry is solved without deflation: no components, the same converged
+    pressure, and deflation returns with the default bound."""
+    phi, u, prm = _pool_case(64, seed=9)
+    rhs = dev(oracle.divergence(*u, prm["h"]))
+    s = make(phi, prm, precision=1)
+    p_ref, _, _ = s.solve(rhs, tol=TOL)
+    assert s.stats()["components"] > 1
+    s.set_opts(label_limit=1)
+    s.set_geometry(dev(phi), prm["rho_l"], prm["rho_g"], prm["sigma"])
+    assert s.components()[1] == 0
+    p, it, _ = s.solve(rhs, tol=TOL)
+    st = s.stats()
+    assert st["components"] == 0 and st["relres"] <= TOL
+    assert rel_l2(host(p), host(p_ref)) < PARITY
+    s.set_opts(label_limit=8192)
+    s.set_geometry(dev(phi), prm["rho_l"], prm["rho_g"], prm["sigma"])
+    s.solve(rhs, tol=TOL)
+    assert s.stats()["components"] > 1
+    s.close()
