@@ -24,7 +24,15 @@ _LIB = os.path.join(_HERE, "_build", "libmp_oracle.so")
 _lib = None
 
 PERIODIC = 0
-NEUMANN = 1
+NEUMANN = 1            # wall or inflow on both sides (zero normal pressure gradient)
+DIRICHLET = 2          # outflow on both sides (p = 0 on the boundary face)
+NEUMANN_DIRICHLET = 3  # wall/inflow on the low side, outflow on the high side
+DIRICHLET_NEUMANN = 4  # outflow on the low side, wall/inflow on the high side
+
+
+def singular(bc):
+    """True when the operator annihilates constants (no outflow side)."""
+    return not any(b in (DIRICHLET, NEUMANN_DIRICHLET, DIRICHLET_NEUMANN) for b in bc)
 
 
 def build(force: bool = False) -> str:
@@ -68,8 +76,8 @@ def _p(a):
 
 
 def _per(bc):
-    arr = (ctypes.c_int * 3)(*[1 if b == PERIODIC else 0 for b in bc])
-    return arr
+    """Boundary codes per axis, as the C oracle takes them."""
+    return (ctypes.c_int * 3)(*[int(b) for b in bc])
 
 
 def _f64(a):
@@ -128,7 +136,8 @@ def residual(f, b, x, h, bc):
 
 
 def cg(f, b, h, bc, tol=1e-12, maxit=200000, x0=None):
-    """Jacobi-PCG solve of A x = b (b mean-free). Returns (x, iters, relres)."""
+    """Jacobi-PCG solve of A x = b (b mean-free unless an axis has an outflow
+    side). Returns (x, iters, relres)."""
     b = _f64(b)
     nz, ny, nx = b.shape
     x = np.zeros_like(b) if x0 is None else _f64(x0).copy()
@@ -188,17 +197,20 @@ def project(phi, kappa, f, p, ux, uy, uz, h, sigma, bc):
 
 
 def assemble(phi, rhs, h, rho_l, rho_g, sigma, bc):
-    """kappa, faces, J and the mean-free right-hand side b = rhs + J - mean."""
+    """kappa, faces, J and the right-hand side b = rhs + J, minus its mean
+    when the operator is singular (no outflow side)."""
     kappa = curvature(phi, h, bc)
     f = faces(phi, rho_l, rho_g, bc)
     J = jump(phi, kappa, f, h, sigma, bc)
     b = _f64(rhs) + J
-    b = b - b.mean()
+    if singular(bc):
+        b = b - b.mean()
     return kappa, f, J, b
 
 
 def solve(phi, rhs, h, rho_l, rho_g, sigma, bc, tol=1e-12, maxit=200000):
-    """Full oracle solve: returns dict with p (mean-free), b, kappa, faces, iters, relres."""
+    """Full oracle solve: returns dict with p (mean-free when singular), b, kappa,
+    faces, iters, relres."""
     kappa, f, J, b = assemble(phi, rhs, h, rho_l, rho_g, sigma, bc)
     x, it, rel = cg(f, b, h, bc, tol=tol, maxit=maxit)
     return dict(p=x, b=b, kappa=kappa, faces=f, J=J, iters=it, relres=rel)

@@ -18,10 +18,22 @@
  *   A p = b,  (A p)_c = sum_faces beta_f (p_nb - p_c) / h^2,
  *   b = rhs + J - mean(rhs + J),   gauge mean(p) = 0.
  *
+ * Boundaries: one code per axis (bc[a]): 0 periodic; 1 wall or inflow on
+ * both sides (zero normal pressure gradient: the face carries no pressure
+ * flux); 2 outflow on both sides (p = 0 on the boundary face); 3 wall/inflow
+ * on the low side and outflow on the high side; 4 the reverse.  The paper
+ * sets boundary types per side (xl_boundary_type / xr_boundary_type with
+ * inflow_ins / outflow_ins in its runtime-parameter TOML figure, Section 4);
+ * an outflow face holds p = 0 through an antisymmetric ghost, p_ghost =
+ * -p_cell, the cell-centred form of that condition.  With an outflow side
+ * the operator has no null space: no mean projection and no gauge.
+ *
  * Storage here is deliberately different from the CUDA path: every axis
  * keeps n+1 faces (face f between cells f-1 and f); on a periodic axis
  * faces 0 and n are the same physical face, on a wall axis both are walls
- * with beta = 0.  Cell arrays are (nz, ny, nx), x fastest.
+ * with beta = 0, on an outflow side the boundary face holds the coefficient
+ * 1/rho of the cell next to it (its ghost lies in the same fluid).  Cell
+ * arrays are (nz, ny, nx), x fastest.
  *
  * Entry points are plain loops, one formula at a time; nothing is blocked,
  * fused or reordered beyond the definitions.
@@ -35,6 +47,14 @@
 #define FX(i, j, k) ((size_t)(i) + (size_t)(nx + 1) * ((size_t)(j) + (size_t)ny * (size_t)(k)))
 #define FY(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)(ny + 1) * (size_t)(k)))
 #define FZ(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)ny * (size_t)(k)))
+
+#define PER(bc, a) ((bc)[a] == 0)
+#define DLO(bc, a) ((bc)[a] == 2 || (bc)[a] == 4) /* outflow on the low side */
+#define DHI(bc, a) ((bc)[a] == 2 || (bc)[a] == 3) /* outflow on the high side */
+
+static int any_outflow(const int bc[3]) {
+  return DLO(bc, 0) || DHI(bc, 0) || DLO(bc, 1) || DHI(bc, 1) || DLO(bc, 2) || DHI(bc, 2);
+}
 
 /* Neighbour index along one axis: periodic wrap, or mirror at a wall
  * (even reflection: ghost -1 -> 0, ghost n -> n-1). */
@@ -59,8 +79,9 @@ static int is_gas(double phi) { return phi > 0.0; } /* phi = 0 counts as liquid 
  * mph_invWeber parameter of the runtime-parameter TOML figure, Section 4;
  * MultiphaseMain, Section 3).
  */
-void oracle_curvature(int nx, int ny, int nz, double h, const int periodic[3],
+void oracle_curvature(int nx, int ny, int nz, double h, const int bc[3],
                       const double *phi, double *kappa) {
+  const int periodic[3] = {PER(bc, 0), PER(bc, 1), PER(bc, 2)};
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -108,9 +129,17 @@ static double face_beta(double pa, double pb, double rho_l, double rho_g) {
   return 1.0 / (theta * ra + (1.0 - theta) * rb);
 }
 
-/* Face coefficients for every face; walls get beta = 0 (no flux). */
-void oracle_faces(int nx, int ny, int nz, const int periodic[3], const double *phi,
+/* Coefficient of an outflow boundary face next to cell value pc: the ghost
+ * cell beyond the face lies in the same fluid as the cell. */
+static double out_beta(double pc, double rho_l, double rho_g) {
+  return 1.0 / (is_gas(pc) ? rho_g : rho_l);
+}
+
+/* Face coefficients for every face; walls get beta = 0 (no flux), outflow
+ * faces the coefficient of the fluid of their cell. */
+void oracle_faces(int nx, int ny, int nz, const int bc[3], const double *phi,
                   double rho_l, double rho_g, double *fx, double *fy, double *fz) {
+  const int periodic[3] = {PER(bc, 0), PER(bc, 1), PER(bc, 2)};
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -118,6 +147,8 @@ void oracle_faces(int nx, int ny, int nz, const int periodic[3], const double *p
         double v;
         if (i == 0 || i == nx) {
           v = periodic[0] ? face_beta(phi[IDX(nx - 1, j, k)], phi[IDX(0, j, k)], rho_l, rho_g) : 0.0;
+          if (i == 0 && DLO(bc, 0)) v = out_beta(phi[IDX(0, j, k)], rho_l, rho_g);
+          if (i == nx && DHI(bc, 0)) v = out_beta(phi[IDX(nx - 1, j, k)], rho_l, rho_g);
         } else {
           v = face_beta(phi[IDX(i - 1, j, k)], phi[IDX(i, j, k)], rho_l, rho_g);
         }
@@ -130,6 +161,8 @@ void oracle_faces(int nx, int ny, int nz, const int periodic[3], const double *p
         double v;
         if (j == 0 || j == ny) {
           v = periodic[1] ? face_beta(phi[IDX(i, ny - 1, k)], phi[IDX(i, 0, k)], rho_l, rho_g) : 0.0;
+          if (j == 0 && DLO(bc, 1)) v = out_beta(phi[IDX(i, 0, k)], rho_l, rho_g);
+          if (j == ny && DHI(bc, 1)) v = out_beta(phi[IDX(i, ny - 1, k)], rho_l, rho_g);
         } else {
           v = face_beta(phi[IDX(i, j - 1, k)], phi[IDX(i, j, k)], rho_l, rho_g);
         }
@@ -142,6 +175,8 @@ void oracle_faces(int nx, int ny, int nz, const int periodic[3], const double *p
         double v;
         if (k == 0 || k == nz) {
           v = periodic[2] ? face_beta(phi[IDX(i, j, nz - 1)], phi[IDX(i, j, 0)], rho_l, rho_g) : 0.0;
+          if (k == 0 && DLO(bc, 2)) v = out_beta(phi[IDX(i, j, 0)], rho_l, rho_g);
+          if (k == nz && DHI(bc, 2)) v = out_beta(phi[IDX(i, j, nz - 1)], rho_l, rho_g);
         } else {
           v = face_beta(phi[IDX(i, j, k - 1)], phi[IDX(i, j, k)], rho_l, rho_g);
         }
@@ -169,9 +204,10 @@ static double face_jump(double pa, double pb, double ka, double kb, double sigma
  * interface face adds +beta [p]_{a->b} / h^2 to row a and -beta [p]_{a->b} / h^2
  * to row b.  J sums to zero.  Face loops visit each physical face once.
  */
-void oracle_jump(int nx, int ny, int nz, double h, const int periodic[3], const double *phi,
+void oracle_jump(int nx, int ny, int nz, double h, const int bc[3], const double *phi,
                  const double *kappa, const double *fx, const double *fy, const double *fz,
                  double sigma, double *J) {
+  const int periodic[3] = {PER(bc, 0), PER(bc, 1), PER(bc, 2)};
   size_t n = (size_t)nx * ny * nz;
   memset(J, 0, n * sizeof(double));
   double ih2 = 1.0 / (h * h);
@@ -205,16 +241,22 @@ void oracle_jump(int nx, int ny, int nz, double h, const int periodic[3], const 
       }
 }
 
-/* Neighbour across a face on a possibly periodic axis; on a wall the face
- * coefficient is zero so any in-range index will do (use the cell itself). */
-static int nb(int i, int n, int periodic) {
-  if (i < 0) return periodic ? n - 1 : 0;
-  if (i >= n) return periodic ? 0 : n - 1;
-  return i;
+/* The cell across the low (low = 1) or high face of cell i on an axis of n
+ * cells with boundary code `code`, given inb = i - 1 or i + 1: its index
+ * inside the grid (wrapped on a periodic axis), -1 at an outflow face (the
+ * ghost value is -x_c), -2 at a wall (the face coefficient is zero; the
+ * cell's own value is used). */
+static int across(int inb, int n, int code, int low) {
+  if (inb >= 0 && inb < n) return inb;
+  if (code == 0) return inb < 0 ? n - 1 : 0;
+  if (low ? (code == 2 || code == 4) : (code == 2 || code == 3)) return -1;
+  return -2;
 }
+static double value(int m, double xin, double xc) { return m >= 0 ? xin : (m == -1 ? -xc : xc); }
 
-/* y = A x, (A x)_c = sum over the six faces of beta_f (x_nb - x_c) / h^2. */
-void oracle_apply(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+/* y = A x, (A x)_c = sum over the six faces of beta_f (x_nb - x_c) / h^2,
+ * x_nb the neighbour's value or the ghost value at a boundary face. */
+void oracle_apply(int nx, int ny, int nz, double h, const int bc[3], const double *fx,
                   const double *fy, const double *fz, const double *x, double *y) {
   double ih2 = 1.0 / (h * h);
 #pragma omp parallel for schedule(static)
@@ -222,27 +264,42 @@ void oracle_apply(int nx, int ny, int nz, double h, const int periodic[3], const
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         double xc = x[IDX(i, j, k)];
+        int a;
         double s = 0.0;
-        s += fx[FX(i, j, k)] * (x[IDX(nb(i - 1, nx, periodic[0]), j, k)] - xc);
-        s += fx[FX(i + 1, j, k)] * (x[IDX(nb(i + 1, nx, periodic[0]), j, k)] - xc);
-        s += fy[FY(i, j, k)] * (x[IDX(i, nb(j - 1, ny, periodic[1]), k)] - xc);
-        s += fy[FY(i, j + 1, k)] * (x[IDX(i, nb(j + 1, ny, periodic[1]), k)] - xc);
-        s += fz[FZ(i, j, k)] * (x[IDX(i, j, nb(k - 1, nz, periodic[2]))] - xc);
-        s += fz[FZ(i, j, k + 1)] * (x[IDX(i, j, nb(k + 1, nz, periodic[2]))] - xc);
+        a = across(i - 1, nx, bc[0], 1);
+        s += fx[FX(i, j, k)] * (value(a, a >= 0 ? x[IDX(a, j, k)] : 0.0, xc) - xc);
+        a = across(i + 1, nx, bc[0], 0);
+        s += fx[FX(i + 1, j, k)] * (value(a, a >= 0 ? x[IDX(a, j, k)] : 0.0, xc) - xc);
+        a = across(j - 1, ny, bc[1], 1);
+        s += fy[FY(i, j, k)] * (value(a, a >= 0 ? x[IDX(i, a, k)] : 0.0, xc) - xc);
+        a = across(j + 1, ny, bc[1], 0);
+        s += fy[FY(i, j + 1, k)] * (value(a, a >= 0 ? x[IDX(i, a, k)] : 0.0, xc) - xc);
+        a = across(k - 1, nz, bc[2], 1);
+        s += fz[FZ(i, j, k)] * (value(a, a >= 0 ? x[IDX(i, j, a)] : 0.0, xc) - xc);
+        a = across(k + 1, nz, bc[2], 0);
+        s += fz[FZ(i, j, k + 1)] * (value(a, a >= 0 ? x[IDX(i, j, a)] : 0.0, xc) - xc);
         y[IDX(i, j, k)] = s * ih2;
       }
 }
 
-/* Diagonal of -A: sum of the six face coefficients over h^2. */
-static void neg_diag(int nx, int ny, int nz, double h, const double *fx, const double *fy,
-                     const double *fz, double *d) {
+/* Diagonal of -A: the six face coefficients over h^2, an outflow face twice
+ * (its ghost value -x_c adds -2 beta x_c to (A x)_c). */
+static void neg_diag(int nx, int ny, int nz, double h, const int bc[3], const double *fx,
+                     const double *fy, const double *fz, double *d) {
   double ih2 = 1.0 / (h * h);
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i)
-        d[IDX(i, j, k)] = (fx[FX(i, j, k)] + fx[FX(i + 1, j, k)] + fy[FY(i, j, k)] +
-                           fy[FY(i, j + 1, k)] + fz[FZ(i, j, k)] + fz[FZ(i, j, k + 1)]) * ih2;
+      for (int i = 0; i < nx; ++i) {
+        double w[6] = {fx[FX(i, j, k)], fx[FX(i + 1, j, k)], fy[FY(i, j, k)],
+                       fy[FY(i, j + 1, k)], fz[FZ(i, j, k)], fz[FZ(i, j, k + 1)]};
+        int m[6] = {across(i - 1, nx, bc[0], 1), across(i + 1, nx, bc[0], 0),
+                    across(j - 1, ny, bc[1], 1), across(j + 1, ny, bc[1], 0),
+                    across(k - 1, nz, bc[2], 1), across(k + 1, nz, bc[2], 0)};
+        double s = 0.0;
+        for (int f = 0; f < 6; ++f) s += m[f] == -1 ? 2.0 * w[f] : w[f];
+        d[IDX(i, j, k)] = s * ih2;
+      }
 }
 
 static double dot(size_t n, const double *a, const double *b) {
@@ -253,11 +310,11 @@ static double dot(size_t n, const double *a, const double *b) {
 }
 
 /* r = b - A x; returns ||r||_2. */
-double oracle_residual(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+double oracle_residual(int nx, int ny, int nz, double h, const int bc[3], const double *fx,
                        const double *fy, const double *fz, const double *b, const double *x,
                        double *r) {
   size_t n = (size_t)nx * ny * nz;
-  oracle_apply(nx, ny, nz, h, periodic, fx, fy, fz, x, r);
+  oracle_apply(nx, ny, nz, h, bc, fx, fy, fz, x, r);
 #pragma omp parallel for schedule(static)
   for (size_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
   return sqrt(dot(n, r, r));
@@ -273,20 +330,20 @@ void oracle_remove_mean(size_t n, double *x) {
 }
 
 /* y = M x with M = -A (symmetric positive semidefinite). */
-static void apply_neg(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+static void apply_neg(int nx, int ny, int nz, double h, const int bc[3], const double *fx,
                       const double *fy, const double *fz, const double *x, double *y) {
   size_t n = (size_t)nx * ny * nz;
-  oracle_apply(nx, ny, nz, h, periodic, fx, fy, fz, x, y);
+  oracle_apply(nx, ny, nz, h, bc, fx, fy, fz, x, y);
 #pragma omp parallel for schedule(static)
   for (size_t i = 0; i < n; ++i) y[i] = -y[i];
 }
 
 /* rho = f - M x, returns ||rho||_2 */
-static double neg_residual(int nx, int ny, int nz, double h, const int periodic[3],
-                           const double *fx, const double *fy, const double *fz, const double *f,
-                           const double *x, double *rho) {
+static double neg_residual(int nx, int ny, int nz, double h, const int bc[3], const double *fx,
+                           const double *fy, const double *fz, const double *f, const double *x,
+                           double *rho) {
   size_t n = (size_t)nx * ny * nz;
-  apply_neg(nx, ny, nz, h, periodic, fx, fy, fz, x, rho);
+  apply_neg(nx, ny, nz, h, bc, fx, fy, fz, x, rho);
 #pragma omp parallel for schedule(static)
   for (size_t i = 0; i < n; ++i) rho[i] = f[i] - rho[i];
   return sqrt(dot(n, rho, rho));
@@ -295,21 +352,22 @@ static double neg_residual(int nx, int ny, int nz, double h, const int periodic[
 /*
  * Jacobi-preconditioned conjugate gradients (textbook PCG) on M x = f with
  * M = -A, f = -b: M is symmetric positive semidefinite with null space the
- * constants, and b must be mean-free so the system is consistent.
- * x is the initial guess on entry and the mean-free solution on exit.
- * Stops when ||b - A x|| <= tol ||b||; the recurrence residual is replaced
- * by the true one every 50 iterations and checked again at the end.
- * Returns iterations, or -1 if maxit was hit; *relres gets the final
- * relative residual.
+ * constants (periodic and wall boundaries; b must then be mean-free so the
+ * system is consistent), or positive definite with an outflow side.
+ * x is the initial guess on entry and the solution on exit (mean-free when
+ * the system is singular).  Stops when ||b - A x|| <= tol ||b||; the
+ * recurrence residual is replaced by the true one every 50 iterations and
+ * checked again at the end.  Returns iterations, or -1 if maxit was hit;
+ * *relres gets the final relative residual.
  */
-int oracle_cg(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+int oracle_cg(int nx, int ny, int nz, double h, const int bc[3], const double *fx,
               const double *fy, const double *fz, const double *b, double *x, double tol,
               int maxit, double *relres) {
   size_t n = (size_t)nx * ny * nz;
   double *f = malloc(n * sizeof(double)), *rho = malloc(n * sizeof(double));
   double *z = malloc(n * sizeof(double)), *p = malloc(n * sizeof(double));
   double *q = malloc(n * sizeof(double)), *d = malloc(n * sizeof(double));
-  neg_diag(nx, ny, nz, h, fx, fy, fz, d);
+  neg_diag(nx, ny, nz, h, bc, fx, fy, fz, d);
   for (size_t i = 0; i < n; ++i) f[i] = -b[i];
   double fn = sqrt(dot(n, f, f));
   int status = -1;
@@ -317,7 +375,7 @@ int oracle_cg(int nx, int ny, int nz, double h, const int periodic[3], const dou
     memset(x, 0, n * sizeof(double));
     status = 0;
   } else {
-    double rn = neg_residual(nx, ny, nz, h, periodic, fx, fy, fz, f, x, rho);
+    double rn = neg_residual(nx, ny, nz, h, bc, fx, fy, fz, f, x, rho);
     double rz_old = 0.0;
     for (int it = 0; it <= maxit; ++it) {
       if (rn <= tol * fn) { status = it; break; }
@@ -333,7 +391,7 @@ int oracle_cg(int nx, int ny, int nz, double h, const int periodic[3], const dou
         for (size_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
       }
       rz_old = rz;
-      apply_neg(nx, ny, nz, h, periodic, fx, fy, fz, p, q);
+      apply_neg(nx, ny, nz, h, bc, fx, fy, fz, p, q);
       double alpha = rz / dot(n, p, q);
 #pragma omp parallel for schedule(static)
       for (size_t i = 0; i < n; ++i) {
@@ -341,13 +399,13 @@ int oracle_cg(int nx, int ny, int nz, double h, const int periodic[3], const dou
         rho[i] -= alpha * q[i];
       }
       if ((it + 1) % 50 == 0)
-        rn = neg_residual(nx, ny, nz, h, periodic, fx, fy, fz, f, x, rho);
+        rn = neg_residual(nx, ny, nz, h, bc, fx, fy, fz, f, x, rho);
       else
         rn = sqrt(dot(n, rho, rho));
     }
   }
-  oracle_remove_mean(n, x);
-  double tn = neg_residual(nx, ny, nz, h, periodic, fx, fy, fz, f, x, rho);
+  if (!any_outflow(bc)) oracle_remove_mean(n, x);
+  double tn = neg_residual(nx, ny, nz, h, bc, fx, fy, fz, f, x, rho);
   *relres = fn > 0.0 ? tn / fn : 0.0;
   if (status >= 0 && tn > tol * fn) status = -1;
   free(f); free(rho); free(z); free(p); free(q); free(d);
@@ -357,9 +415,11 @@ int oracle_cg(int nx, int ny, int nz, double h, const int periodic[3], const dou
 /*
  * Lexicographic Gauss-Seidel for small grids: each cell in turn takes
  *   x_c = (sum_f beta_f x_nb - h^2 b_c) / sum_f beta_f,
- * i.e. row c of A x = b solved for x_c.  Sweeps until ||b - A x|| <= tol ||b||.
+ * i.e. row c of A x = b solved for x_c; an outflow face's ghost value -x_c
+ * moves to the left-hand side (twice its coefficient in the denominator,
+ * nothing in the numerator).  Sweeps until ||b - A x|| <= tol ||b||.
  */
-int oracle_gs(int nx, int ny, int nz, double h, const int periodic[3], const double *fx,
+int oracle_gs(int nx, int ny, int nz, double h, const int bc[3], const double *fx,
               const double *fy, const double *fz, const double *b, double *x, double tol,
               int maxsweeps, double *relres) {
   size_t n = (size_t)nx * ny * nz;
@@ -367,27 +427,33 @@ int oracle_gs(int nx, int ny, int nz, double h, const int periodic[3], const dou
   double bn = sqrt(dot(n, b, b));
   int status = -1;
   for (int s = 0; s <= maxsweeps; ++s) {
-    double rn = oracle_residual(nx, ny, nz, h, periodic, fx, fy, fz, b, x, r);
+    double rn = oracle_residual(nx, ny, nz, h, bc, fx, fy, fz, b, x, r);
     if (rn <= tol * bn) { status = s; break; }
     if (s == maxsweeps) break;
     for (int k = 0; k < nz; ++k)
       for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
-          double wxm = fx[FX(i, j, k)], wxp = fx[FX(i + 1, j, k)];
-          double wym = fy[FY(i, j, k)], wyp = fy[FY(i, j + 1, k)];
-          double wzm = fz[FZ(i, j, k)], wzp = fz[FZ(i, j, k + 1)];
-          double num = wxm * x[IDX(nb(i - 1, nx, periodic[0]), j, k)] +
-                       wxp * x[IDX(nb(i + 1, nx, periodic[0]), j, k)] +
-                       wym * x[IDX(i, nb(j - 1, ny, periodic[1]), k)] +
-                       wyp * x[IDX(i, nb(j + 1, ny, periodic[1]), k)] +
-                       wzm * x[IDX(i, j, nb(k - 1, nz, periodic[2]))] +
-                       wzp * x[IDX(i, j, nb(k + 1, nz, periodic[2]))];
-          double den = wxm + wxp + wym + wyp + wzm + wzp;
+          double w[6] = {fx[FX(i, j, k)], fx[FX(i + 1, j, k)], fy[FY(i, j, k)],
+                         fy[FY(i, j + 1, k)], fz[FZ(i, j, k)], fz[FZ(i, j, k + 1)]};
+          int m[6] = {across(i - 1, nx, bc[0], 1), across(i + 1, nx, bc[0], 0),
+                      across(j - 1, ny, bc[1], 1), across(j + 1, ny, bc[1], 0),
+                      across(k - 1, nz, bc[2], 1), across(k + 1, nz, bc[2], 0)};
+          size_t nbi[6] = {IDX(m[0], j, k), IDX(m[1], j, k), IDX(i, m[2], k),
+                           IDX(i, m[3], k), IDX(i, j, m[4]), IDX(i, j, m[5])};
+          double num = 0.0, den = 0.0;
+          for (int f = 0; f < 6; ++f) {
+            if (m[f] >= 0) {
+              num += w[f] * x[nbi[f]];
+              den += w[f];
+            } else if (m[f] == -1) {
+              den += 2.0 * w[f];
+            }
+          }
           x[IDX(i, j, k)] = (num - h * h * b[IDX(i, j, k)]) / den;
         }
   }
-  oracle_remove_mean(n, x);
-  *relres = oracle_residual(nx, ny, nz, h, periodic, fx, fy, fz, b, x, r) / bn;
+  if (!any_outflow(bc)) oracle_remove_mean(n, x);
+  *relres = oracle_residual(nx, ny, nz, h, bc, fx, fy, fz, b, x, r) / bn;
   free(r);
   return status;
 }
@@ -407,17 +473,25 @@ void oracle_divergence(int nx, int ny, int nz, double h, const double *ux, const
 /*
  * Velocity correction of the projection step (Delta t = 1):
  *   u_f = u*_f - beta_f (p_b - p_a - [p]_{a->b}) / h
- * on every face between a (low) and b (high); wall faces keep u*.
+ * on every face between a (low) and b (high); wall faces keep u*.  An
+ * outflow boundary face takes the ghost value -p of its cell for the
+ * missing side (no jump: the ghost lies in the cell's fluid).
  * Updates ux, uy, uz (n+1 faces per axis) in place.
  */
-void oracle_project(int nx, int ny, int nz, double h, const int periodic[3], const double *phi,
+void oracle_project(int nx, int ny, int nz, double h, const int bc[3], const double *phi,
                     const double *kappa, const double *fx, const double *fy, const double *fz,
                     double sigma, const double *p, double *ux, double *uy, double *uz) {
+  const int periodic[3] = {PER(bc, 0), PER(bc, 1), PER(bc, 2)};
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i <= nx; ++i) {
-        if ((i == 0 || i == nx) && !periodic[0]) continue;
+        if ((i == 0 || i == nx) && !periodic[0]) {
+          if (i == 0 && DLO(bc, 0)) ux[FX(i, j, k)] -= fx[FX(i, j, k)] * (2.0 * p[IDX(0, j, k)]) / h;
+          if (i == nx && DHI(bc, 0))
+            ux[FX(i, j, k)] -= fx[FX(i, j, k)] * (-2.0 * p[IDX(nx - 1, j, k)]) / h;
+          continue;
+        }
         size_t a = IDX(i == 0 ? nx - 1 : i - 1, j, k), b = IDX(i == nx ? 0 : i, j, k);
         double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
         ux[FX(i, j, k)] -= fx[FX(i, j, k)] * (p[b] - p[a] - jp) / h;
@@ -426,7 +500,12 @@ void oracle_project(int nx, int ny, int nz, double h, const int periodic[3], con
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j <= ny; ++j)
       for (int i = 0; i < nx; ++i) {
-        if ((j == 0 || j == ny) && !periodic[1]) continue;
+        if ((j == 0 || j == ny) && !periodic[1]) {
+          if (j == 0 && DLO(bc, 1)) uy[FY(i, j, k)] -= fy[FY(i, j, k)] * (2.0 * p[IDX(i, 0, k)]) / h;
+          if (j == ny && DHI(bc, 1))
+            uy[FY(i, j, k)] -= fy[FY(i, j, k)] * (-2.0 * p[IDX(i, ny - 1, k)]) / h;
+          continue;
+        }
         size_t a = IDX(i, j == 0 ? ny - 1 : j - 1, k), b = IDX(i, j == ny ? 0 : j, k);
         double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
         uy[FY(i, j, k)] -= fy[FY(i, j, k)] * (p[b] - p[a] - jp) / h;
@@ -435,7 +514,12 @@ void oracle_project(int nx, int ny, int nz, double h, const int periodic[3], con
   for (int k = 0; k <= nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
-        if ((k == 0 || k == nz) && !periodic[2]) continue;
+        if ((k == 0 || k == nz) && !periodic[2]) {
+          if (k == 0 && DLO(bc, 2)) uz[FZ(i, j, k)] -= fz[FZ(i, j, k)] * (2.0 * p[IDX(i, j, 0)]) / h;
+          if (k == nz && DHI(bc, 2))
+            uz[FZ(i, j, k)] -= fz[FZ(i, j, k)] * (-2.0 * p[IDX(i, j, nz - 1)]) / h;
+          continue;
+        }
         size_t a = IDX(i, j, k == 0 ? nz - 1 : k - 1), b = IDX(i, j, k == nz ? 0 : k);
         double jp = face_jump(phi[a], phi[b], kappa[a], kappa[b], sigma);
         uz[FZ(i, j, k)] -= fz[FZ(i, j, k)] * (p[b] - p[a] - jp) / h;

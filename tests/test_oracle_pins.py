@@ -318,3 +318,127 @@ def test_projection_makes_velocity_divergence_free():
     div = oracle.divergence_full(fx, fy, fz, h)
     assert np.linalg.norm(div) <= 1e-10 * np.linalg.norm(rhs)
     assert np.all(fz[0] == 0.0) and np.all(fz[-1] == 0.0)
+
+
+# ---------------------------------------------------- outflow (p = 0) sides
+D, ND, DN = oracle.DIRICHLET, oracle.NEUMANN_DIRICHLET, oracle.DIRICHLET_NEUMANN
+OUT_BCS = [(P, P, D), (D, N, P), (ND, P, DN), (D, D, D), (N, DN, ND)]
+
+
+def _eig_axis_any(n, kind):
+    """_eig_axis plus the outflow kinds, from the closed forms of the 1-D
+    cell-centred second difference with p = 0 on a boundary face (ghost
+    -p): both sides sin(pi m (i+1/2)/n), m = 1..n; wall low / outflow high
+    cos(a (i+1/2)), outflow low / wall high sin(a (i+1/2)), a = (2m+1) pi/(2n)."""
+    if kind in (P, N):
+        return _eig_axis(n, kind)
+    i = np.arange(n) + 0.5
+    if kind == D:
+        m = np.arange(1, n + 1)
+        lam = 2.0 * np.cos(np.pi * m / n) - 2.0
+        V = np.sin(np.pi * np.outer(i, m) / n)
+    else:
+        a = (2 * np.arange(n) + 1) * np.pi / (2 * n)
+        lam = 2.0 * np.cos(a) - 2.0
+        V = np.cos(np.outer(i, a)) if kind == ND else np.sin(np.outer(i, a))
+    return lam, V / np.linalg.norm(V, axis=0)
+
+
+def spectral_solve_any(b, h, beta, bc):
+    """Exact discrete solution of beta * L p = b by diagonalisation (no mean
+    removal: with an outflow side L has no null space)."""
+    nz, ny, nx = b.shape
+    lx, Vx = _eig_axis_any(nx, bc[0])
+    ly, Vy = _eig_axis_any(ny, bc[1])
+    lz, Vz = _eig_axis_any(nz, bc[2])
+    bh = np.einsum("kji,ia,jb,kc->cba", b.astype(complex), Vx.conj(), Vy.conj(), Vz.conj())
+    lam = (lz[:, None, None] + ly[None, :, None] + lx[None, None, :]) * beta / (h * h)
+    assert np.abs(lam).min() > 0.0
+    return np.einsum("cba,ia,jb,kc->kji", bh / lam, Vx, Vy, Vz).real
+
+
+@pytest.mark.parametrize("bc", OUT_BCS)
+def test_outflow_constant_coefficient_matches_spectral(bc):
+    """rho_l = rho_g: beta times the 7-point Laplacian with p = 0 on the
+    outflow faces, solved exactly by sine/cosine bases; b keeps its mean."""
+    shape, h = (8, 12, 16), 1.0 / 16
+    phi = synth.level_set(shape, h, [((0.5, 0.4, 0.3), 0.2)], bc=(N, N, N))
+    rhs = rng(4).standard_normal(shape)
+    res = oracle.solve(phi, rhs, h, 0.5, 0.5, 0.0, bc, tol=1e-13)
+    assert res["iters"] >= 0 and np.array_equal(res["b"], rhs)
+    exact = spectral_solve_any(rhs, h, 2.0, bc)
+    assert np.linalg.norm(res["p"] - exact) / np.linalg.norm(exact) < 1e-10
+
+
+@pytest.mark.parametrize("bc", OUT_BCS[:3])
+def test_outflow_operator_symmetric_negative_definite(bc):
+    """With an outflow side the operator stays symmetric and becomes
+    negative definite: constants are no longer in its null space and the
+    smallest eigenvalue of -A (dense, 6x4x8 cells) is positive."""
+    shape, h = (6, 4, 8), 1.0 / 8
+    phi = synth.level_set(shape, h, [((0.4, 0.5, 0.45), 0.3)], bc=(N, N, N))
+    f = oracle.faces(phi, 1.0, 1e-3, bc)
+    n = int(np.prod(shape))
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = oracle.apply(f, e.reshape(shape), h, bc).ravel()
+    assert np.allclose(A, A.T, rtol=0, atol=1e-12 * np.abs(A).max())
+    assert np.linalg.eigvalsh(-A).min() > 0.0
+    assert np.abs(oracle.apply(f, np.ones(shape), h, bc)).max() > 0.0
+
+
+def test_outflow_flux_problem_converges_second_order():
+    """1-D in z: wall at z = 0, outflow p = 0 at z = 1, liquid below the flat
+    interface z0 and gas above, uniform source f.  Continuum: the flux
+    beta p' = f z is continuous, p(z) = -int_z^1 f s / beta(s) ds.  The
+    discrete solution (ghost-fluid faces, outflow ghost) converges at second
+    order; a p = 0 placed at the last cell centre instead of the face would
+    be first order."""
+    z0, f, rl, rg = 0.37, 1.0, 1.0, 1e-3
+    errs = []
+    for nz in (16, 32, 64):
+        h = 1.0 / nz
+        shape = (nz, 4, 4)
+        zc = (np.arange(nz) + 0.5) * h
+        phi = np.broadcast_to((zc - z0)[:, None, None], shape).copy()
+        rhs = np.full(shape, f)
+        res = oracle.solve(phi, rhs, h, rl, rg, 0.0, (P, P, ND), tol=1e-13)
+        # exact: p(z) = -int_z^1 f s beta(s)^-1 ds, beta = 1/rho
+        def P_exact(z):
+            if z >= z0:
+                return -f * rg * (1.0 - z * z) / 2.0
+            return -f * rg * (1.0 - z0 * z0) / 2.0 - f * rl * (z0 * z0 - z * z) / 2.0
+        ex = np.array([P_exact(z) for z in zc])
+        errs.append(np.max(np.abs(res["p"][:, 0, 0] - ex)) / np.max(np.abs(ex)))
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > 1.8, (errs, orders)
+
+
+def test_outflow_solvers_agree_and_projection_is_divergence_free():
+    """A bubble under an outflow top: Jacobi-PCG, Gauss-Seidel and a dense
+    direct solve give one pressure; the velocity correction, outflow faces
+    included, leaves a divergence equal to the residual (~1e-12 of div u*)."""
+    shape, h = (8, 8, 8), 1.0 / 8
+    bc = (P, P, ND)
+    phi = synth.level_set(shape, h, [((0.5, 0.5, 0.5), 0.3)], bc=bc)
+    u = synth.velocity(3, shape, h, bc=(P, P, N))
+    rhs = oracle.divergence(*u, h)
+    res = oracle.solve(phi, rhs, h, 1.0, 1e-3, 0.02, bc, tol=1e-13)
+    xg, sweeps, rel = oracle.gs(res["faces"], res["b"], h, bc, tol=1e-11, maxsweeps=200000)
+    assert sweeps >= 0
+    assert np.linalg.norm(xg - res["p"]) / np.linalg.norm(res["p"]) < 1e-9
+    n = int(np.prod(shape))
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = oracle.apply(res["faces"], e.reshape(shape), h, bc).ravel()
+    xd = np.linalg.solve(A, res["b"].ravel()).reshape(shape)
+    assert np.linalg.norm(xd - res["p"]) / np.linalg.norm(xd) < 1e-10
+    fx, fy, fz = oracle.project(phi, res["kappa"], res["faces"], res["p"], *u, h, 0.02, bc)
+    div = oracle.divergence_full(fx, fy, fz, h)
+    assert np.linalg.norm(div) <= 1e-10 * np.linalg.norm(rhs)
+    assert np.all(fz[0] == 0.0)          # wall bottom keeps u* = 0
+    assert np.abs(fz[-1]).max() > 0.0    # the outflow top carries the flux out
