@@ -51,7 +51,22 @@ typedef enum {
   MP_ERR_NO_NET = 7         /* learned initial guess requested without weights */
 } mp_status;
 
-typedef enum { MP_BC_PERIODIC = 0, MP_BC_NEUMANN = 1 } mp_bc; /* Neumann = zero-flux wall */
+/* Boundary type of an axis (per side where it differs).  The paper sets the
+ * boundary types per side (xl_boundary_type / xr_boundary_type: inflow_ins,
+ * outflow_ins in its runtime-parameter TOML figure, Section 4).  For the
+ * pressure: a wall or an inflow side prescribes the normal velocity, so the
+ * pressure correction has no normal gradient there (Neumann: the face
+ * carries no pressure flux); an outflow side holds p = 0 on the boundary
+ * face (Dirichlet, an antisymmetric ghost p_ghost = -p_cell whose face
+ * coefficient is 1/rho of the cell's fluid).  With an outflow side the
+ * operator has no null space: b keeps its mean and p is not gauged. */
+typedef enum {
+  MP_BC_PERIODIC = 0,          /* periodic (even number of cells) */
+  MP_BC_NEUMANN = 1,           /* wall or inflow on both sides */
+  MP_BC_DIRICHLET = 2,         /* outflow on both sides */
+  MP_BC_NEUMANN_DIRICHLET = 3, /* wall/inflow on the low side, outflow on the high side */
+  MP_BC_DIRICHLET_NEUMANN = 4  /* outflow on the low side, wall/inflow on the high side */
+} mp_bc;
 
 typedef struct {
   int nx, ny, nz;
@@ -86,8 +101,10 @@ typedef struct {
   int deflate;       /* method 0: 1 (default) deflates CG by the indicator vectors of the
                         connected gas components (phi > 0), removing the bubbles' pressure
                         levels, which the V-cycle resolves poorly at density ratio 1000;
-                        0 = plain MG-preconditioned CG.  Same converged answer. */
-  int smoother;      /* FP32 V-cycle levels (mixed precision) with nx a multiple of 8:
+                        0 = plain MG-preconditioned CG.  Same converged answer.  Applies to
+                        periodic and wall boundaries (off with an outflow side). */
+  int smoother;      /* FP32 V-cycle levels (mixed precision) with nx a multiple of 8 and
+                        no outflow side:
                         1 (default) = one fused pass per red-black sweep (both colours,
                         shared-memory halo staging, second iterate buffer); 0 = one
                         in-place launch per colour.  Bitwise the same result. */
@@ -162,7 +179,8 @@ mp_status mp_poisson_set_opts(mp_handle hd, const mp_opts *opts);
  * Defines: the pressure Poisson solve of the projection step
  * (Grid_solvePoisson, Section 3; fractional-step projection, Section 2).
  *
- * Solve A p = b with b = rhs + J - mean, to ||b - A p|| <= tol ||b||.
+ * Solve A p = b with b = rhs + J - mean, to ||b - A p|| <= tol ||b|| (with an
+ * outflow side b = rhs + J keeps its mean and p is not gauged).
  * rhs_dev: device, N f64 (e.g. div u*).  p_dev: device, N f64, in/out
  * (read only if initial_guess = 1), mean-free on exit.  iterations (may be
  * NULL) gets mp_stats.iterations.  res_hist (host, may be NULL) gets up to
@@ -185,6 +203,13 @@ mp_status mp_poisson_solve(mp_handle hd, const double *rhs_dev, double *p_dev, d
  * mp_poisson_solve, then correct the face velocities in place,
  * u = u* - beta (grad_h p - [p]).  ux/uy/uz_dev: device, N f64 each
  * (low-face ownership), in/out.  p_dev as in mp_poisson_solve.
+ * The low-face-owned layout stores one boundary face per non-periodic axis
+ * (shared by both walls), so this call, mp_poisson_project_step_host,
+ * mp_poisson_divergence and mp_poisson_project serve periodic and wall
+ * boundaries; with an outflow side they return MP_ERR_INVALID_ARG (form
+ * the divergence with your boundary velocities and call mp_poisson_solve;
+ * an outflow face's velocity is corrected by -2 beta p_cell / h on a low
+ * side, +2 beta p_cell / h on a high side, beta = 1/rho of the cell).
  */
 mp_status mp_poisson_project_step(mp_handle hd, double *ux_dev, double *uy_dev, double *uz_dev,
                                   double *p_dev, double tol, int *iterations);
@@ -234,8 +259,9 @@ mp_status mp_poisson_project(mp_handle hd, const double *p_dev, double *ux_dev, 
  * Copy setup fields out (device pointers, each N f64; any may be NULL):
  * curvature kappa (evaluated in the interface band -- cells with a face
  * neighbour of the other fluid -- and 0 elsewhere), face coefficients
- * beta_x/y/z (low-face ownership, wall faces 0), jump source J (unscaled,
- * sums to zero). */
+ * beta_x/y/z (low-face ownership, boundary faces of non-periodic axes 0;
+ * an outflow face's coefficient is 1/rho of its cell's fluid), jump
+ * source J (unscaled, sums to zero). */
 mp_status mp_poisson_get_fields(mp_handle hd, double *kappa_dev, double *bx_dev, double *by_dev,
                                 double *bz_dev, double *J_dev);
 

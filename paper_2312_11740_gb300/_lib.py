@@ -23,6 +23,9 @@ MP_NOALLOC_MAX_CELLS = 134217728
 
 MP_BC_PERIODIC = 0
 MP_BC_NEUMANN = 1
+MP_BC_DIRICHLET = 2
+MP_BC_NEUMANN_DIRICHLET = 3
+MP_BC_DIRICHLET_NEUMANN = 4
 
 
 class mp_grid(ctypes.Structure):

@@ -615,7 +615,7 @@ __global__ void k_defl_resid_band(const int *__restrict__ band, int nband,
     const size_t c = (size_t)band[e];
     int i, j, k;
     cell_ijk(d, c, i, j, k);
-    const double res = p ? resid_at<double>(p, b, bx, by, bz, diag, d, i, j, k) : b[c];
+    const double res = p ? resid_at<double>(p, b, bx, by, bz, diag, nullptr, d, i, j, k) : b[c];
     r32[c] = (float)(res - band_aw(bx, by, bz, comp, d, c, i, j, k, coef));
   }
 }

@@ -188,21 +188,54 @@ __global__ void k_jump(const double *__restrict__ phi, const double *__restrict_
   Jt[c] = s;
 }
 
-// diag = sum of the six face betas (always); MODE & 1: idiag = 1/diag (the
-// FP64 smoother); MODE & 2: FP32 faces and 1/diag (CG operator, one-CTA tail)
-// and the FP16 faces of the FP32 V-cycle, stored as beta * fs
+// Outflow boundary sides of a level: per side (x low, x high, y low, y
+// high, z low, z high) the coefficients of the boundary faces as a plane
+// (x sides: j + ny k; y sides: i + nx k; z sides: i + nx j), or null.
+struct BndPlanes {
+  const double *p[6];
+};
+// 2 beta_b summed over the outflow faces of cell (i, j, k): the ghost value
+// -x_c turns a face's term beta_b (x_ghost - x_c) into -2 beta_b x_c
+__device__ __forceinline__ double outflow_diag(const BndPlanes &bp, const Dims &d, int i, int j,
+                                               int k) {
+  double s = 0.0;
+  if (i == 0 && bp.p[0]) s += 2.0 * bp.p[0][j + d.ny * k];
+  if (i == d.nx - 1 && bp.p[1]) s += 2.0 * bp.p[1][j + d.ny * k];
+  if (j == 0 && bp.p[2]) s += 2.0 * bp.p[2][i + d.nx * k];
+  if (j == d.ny - 1 && bp.p[3]) s += 2.0 * bp.p[3][i + d.nx * k];
+  if (k == 0 && bp.p[4]) s += 2.0 * bp.p[4][i + d.nx * j];
+  if (k == d.nz - 1 && bp.p[5]) s += 2.0 * bp.p[5][i + d.nx * j];
+  return s;
+}
+
+// diag = sum of the six face betas (always), plus the outflow diagonal when
+// dd is not null (stored in dd, and as FP32 / scaled FP16 copies with MODE
+// & 2); MODE & 1: idiag = 1/diag (the FP64 smoother); MODE & 2: FP32 faces
+// and 1/diag (CG operator, one-CTA tail) and the FP16 faces of the FP32
+// V-cycle, stored as beta * fs
 template <int MODE>
 __global__ void k_diag(const double *__restrict__ bx, const double *__restrict__ by,
                        const double *__restrict__ bz, double *__restrict__ diag,
                        double *__restrict__ idiag, float *__restrict__ bx32,
                        float *__restrict__ by32, float *__restrict__ bz32,
                        float *__restrict__ idiag32, __half *__restrict__ bx16,
-                       __half *__restrict__ by16, __half *__restrict__ bz16, float fs, Dims d) {
+                       __half *__restrict__ by16, __half *__restrict__ bz16, float fs, Dims d,
+                       BndPlanes bp, double *__restrict__ dd, float *__restrict__ dd32,
+                       __half *__restrict__ dd16) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
   double s = bx[c] + bx[at(d, whi(i, d.nx), j, k)] + by[c] + by[at(d, i, whi(j, d.ny), k)] + bz[c] +
              bz[at(d, i, j, whi(k, d.nz))];
+  if (dd) {
+    const double o = outflow_diag(bp, d, i, j, k);
+    dd[c] = o;
+    s += o;
+    if (MODE & 2) {
+      dd32[c] = (float)o;
+      dd16[c] = __float2half_rn((float)o * fs * 0.25f);  // see dd_h
+    }
+  }
   diag[c] = s;
   if (MODE & 1) {
     // 1/s: FP32 reciprocal refined by one Newton step in FP64 (relative error
@@ -241,17 +274,18 @@ __global__ void k_coarsen_faces(const double *__restrict__ fx, const double *__r
 }
 
 // ---------------------------------------------- A9: coarsest direct solve
-// Dense M = -At + 11^T/n (symmetric positive definite) as the left half of
-// [M | I] (row-major, n x 2n); one thread per row, each row written once.
+// Dense M = -At + 11^T/n (symmetric positive definite; the 11^T/n term only
+// for a singular operator) as the left half of [M | I] (row-major, n x 2n);
+// one thread per row, each row written once.
 __global__ void k_dense_build(const double *__restrict__ bx, const double *__restrict__ by,
                               const double *__restrict__ bz, const double *__restrict__ diag,
-                              double *__restrict__ M, Dims d) {
+                              double *__restrict__ M, Dims d, int singular) {
   int n = d.nx * d.ny * d.nz;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int i = r % d.nx, j = (r / d.nx) % d.ny, k = r / (d.nx * d.ny);
   double *row = M + (size_t)r * 2 * n;
-  double inv_n = 1.0 / n;
+  double inv_n = singular ? 1.0 / n : 0.0;
   for (int c = 0; c < n; ++c) row[c] = inv_n;
   for (int c = 0; c < n; ++c) row[n + c] = (c == r) ? 1.0 : 0.0;
   row[r] += diag[r];
@@ -332,18 +366,19 @@ __global__ void k_inverse_cols(const double *__restrict__ Maug, double *__restri
   for (int r = tid; r < n; r += nt) Minv[(size_t)r * n + j] = y[r];
 }
 
-// e = M^-1 (-(b - mean b)), FP64 internally for any storage type T.
-// One block of 512 threads; n <= 512.
+// e = M^-1 (-(b - mean b)), FP64 internally for any storage type T (the
+// mean is removed only for a singular operator).  One block of 512
+// threads; n <= 512.
 template <typename T>
 __global__ void k_coarse_solve(const double *__restrict__ Minv, const T *__restrict__ b,
-                               T *__restrict__ e, int n) {
+                               T *__restrict__ e, int n, int singular) {
   griddep_wait();
   __shared__ double sb[512];
   __shared__ double mean;
   int t = threadIdx.x;
   double v = t < n ? (double)b[t] : 0.0;
   double s = block_sum(v);
-  if (t == 0) mean = s / n;
+  if (t == 0) mean = singular ? s / n : 0.0;
   __syncthreads();
   sb[t] = t < n ? v - mean : 0.0;
   __syncthreads();
@@ -400,11 +435,14 @@ __global__ void k_rbgs(T *__restrict__ x, const T *__restrict__ b, const T *__re
 // operations; FP64 keeps ~13 digits after the cancellation at density
 // ratio 1e3).  FP32: sum_f beta_f (x_nb - x_c): differences first, so the
 // cancellation between the beta ~ 1e3 terms of a gas cell does not eat the
-// 7-digit FP32 mantissa.
+// 7-digit FP32 mantissa.  dd (may be null): the diagonal of the outflow
+// faces of the cell (2 beta_b per outflow face: the ghost value -x_c),
+// subtracted in the difference form (the stored diag already holds it).
 template <typename T>
 __device__ __forceinline__ T op_at(const T *__restrict__ x, const T *__restrict__ bx,
                                    const T *__restrict__ by, const T *__restrict__ bz,
-                                   const T *__restrict__ diag, const Dims &d, int i, int j, int k) {
+                                   const T *__restrict__ diag, const T *__restrict__ dd,
+                                   const Dims &d, int i, int j, int k) {
   size_t c = at(d, i, j, k);
   size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
   size_t yl = at(d, i, wlo(j, d.ny), k), yh = at(d, i, whi(j, d.ny), k);
@@ -426,6 +464,7 @@ __device__ __forceinline__ T op_at(const T *__restrict__ x, const T *__restrict_
     s = fma(by[yh], x[yh] - xc, s);
     s = fma(bz[c], x[zl] - xc, s);
     s = fma(bz[zh], x[zh] - xc, s);
+    if (dd) s = fma(-dd[c], xc, s);
     return s;
   }
 }
@@ -435,8 +474,9 @@ template <typename T>
 __device__ __forceinline__ T resid_at(const T *__restrict__ x, const T *__restrict__ b,
                                       const T *__restrict__ bx, const T *__restrict__ by,
                                       const T *__restrict__ bz, const T *__restrict__ diag,
-                                      const Dims &d, int i, int j, int k) {
-  return b[at(d, i, j, k)] - op_at(x, bx, by, bz, diag, d, i, j, k);
+                                      const T *__restrict__ dd, const Dims &d, int i, int j,
+                                      int k) {
+  return b[at(d, i, j, k)] - op_at(x, bx, by, bz, diag, dd, d, i, j, k);
 }
 
 
@@ -453,19 +493,22 @@ constexpr int TAIL_THREADS = 1024;
 struct TailLevel {
   Dims d;
   int n, nu1, nu2;
-  int off;  // element offset of the level's six arrays in shared memory
+  int off;  // element offset of the level's arrays in shared memory
   const void *bx, *by, *bz, *idiag;
+  const void *dd;  // outflow diagonal (null without outflow sides)
 };
 struct TailArgs {
   int nlev;  // levels in the tail (the last one is the coarsest)
   TailLevel lv[TAIL_MAX_LEVELS];
   const double *Minv;
+  int singular;  // the operator annihilates constants: mean-project the coarsest rhs
 };
 
-// shared-memory arrays of one tail level: x, b, bx, by, bz, 1/diag
+// shared-memory arrays of one tail level: x, b, bx, by, bz, 1/diag, and the
+// outflow diagonal when the level has one
 template <typename T>
 struct TailView {
-  T *x, *b, *wx, *wy, *wz, *id;
+  T *x, *b, *wx, *wy, *wz, *id, *dd;
   __device__ TailView(T *base, const TailLevel &l) {
     x = base + l.off;
     b = x + l.n;
@@ -473,6 +516,7 @@ struct TailView {
     wy = wx + l.n;
     wz = wy + l.n;
     id = wz + l.n;
+    dd = l.dd ? id + l.n : nullptr;
   }
 };
 
@@ -515,11 +559,13 @@ k_tail(TailArgs a, const T *__restrict__ rhs, T *__restrict__ xout) {
     TailView<T> v(base, a.lv[l]);
     const T *gx = (const T *)a.lv[l].bx, *gy = (const T *)a.lv[l].by, *gz = (const T *)a.lv[l].bz,
             *gi = (const T *)a.lv[l].idiag;
+    const T *gd = (const T *)a.lv[l].dd;
     for (int e = threadIdx.x; e < a.lv[l].n; e += TAIL_THREADS) {
       v.wx[e] = gx[e];
       v.wy[e] = gy[e];
       v.wz[e] = gz[e];
       v.id[e] = gi[e];
+      if (gd) v.dd[e] = gd[e];
     }
   }
   {
@@ -542,8 +588,8 @@ k_tail(TailArgs a, const T *__restrict__ rhs, T *__restrict__ xout) {
       const int I = e % dc.nx, J = (e / dc.nx) % dc.ny, K = e / (dc.nx * dc.ny);
       T sum = 0;
       for (int q = 0; q < 8; ++q)
-        sum += resid_at(v.x, v.b, v.wx, v.wy, v.wz, (const T *)nullptr, d, 2 * I + (q & 1),
-                        2 * J + ((q >> 1) & 1), 2 * K + (q >> 2));
+        sum += resid_at(v.x, v.b, v.wx, v.wy, v.wz, (const T *)nullptr, (const T *)v.dd, d,
+                        2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + (q >> 2));
       vc.b[e] = (T)0.5 * sum;
     }
     __syncthreads();
@@ -555,7 +601,7 @@ k_tail(TailArgs a, const T *__restrict__ rhs, T *__restrict__ xout) {
     double acc0 = 0.0;
     for (int e = threadIdx.x; e < n; e += TAIL_THREADS) acc0 += (double)v.b[e];
     double sum = block_sum(acc0);
-    if (threadIdx.x == 0) mean_s = sum / n;
+    if (threadIdx.x == 0) mean_s = a.singular ? sum / n : 0.0;
     __syncthreads();
     const double m = mean_s;
     for (int r = threadIdx.x; r < n; r += TAIL_THREADS) {
@@ -600,7 +646,7 @@ __device__ __forceinline__ void resid_restrict_cell(const T *__restrict__ x,
   T s = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    s += resid_at(x, b, bx, by, bz, diag, df, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1),
+    s += resid_at(x, b, bx, by, bz, diag, (const T *)nullptr, df, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1),
                   2 * K + (q >> 2));
   bc[at(dc, I, J, K)] = (T)0.5 * s;
 }
@@ -620,11 +666,19 @@ __device__ __forceinline__ float hf(const __half *__restrict__ p, size_t i) {
 
 // new value of one cell of a red-black half-sweep (loads only):
 // x_c = (sum_f w_f x_nb - fs bt_c) / sum_f w_f with w = fs beta
+// The FP16 outflow diagonal is stored as fs/4 times its value: up to six
+// outflow faces of 2 beta fs <= 2^15 each stay below the FP16 maximum; the
+// power-of-two factor is exact.
+__device__ __forceinline__ float dd_h(const __half *__restrict__ dd16, size_t c) {
+  return 4.f * __half2float(dd16[c]);
+}
+
 __device__ __forceinline__ float rbgs_h_val(const float *__restrict__ x,
                                             const float *__restrict__ b,
                                             const __half *__restrict__ hx,
                                             const __half *__restrict__ hy,
-                                            const __half *__restrict__ hz, const Dims &d, int i,
+                                            const __half *__restrict__ hz,
+                                            const __half *__restrict__ dd16, const Dims &d, int i,
                                             int j, int k, int zero, float fs) {
   const size_t c = at(d, i, j, k);
   const size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
@@ -641,19 +695,23 @@ __device__ __forceinline__ float rbgs_h_val(const float *__restrict__ x,
     s = fmaf(wzl, x[zl], s);
     s = fmaf(wzh, x[zh], s);
   }
-  return __fdividef(s, ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh));
+  float den = ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh);
+  if (dd16) den += dd_h(dd16, c);
+  return __fdividef(s, den);
 }
 
 // red-black half-sweep on the FP16 faces (one cell of the colour per thread;
-// two planes per thread measured slower: fewer resident warps)
+// two planes per thread measured slower: fewer resident warps); dd16: the
+// outflow diagonal scaled by fs, or null
 __global__ void k_rbgs_h(float *__restrict__ x, const float *__restrict__ b,
                          const __half *__restrict__ hx, const __half *__restrict__ hy,
-                         const __half *__restrict__ hz, Dims d, int colour, int zero, float fs) {
+                         const __half *__restrict__ hz, const __half *__restrict__ dd16, Dims d,
+                         int colour, int zero, float fs) {
   griddep_wait();
   const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (t >= (d.nx >> 1) || j >= d.ny) return;
   const int i = 2 * t + ((j + k + colour) & 1);
-  x[at(d, i, j, k)] = rbgs_h_val(x, b, hx, hy, hz, d, i, j, k, zero, fs);
+  x[at(d, i, j, k)] = rbgs_h_val(x, b, hx, hy, hz, dd16, d, i, j, k, zero, fs);
 }
 
 // The same half-sweep with 16-byte rows (nx a multiple of 4, 16-byte aligned
@@ -674,7 +732,8 @@ __device__ __forceinline__ float f4_at(const float4 &v, int q) {
 
 __global__ void k_rbgs_h4(float *__restrict__ x, const float *__restrict__ b,
                           const __half *__restrict__ hx, const __half *__restrict__ hy,
-                          const __half *__restrict__ hz, Dims d, int colour, int zero, float fs) {
+                          const __half *__restrict__ hz, const __half *__restrict__ dd16, Dims d,
+                          int colour, int zero, float fs) {
   griddep_wait();
   const int qx = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (qx >= (d.nx >> 2) || j >= d.ny) return;
@@ -718,7 +777,9 @@ __global__ void k_rbgs_h4(float *__restrict__ x, const float *__restrict__ b,
       s = fmaf(wzl, f4_at(xzl, q), s);
       s = fmaf(wzh, f4_at(xzh, q), s);
     }
-    v[e] = __fdividef(s, ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh));
+    float den = ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh);
+    if (dd16) den += dd_h(dd16, c0 + q);
+    v[e] = __fdividef(s, den);
   }
   x[c0 + o] = v[0];
   x[c0 + o + 2] = v[1];
@@ -728,7 +789,8 @@ __global__ void k_rbgs_h4(float *__restrict__ x, const float *__restrict__ b,
 __device__ __forceinline__ float resid_h(const float *__restrict__ x, const float *__restrict__ b,
                                          const __half *__restrict__ hx,
                                          const __half *__restrict__ hy,
-                                         const __half *__restrict__ hz, float inv_fs,
+                                         const __half *__restrict__ hz,
+                                         const __half *__restrict__ dd16, float inv_fs,
                                          const Dims &d, int i, int j, int k) {
   const size_t c = at(d, i, j, k);
   const size_t xl = at(d, wlo(i, d.nx), j, k), xh = at(d, whi(i, d.nx), j, k);
@@ -741,21 +803,22 @@ __device__ __forceinline__ float resid_h(const float *__restrict__ x, const floa
   s = fmaf(hf(hy, yh), x[yh] - xc, s);
   s = fmaf(hf(hz, c), x[zl] - xc, s);
   s = fmaf(hf(hz, zh), x[zh] - xc, s);
+  if (dd16) s = fmaf(-dd_h(dd16, c), xc, s);
   return b[c] - s * inv_fs;
 }
 
 // residual + restriction (half the sum of the 8 children) on the FP16 faces
 __global__ void k_resid_restrict_h(const float *__restrict__ x, const float *__restrict__ b,
                                    const __half *__restrict__ hx, const __half *__restrict__ hy,
-                                   const __half *__restrict__ hz, float inv_fs, Dims df,
-                                   float *__restrict__ bc, Dims dc) {
+                                   const __half *__restrict__ hz, const __half *__restrict__ dd16,
+                                   float inv_fs, Dims df, float *__restrict__ bc, Dims dc) {
   griddep_wait();
   const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
   if (I >= dc.nx || J >= dc.ny) return;
   float s = 0.f;
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    s += resid_h(x, b, hx, hy, hz, inv_fs, df, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1),
+    s += resid_h(x, b, hx, hy, hz, dd16, inv_fs, df, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1),
                  2 * K + (q >> 2));
   bc[at(dc, I, J, K)] = 0.5f * s;
 }
@@ -765,7 +828,8 @@ __global__ void k_resid_restrict_h(const float *__restrict__ x, const float *__r
 __device__ __forceinline__ void resid_h4(const float *__restrict__ x, const float *__restrict__ b,
                                          const __half *__restrict__ hx,
                                          const __half *__restrict__ hy,
-                                         const __half *__restrict__ hz, float inv_fs,
+                                         const __half *__restrict__ hz,
+                                         const __half *__restrict__ dd16, float inv_fs,
                                          const Dims &d, int i0, int j, int k, float r[4]) {
   const size_t c0 = at(d, i0, j, k);
   const size_t cyl = at(d, i0, wlo(j, d.ny), k), cyh = at(d, i0, whi(j, d.ny), k);
@@ -793,6 +857,7 @@ __device__ __forceinline__ void resid_h4(const float *__restrict__ x, const floa
     s = fmaf(h4_at(fyh, q), f4_at(xyh, q) - v, s);
     s = fmaf(h4_at(fz, q), f4_at(xzl, q) - v, s);
     s = fmaf(h4_at(fzh, q), f4_at(xzh, q) - v, s);
+    if (dd16) s = fmaf(-dd_h(dd16, c0 + q), v, s);
     r[q] = f4_at(bb, q) - s * inv_fs;
   }
 }
@@ -802,15 +867,15 @@ __device__ __forceinline__ void resid_h4(const float *__restrict__ x, const floa
 // of each of its four fine rows; children summed in k_resid_restrict_h's order
 __global__ void k_resid_restrict_h4(const float *__restrict__ x, const float *__restrict__ b,
                                     const __half *__restrict__ hx, const __half *__restrict__ hy,
-                                    const __half *__restrict__ hz, float inv_fs, Dims df,
-                                    float *__restrict__ bc, Dims dc) {
+                                    const __half *__restrict__ hz, const __half *__restrict__ dd16,
+                                    float inv_fs, Dims df, float *__restrict__ bc, Dims dc) {
   griddep_wait();
   const int m = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
   if (m >= (df.nx >> 2) || J >= dc.ny) return;
   float s0 = 0.f, s1 = 0.f, r[4];
 #pragma unroll
   for (int row = 0; row < 4; ++row) {  // (dj, dk) = (0,0), (1,0), (0,1), (1,1)
-    resid_h4(x, b, hx, hy, hz, inv_fs, df, 4 * m, 2 * J + (row & 1), 2 * K + (row >> 1), r);
+    resid_h4(x, b, hx, hy, hz, dd16, inv_fs, df, 4 * m, 2 * J + (row & 1), 2 * K + (row >> 1), r);
     s0 += r[0];
     s0 += r[1];
     s1 += r[2];
@@ -881,15 +946,15 @@ enum { OP_STORE = 0, OP_ALPHA, OP_BETA, OP_MEAN };
 template <typename T>
 __global__ void k_apply_dot(const T *__restrict__ dv, T *__restrict__ q, const T *__restrict__ bx,
                             const T *__restrict__ by, const T *__restrict__ bz,
-                            const T *__restrict__ diag, Dims d, int zper,
-                            double *__restrict__ partial) {
+                            const T *__restrict__ diag, const T *__restrict__ dd, Dims d,
+                            int zper, double *__restrict__ partial) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
   T acc = 0;
   if (i < d.nx && j < d.ny)
     for (int k = k0; k < k1; ++k) {
       size_t c = at(d, i, j, k);
-      T s = op_at(dv, bx, by, bz, diag, d, i, j, k);
+      T s = op_at(dv, bx, by, bz, diag, dd, d, i, j, k);
       q[c] = s;
       acc = fma(s, dv[c], acc);
     }
@@ -902,8 +967,8 @@ __global__ void k_apply_dot(const T *__restrict__ dv, T *__restrict__ q, const T
 // 4-cell x-chunk in each of its zper planes and loads it as vectors
 __global__ void __launch_bounds__(BX * BY)
 k_apply_dot4(const float *__restrict__ dv, float *__restrict__ q, const float *__restrict__ bx,
-             const float *__restrict__ by, const float *__restrict__ bz, Dims d, int zper,
-             double *__restrict__ partial) {
+             const float *__restrict__ by, const float *__restrict__ bz,
+             const float *__restrict__ dd32, Dims d, int zper, double *__restrict__ partial) {
   const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   const int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
   float acc = 0.f;
@@ -936,6 +1001,7 @@ k_apply_dot4(const float *__restrict__ dv, float *__restrict__ q, const float *_
         s = fmaf(f4_at(fyh, e), f4_at(xyh, e) - v, s);
         s = fmaf(f4_at(fz, e), f4_at(xzl, e) - v, s);
         s = fmaf(f4_at(fzh, e), f4_at(xzh, e) - v, s);
+        if (dd32) s = fmaf(-dd32[c0 + e], v, s);
         if (e == 0) out.x = s; else if (e == 1) out.y = s; else if (e == 2) out.z = s; else out.w = s;
         acc = fmaf(s, v, acc);
       }
@@ -951,13 +1017,14 @@ __global__ void k_residual(const T *__restrict__ x, const T *__restrict__ b, T *
                            const T *__restrict__ bx, const T *__restrict__ by,
                            const T *__restrict__ bz, const T *__restrict__ diag, Dims d, int zper,
                            double *__restrict__ partial, int zero) {
+  const T *dd = nullptr;  // diag holds the outflow diagonal
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
   double acc = 0.0;
   if (i < d.nx && j < d.ny)
     for (int k = k0; k < k1; ++k) {
       size_t c = at(d, i, j, k);
-      T v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, d, i, j, k);
+      T v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, dd, d, i, j, k);
       r[c] = v;
       acc = fma((double)v, (double)v, acc);
     }
@@ -977,7 +1044,7 @@ __global__ void k_residual_mixed(const double *__restrict__ x, const double *__r
   if (i < d.nx && j < d.ny)
     for (int k = k0; k < k1; ++k) {
       size_t c = at(d, i, j, k);
-      double v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, d, i, j, k);
+      double v = zero ? b[c] : resid_at(x, b, bx, by, bz, diag, (const double *)nullptr, d, i, j, k);
       r32[c] = (float)v;
       acc = fma(v, v, acc);
     }
@@ -1264,6 +1331,35 @@ __global__ void k_project(const double *__restrict__ p, const double *__restrict
   ux[c] = fma(-bx[c] * ih, dx, ux[c]);
   uy[c] = fma(-by[c] * ih, dy, uy[c]);
   uz[c] = fma(-bz[c] * ih, dz, uz[c]);
+}
+
+// ------------------------------------------------ outflow boundary planes
+// Finest level: the coefficient of every outflow boundary face, 1/rho of the
+// fluid of the cell next to it (its ghost lies in that fluid).  side: 0..5
+// (x low, x high, y low, y high, z low, z high); the plane layout as in
+// BndPlanes.
+__global__ void k_bnd_init(const double *__restrict__ phi, double *__restrict__ plane, Dims d,
+                           int side, double irl, double irg) {
+  const int axis = side >> 1, hi = side & 1;
+  const int na = axis == 0 ? d.ny : d.nx, nb = axis == 2 ? d.ny : d.nz;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= na * nb) return;
+  const int u = e % na, v = e / na;
+  int i, j, k;
+  if (axis == 0) { i = hi ? d.nx - 1 : 0; j = u; k = v; }
+  else if (axis == 1) { j = hi ? d.ny - 1 : 0; i = u; k = v; }
+  else { k = hi ? d.nz - 1 : 0; i = u; j = v; }
+  plane[e] = gas(phi[at(d, i, j, k)]) ? irg : irl;
+}
+
+// A coarse boundary face is the mean of the four fine faces that tile it.
+__global__ void k_bnd_coarsen(const double *__restrict__ fine, double *__restrict__ coarse,
+                              int na, int nb) {  // coarse plane na x nb, fine 2na x 2nb
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= na * nb) return;
+  const int u = e % na, v = e / na, fa = 2 * na;
+  coarse[e] = 0.25 * (fine[2 * u + fa * 2 * v] + fine[2 * u + 1 + fa * 2 * v] +
+                      fine[2 * u + fa * (2 * v + 1)] + fine[2 * u + 1 + fa * (2 * v + 1)]);
 }
 
 // y = scale * v (used to unscale J and the operator for the test API)

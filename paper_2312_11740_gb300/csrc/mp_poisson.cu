@@ -40,6 +40,12 @@ struct Level {
   float *b32 = nullptr, *e32 = nullptr;
   float *t32 = nullptr;  // second FP32 iterate of the fused sweep (levels it runs on)
   int ftx = 0, fty = 0, fchunk = 0;  // fused sweep grid: tiles in x, y; z-chunks
+  // outflow sides: the boundary-face coefficients per side (planes, null for
+  // other sides) and the per-cell outflow diagonal (null without outflow)
+  double *bnd[6] = {};
+  double *dd = nullptr;
+  float *dd32 = nullptr;
+  __half *dd16 = nullptr;
 };
 
 enum KernelId {
@@ -77,6 +83,7 @@ struct Pending {
 struct mp_poisson {
   mp_grid g{};
   int per = 0;
+  int outflow = 0;  // bits 2a (low) and 2a+1 (high): outflow (p = 0) sides of axis a
   double h = 1.0, rho_l = 1.0, rho_g = 1.0, sigma = 0.0;
   mp_opts opts{};
   cudaStream_t st = nullptr;
@@ -313,6 +320,7 @@ template <> struct LV<double> {
   static double *idiag(Level &l) { return l.idiag; }
   static double *b(Level &l) { return l.b; }
   static double *e(Level &l) { return l.e; }
+  static double *dd(Level &l) { return l.dd; }
 };
 template <> struct LV<float> {
   static float *bx(Level &l) { return l.bx32; }
@@ -322,6 +330,7 @@ template <> struct LV<float> {
   static float *idiag(Level &l) { return l.idiag32; }
   static float *b(Level &l) { return l.b32; }
   static float *e(Level &l) { return l.e32; }
+  static float *dd(Level &l) { return l.dd32; }
 };
 
 // One symmetric V-cycle with zero initial guess: x ~= At^-1 rhs on level l.
@@ -337,6 +346,7 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
     TailArgs a{};
     a.nlev = (int)hd->L.size() - l;
     a.Minv = hd->Minv;
+    a.singular = hd->outflow == 0;
     double bytes = 0.0;
     int off = 0;
     // the FP32 tail (levels <= 16^3, latency-bound at about a microsecond per
@@ -347,8 +357,9 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
     for (int q = 0; q < a.nlev; ++q) {
       Level &t = hd->L[l + q];
       a.lv[q] = TailLevel{t.d, (int)t.n, std::min(t.nu1, cap), std::min(t.nu2, cap), off,
-                          LV<T>::bx(t), LV<T>::by(t), LV<T>::bz(t), LV<T>::idiag(t)};
-      off += 6 * (int)t.n;
+                          LV<T>::bx(t), LV<T>::by(t), LV<T>::bz(t), LV<T>::idiag(t),
+                          LV<T>::dd(t)};
+      off += (hd->outflow ? 7 : 6) * (int)t.n;
       bytes += 4.0 * t.n * sizeof(T);
     }
     size_t smem = sizeof(T) == 8 ? hd->tail64_bytes : hd->tail32_bytes;
@@ -358,7 +369,7 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
   }
   if (l == (int)hd->L.size() - 1) {
     LAUNCH_PDL(hd, kid<T>(K_COARSE64, K_COARSE32), l, lv.n * (lv.n * 8.0 + 2.0 * sizeof(T)),
-               k_coarse_solve<T>, 1, 512, 0, hd->Minv, rhs, x, (int)lv.n);
+               k_coarse_solve<T>, 1, 512, 0, hd->Minv, rhs, x, (int)lv.n, hd->outflow == 0 ? 1 : 0);
     return launch_ok();
   }
   Level &lc = hd->L[l + 1];
@@ -377,10 +388,11 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
         if (lv.d.nx % 4 == 0)  // 16-byte rows (level buffers are 256-byte aligned)
           LAUNCH_PDL(hd, krb, l, bytes, k_rbgs_h4,
                      dim3((lv.d.nx / 4 + BX - 1) / BX, (lv.d.ny + BY - 1) / BY, lv.d.nz), kBlock,
-                     0, x, rhs, lv.bx16, lv.by16, lv.bz16, lv.d, colour, zero, hd->fs16);
+                     0, x, rhs, lv.bx16, lv.by16, lv.bz16, (const __half *)lv.dd16, lv.d, colour, zero,
+                     hd->fs16);
         else
           LAUNCH_PDL(hd, krb, l, bytes, k_rbgs_h, hg, kBlock, 0, x, rhs, lv.bx16, lv.by16,
-                     lv.bz16, lv.d, colour, zero, hd->fs16);
+                     lv.bz16, (const __half *)lv.dd16, lv.d, colour, zero, hd->fs16);
       }
       else
         LAUNCH_PDL(hd, krb, l, bytes, k_rbgs<T>, hg, kBlock, 0, x, rhs, bx, by, bz, idiag, lv.d,
@@ -390,7 +402,7 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
     // FP32 levels with a fused-sweep grid: one launch per sweep, ping-pong
     // between x and t32 (pairs of sweeps end in x); an odd last sweep, and
     // every sweep of the other levels, is one in-place launch per colour
-    const bool fused = sizeof(T) == 4 && hd->opts.smoother == 1 && lv.fchunk > 0;
+    const bool fused = sizeof(T) == 4 && hd->opts.smoother == 1 && lv.fchunk > 0 && !hd->outflow;
     auto fsweep = [&](const float *xin, float *xout, int c0, int zero) -> mp_status {
       FusedArgs fa{xin, xout, (const float *)rhs, lv.bx16, lv.by16, lv.bz16, lv.d, c0, zero,
                    hd->fs16, lv.ftx, lv.fty, lv.fchunk};
@@ -423,12 +435,12 @@ mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
       if (lv.d.nx % 4 == 0)
         LAUNCH_PDL(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h4,
                    dim3((lv.d.nx / 4 + BX - 1) / BX, (lc.d.ny + BY - 1) / BY, lc.d.nz), kBlock,
-                   0, x, rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d, LV<T>::b(lc),
-                   lc.d);
+                   0, x, rhs, lv.bx16, lv.by16, lv.bz16, (const __half *)lv.dd16, 1.f / hd->fs16,
+                   lv.d, LV<T>::b(lc), lc.d);
       else
         LAUNCH_PDL(hd, K_RESTR32, l, 4.625 * nl * sz, k_resid_restrict_h, cell_grid(lc.d),
-                   kBlock, 0, x, rhs, lv.bx16, lv.by16, lv.bz16, 1.f / hd->fs16, lv.d,
-                   LV<T>::b(lc), lc.d);
+                   kBlock, 0, x, rhs, lv.bx16, lv.by16, lv.bz16, (const __half *)lv.dd16,
+                   1.f / hd->fs16, lv.d, LV<T>::b(lc), lc.d);
     } else
       LAUNCH_PDL(hd, kid<T>(K_RESTR64, K_RESTR32), l, 6.125 * nl * sz, k_resid_restrict<T>,
                  cell_grid(lc.d), kBlock, 0, x, rhs, bx, by, bz, diag, lv.d, LV<T>::b(lc), lc.d);
@@ -510,6 +522,9 @@ mp_status deflation_setup(mp_poisson *hd) {
   hd->defl_m = 0;
   hd->defl_nband = 0;
   if (n >= ((size_t)1 << 31)) return MP_OK;  // 32-bit cell indices
+  // the band sums form E = Z^T A Z from the face arrays, which do not hold the
+  // outflow faces: deflation is for periodic and wall boundaries
+  if (hd->outflow) return MP_OK;
   const int nblk = (int)((n + BAND_CELLS - 1) / BAND_CELLS);
   // dint: [0] components (roots), [1] band cells, [2] labelling bound exceeded
   CK(cudaMemsetAsync(hd->dint, 0, 4 * sizeof(int), hd->st));
@@ -705,7 +720,8 @@ mp_status pcg(mp_poisson *hd, T *x, T *r, T *z, T *dv, T *q, double tol_abs, int
     LAUNCH(hd, kid<T>(K_XPBY64, K_XPBY32), 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<T>, VEC_BLOCKS,
            VEC_THREADS, dv, z, n, hd->scal, it == 0);
     LAUNCH(hd, kid<T>(K_APPLY64, K_APPLY32), 0, (sizeof(T) == 8 ? 6.0 : 5.0) * nsz,
-           k_apply_dot<T>, zgrid(l0.d), kBlock, dv, q, bx, by, bz, diag, l0.d, zper_of(l0.d),
+           k_apply_dot<T>, zgrid(l0.d), kBlock, dv, q, bx, by, bz, diag, (const T *)nullptr, l0.d,
+           zper_of(l0.d),
            hd->partial);
     CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
     LAUNCH(hd, kid<T>(K_AXPY64, K_AXPY32), 0, 6.0 * nsz, k_axpy2<T>, VEC_BLOCKS, VEC_THREADS, x,
@@ -816,11 +832,12 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
     if (l0.d.nx % 4 == 0) {  // 16-byte rows
       const Dims dq = chunk_dims(l0.d);
       LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot4, zgrid(dq), kBlock, dv, q, l0.bx32,
-             l0.by32, l0.bz32, l0.d, zper_of(dq), hd->partial);
+             l0.by32, l0.bz32, (const float *)l0.dd32, l0.d, zper_of(dq), hd->partial);
       CKS(reduce(hd, zblocks(dq), OP_ALPHA, 0));
     } else {
       LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot<float>, zgrid(l0.d), kBlock, dv, q,
-             l0.bx32, l0.by32, l0.bz32, (float *)nullptr, l0.d, zper_of(l0.d), hd->partial);
+             l0.bx32, l0.by32, l0.bz32, (float *)nullptr, (const float *)l0.dd32, l0.d,
+             zper_of(l0.d), hd->partial);
       CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
     }
     LAUNCH(hd, K_AXPY32, 0, 6.0 * nsz, k_axpy2<float>, VEC_BLOCKS, VEC_THREADS, e, r, dv, q, n,
@@ -880,7 +897,15 @@ mp_status remove_mean(mp_poisson *hd, double *x) {
 
 // bt (already holding h^2 rhs + Jt with block sums in partial, np blocks)
 // -> subtract mean, store ||bt||^2 in S_BB
+// With an outflow side the operator is nonsingular: b keeps its mean and only
+// ||bt||^2 is formed.
 mp_status finish_rhs(mp_poisson *hd, int np) {
+  if (hd->outflow) {
+    LAUNCH(hd, K_DOT64, 0, hd->n * 8.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, hd->b, hd->b,
+           hd->n, hd->partial);
+    CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_BB));
+    return launch_ok();
+  }
   CKS(reduce(hd, np, OP_MEAN, 0, (double)hd->n));
   LAUNCH(hd, K_SUBMEAN, 0, hd->n * 16.0, k_sub_mean, VEC_BLOCKS, VEC_THREADS, hd->b, hd->n,
          hd->scal, hd->partial);
@@ -916,6 +941,7 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
   hd->stats.coarse_n = hd->nc;
   hd->stats.components = defl_active(hd) ? hd->defl_m : 0;
   if (o.initial_guess == 2 && !hd->net) return MP_ERR_NO_NET;
+  if (o.initial_guess == 2 && hd->outflow) return MP_ERR_INVALID_ARG;  // walls/periodic only
   const int need = o.precision == 0 ? 1 : 2;
   if ((hd->diag_mode & need) != need) CKS(diag_fields(hd, need));
   int zero = o.initial_guess == 0;
@@ -948,11 +974,12 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
              hd->n, hd->partial);
       const Dims dq = chunk_dims(l0.d);
       LAUNCH(hd, K_APPLY32, 0, hd->n * 20.0, k_apply_dot4, zgrid(dq), kBlock, hd->z32, hd->q32,
-             l0.bx32, l0.by32, l0.bz32, l0.d, zper_of(dq), hd->partial);
+             l0.bx32, l0.by32, l0.bz32, (const float *)l0.dd32, l0.d, zper_of(dq), hd->partial);
       CKS(reduce(hd, zblocks(dq), OP_STORE, S_TMP));
     } else {
       LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, p, hd->q,
-             l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial);
+             l0.bx, l0.by, l0.bz, l0.diag, (const double *)nullptr, l0.d, zper_of(l0.d),
+             hd->partial);
       CKS(reduce(hd, zblocks(l0.d), OP_STORE, S_TMP));
     }
     LAUNCH(hd, K_DOT64, 0, hd->n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, p, hd->b, hd->n,
@@ -1058,7 +1085,7 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     hd->stats.outer_steps = outer;
   }
   if (st == MP_OK || st == MP_ERR_NOT_CONVERGED) {
-    CKS(remove_mean(hd, p));
+    if (!hd->outflow) CKS(remove_mean(hd, p));  // gauge of the singular problem
     // final true FP64 residual of the returned p
     LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b,
            hd->r, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial, 0);
@@ -1094,9 +1121,12 @@ mp_status diag_fields(mp_poisson *hd, int mode) {
   for (size_t l = 0; l < hd->L.size(); ++l) {
     Level &lv = hd->L[l];
     auto kd = mode == 1 ? k_diag<1> : (mode == 2 ? k_diag<2> : k_diag<3>);
+    BndPlanes bp{};
+    for (int q = 0; q < 6; ++q) bp.p[q] = lv.bnd[q];
     LAUNCH(hd, K_DIAG, (int)l, lv.n * (mode == 1 ? 48.0 : (mode == 2 ? 58.0 : 66.0)), kd,
            cell_grid(lv.d), kBlock, lv.bx, lv.by, lv.bz, lv.diag, lv.idiag, lv.bx32, lv.by32,
-           lv.bz32, lv.idiag32, lv.bx16, lv.by16, lv.bz16, hd->fs16, lv.d);
+           lv.bz32, lv.idiag32, lv.bx16, lv.by16, lv.bz16, hd->fs16, lv.d, bp, lv.dd, lv.dd32,
+           lv.dd16);
     CKS(launch_ok());
   }
   hd->diag_mode |= mode;
@@ -1131,13 +1161,32 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
              lf.by, lf.bz, lf.d, lv.bx, lv.by, lv.bz, lv.d);
     }
   }
+  if (hd->outflow) {  // outflow boundary faces of every level
+    Level &f0 = hd->L[0];
+    for (int q = 0; q < 6; ++q)
+      if (f0.bnd[q]) {
+        const int na = q < 2 ? f0.d.ny : f0.d.nx, nb = q < 4 ? f0.d.nz : f0.d.ny;
+        LAUNCH(hd, K_FACES, 0, na * nb * 16.0, k_bnd_init, (na * nb + 255) / 256, 256, hd->phi,
+               f0.bnd[q], f0.d, q, 1.0 / rho_l, 1.0 / rho_g);
+      }
+    for (size_t l = 1; l < hd->L.size(); ++l) {
+      Level &lv = hd->L[l], &lf = hd->L[l - 1];
+      for (int q = 0; q < 6; ++q)
+        if (lv.bnd[q]) {
+          const int na = q < 2 ? lv.d.ny : lv.d.nx, nb = q < 4 ? lv.d.nz : lv.d.ny;
+          LAUNCH(hd, K_COARSEN, (int)l, na * nb * 40.0, k_bnd_coarsen, (na * nb + 255) / 256, 256,
+                 lf.bnd[q], lv.bnd[q], na, nb);
+        }
+    }
+    CKS(launch_ok());
+  }
   hd->diag_mode = 0;
   CKS(diag_fields(hd, hd->opts.precision == 0 ? 1 : 2));
   Level &lc = hd->L.back();
   const int lcl = (int)hd->L.size() - 1;
   const double nc = (double)hd->nc;
   LAUNCH(hd, K_DENSE, lcl, nc * 2.0 * nc * 8.0, k_dense_build, (hd->nc + 127) / 128, 128, lc.bx,
-         lc.by, lc.bz, lc.diag, hd->Maug, lc.d);
+         lc.by, lc.bz, lc.diag, hd->Maug, lc.d, hd->outflow == 0 ? 1 : 0);
   if (hd->nc <= GJ_SMEM_MAX)
     LAUNCH_SMEM(hd, K_GJ, lcl, nc * 3.0 * nc * 8.0, k_inverse_cols, hd->nc, 256,
                 (size_t)(hd->nc + 1) * hd->nc * sizeof(double), hd->Maug, hd->Minv, hd->nc);
@@ -1192,8 +1241,12 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
   hd->g = g;
   hd->h = h;
   hd->per = 0;
+  hd->outflow = 0;
   for (int a = 0; a < 3; ++a) {
-    if (bc[a] != MP_BC_PERIODIC && bc[a] != MP_BC_NEUMANN) return MP_ERR_INVALID_ARG;
+    if (bc[a] < MP_BC_PERIODIC || bc[a] > MP_BC_DIRICHLET_NEUMANN) return MP_ERR_INVALID_ARG;
+    if (bc[a] == MP_BC_DIRICHLET || bc[a] == MP_BC_DIRICHLET_NEUMANN) hd->outflow |= 1 << (2 * a);
+    if (bc[a] == MP_BC_DIRICHLET || bc[a] == MP_BC_NEUMANN_DIRICHLET)
+      hd->outflow |= 1 << (2 * a + 1);
     if (dims[a] < 2 || dims[a] > (1 << 16)) return MP_ERR_INVALID_ARG;
     if (bc[a] == MP_BC_PERIODIC) {
       if (dims[a] & 1) return MP_ERR_INVALID_ARG;
@@ -1240,6 +1293,16 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
       CKS(dalloc(hd, &lv.e, lv.n));
       CKS(dalloc(hd, &lv.b32, lv.n));
       CKS(dalloc(hd, &lv.e32, lv.n));
+    }
+    if (hd->outflow) {
+      CKS(dalloc(hd, &lv.dd, lv.n));
+      CKS(dalloc(hd, &lv.dd32, lv.n));
+      CKS(dalloc(hd, &lv.dd16, lv.n));
+      for (int q = 0; q < 6; ++q)
+        if (hd->outflow & (1 << q)) {
+          const size_t na = q < 2 ? lv.d.ny : lv.d.nx, nb = q < 4 ? lv.d.nz : lv.d.ny;
+          CKS(dalloc(hd, &lv.bnd[q], na * nb));
+        }
     }
   }
   CKS(dalloc(hd, &hd->phi, n));
@@ -1299,10 +1362,11 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
     size_t elem = pass == 0 ? sizeof(double) : sizeof(float);
     size_t budget = pass == 0 ? TAIL_BUDGET64 : TAIL_BUDGET32;
     int start = (int)hd->L.size() - 1;
-    size_t bytes = 6 * hd->L.back().n * elem;
-    while (start > 0 && bytes + 6 * hd->L[start - 1].n * elem <= budget) {
+    const size_t arrays = hd->outflow ? 7 : 6;  // + the outflow diagonal
+    size_t bytes = arrays * hd->L.back().n * elem;
+    while (start > 0 && bytes + arrays * hd->L[start - 1].n * elem <= budget) {
       --start;
-      bytes += 6 * hd->L[start].n * elem;
+      bytes += arrays * hd->L[start].n * elem;
     }
     if (pass == 0) {
       hd->tail64 = start;
@@ -1424,6 +1488,7 @@ mp_status mp_poisson_solve(mp_handle hd, const double *rhs_dev, double *p_dev, d
 mp_status mp_poisson_project_step(mp_handle hd, double *ux, double *uy, double *uz, double *p,
                                   double tol, int *iterations) {
   if (!hd || !ux || !uy || !uz || !p || !(tol > 0.0)) return MP_ERR_INVALID_ARG;
+  if (hd->outflow) return MP_ERR_INVALID_ARG;  // one boundary face slot per axis
   CKS(assemble_rhs_u(hd, ux, uy, uz));
   mp_status s = solve_assembled(hd, p, tol, nullptr);
   if (iterations) *iterations = hd->stats.iterations;
@@ -1461,7 +1526,7 @@ mp_status mp_poisson_apply(mp_handle hd, const double *x, double *y) {
   if (!hd || !x || !y) return MP_ERR_INVALID_ARG;
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, x, y,
-         l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d), hd->partial);
+         l0.bx, l0.by, l0.bz, l0.diag, (const double *)nullptr, l0.d, zper_of(l0.d), hd->partial);
   LAUNCH(hd, K_SCALE, 0, hd->n * 16.0, k_scale, VEC_BLOCKS, VEC_THREADS, y, y, hd->n,
          1.0 / (hd->h * hd->h));
   CKS(launch_ok());
@@ -1473,6 +1538,7 @@ mp_status mp_poisson_apply(mp_handle hd, const double *x, double *y) {
 mp_status mp_poisson_divergence(mp_handle hd, const double *ux, const double *uy,
                                 const double *uz, double *dv) {
   if (!hd || !ux || !uy || !uz || !dv) return MP_ERR_INVALID_ARG;
+  if (hd->outflow) return MP_ERR_INVALID_ARG;  // one boundary face slot per axis
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_DIV, 0, hd->n * 32.0, k_divergence, cell_grid(l0.d), kBlock, ux, uy, uz, dv, l0.d,
          hd->h);
@@ -1495,6 +1561,7 @@ mp_status mp_poisson_rhs(mp_handle hd, const double *rhs, double *b) {
 
 mp_status mp_poisson_project(mp_handle hd, const double *p, double *ux, double *uy, double *uz) {
   if (!hd || !p || !ux || !uy || !uz) return MP_ERR_INVALID_ARG;
+  if (hd->outflow) return MP_ERR_INVALID_ARG;  // one boundary face slot per axis
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
          l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, 1.0 / hd->h);

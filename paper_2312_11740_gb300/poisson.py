@@ -9,6 +9,9 @@ from . import _lib
 
 PERIODIC = _lib.MP_BC_PERIODIC
 NEUMANN = _lib.MP_BC_NEUMANN
+DIRICHLET = _lib.MP_BC_DIRICHLET                  # outflow (p = 0) on both sides
+NEUMANN_DIRICHLET = _lib.MP_BC_NEUMANN_DIRICHLET  # wall/inflow low, outflow high
+DIRICHLET_NEUMANN = _lib.MP_BC_DIRICHLET_NEUMANN  # outflow low, wall/inflow high
 
 
 class MPError(RuntimeError):

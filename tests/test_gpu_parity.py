@@ -560,3 +560,80 @@ def test_labelling_bound_turns_deflation_off_and_the_solve_still_converges():
     s.solve(rhs, tol=TOL)
     assert s.stats()["components"] > 1
     s.close()
+
+
+# ---------------------------------------------------- outflow (p = 0) sides
+D, ND, DN = oracle.DIRICHLET, oracle.NEUMANN_DIRICHLET, oracle.DIRICHLET_NEUMANN
+
+
+def _outflow_case(name):
+    g = rng_np(17)
+    if name == "pool_outflow_top":   # liquid pool + bubble, wall bottom, outflow top
+        shape, h, bc = (32, 32, 32), 1.0 / 32, (P, P, ND)
+        phi = synth.level_set(shape, h, [((0.5, 0.5, 0.3), 0.15)], pool_z0=0.6, bc=bc)
+    elif name == "channel":          # outflow at both x ends, walls in y, periodic z
+        shape, h, bc = (16, 24, 40), 1.0 / 40, (D, N, P)
+        phi = synth.level_set(shape, h, [((0.3, 0.3, 0.5), 0.12), ((0.75, 0.6, 0.4), 0.1)], bc=bc)
+    elif name == "inflow_outflow":   # the paper's TOML pattern: inflow low x, outflow high x
+        shape, h, bc = (24, 16, 48), 1.0 / 48, (ND, DN, N)
+        phi = synth.level_set(shape, h, [((0.5, 0.4, 0.3), 0.2)], bc=bc)
+    else:                            # outflow on every side
+        shape, h, bc = (16, 16, 24), 1.0 / 24, (D, D, D)
+        phi = synth.level_set(shape, h, [((0.5, 0.5, 0.5), 0.25)], bc=bc)
+    rhs = g.standard_normal(shape)
+    return phi, rhs, dict(h=h, rho_l=1.0, rho_g=1e-3, sigma=0.05, bc=bc)
+
+
+def rng_np(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+OUT_CASES = ["pool_outflow_top", "channel", "inflow_outflow", "all_outflow"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", OUT_CASES)
+def test_outflow_solve_matches_oracle(name, precision):
+    """p = 0 on outflow faces (antisymmetric ghost): the operator is
+    nonsingular, b keeps its mean, no gauge.  GPU pressure against the
+    oracle's, element by element (relative L2 <= 1e-8), FP64 and mixed;
+    deflation and the fused sweep switch themselves off."""
+    phi, rhs, prm = _outflow_case(name)
+    ref = oracle.solve(phi, rhs, prm["h"], prm["rho_l"], prm["rho_g"], prm["sigma"], prm["bc"],
+                       tol=REF_TOL)
+    assert ref["iters"] >= 0
+    s = make(phi, prm, precision=precision)
+    p, it, _ = s.solve(dev(rhs), tol=TOL)
+    st = s.stats()
+    assert st["relres"] <= TOL and st["components"] == 0
+    assert rel_l2(host(p), ref["p"]) < PARITY
+    assert abs(host(p).mean()) > 1e-6 * np.abs(host(p)).max()  # not gauged to mean zero
+    s.close()
+
+
+@pytest.mark.parametrize("name", OUT_CASES)
+def test_outflow_apply_and_rhs_match_oracle(name):
+    phi, rhs, prm = _outflow_case(name)
+    h, bc = prm["h"], prm["bc"]
+    s = make(phi, prm)
+    x = rng_np(23).standard_normal(phi.shape)
+    f = oracle.faces(phi, prm["rho_l"], prm["rho_g"], bc)
+    assert rel_max(host(s.apply(dev(x))), oracle.apply(f, x, h, bc)) < 1e-12
+    _, _, _, b = oracle.assemble(phi, rhs, h, prm["rho_l"], prm["rho_g"], prm["sigma"], bc)
+    assert rel_max(host(s.rhs(dev(rhs))), b) < 1e-11
+    s.close()
+
+
+def test_outflow_rejects_face_velocity_calls_and_learned_guess():
+    """The low-face-owned velocity layout has one boundary slot per
+    non-periodic axis: the fused divergence/correction calls refuse outflow
+    handles."""
+    phi, rhs, prm = _outflow_case("pool_outflow_top")
+    s = make(phi, prm)
+    u = [dev(np.zeros(phi.shape)) for _ in range(3)]
+    for call in (lambda: s.divergence(*u), lambda: s.project_step(*u, dev(np.zeros(phi.shape))),
+                 lambda: s.project(dev(np.zeros(phi.shape)), *u)):
+        with pytest.raises(MPError) as e:
+            call()
+        assert e.value.status == _lib.MP_ERR_INVALID_ARG
+    s.close()
