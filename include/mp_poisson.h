@@ -221,7 +221,11 @@ mp_status mp_poisson_project_step(mp_handle hd, double *ux_dev, double *uy_dev, 
  * The same step on HOST buffers: copies u* (3N f64) and, for
  * initial_guess = 1, p (N f64) to the device, runs mp_poisson_project_step
  * and copies the corrected velocities and p back.  Uses device staging
- * buffers allocated at setup.
+ * buffers and a second (copy) stream created at setup: the copies run in
+ * z-slabs (whole planes), uploads overlapping the right-hand-side assembly
+ * and downloads overlapping the velocity correction; pinned buffers let the
+ * copies run asynchronously.  Returns after every copy has completed (also
+ * on error).  Same bits as mp_poisson_project_step.
  */
 mp_status mp_poisson_project_step_host(mp_handle hd, double *ux_host, double *uy_host,
                                        double *uz_host, double *p_host, double tol,

@@ -1279,10 +1279,12 @@ __global__ void k_assemble(const double *__restrict__ rhs, const double *__restr
 // bt = h^2 div_h u* + Jt = h * sum(u_high - u_low) + Jt, fused divergence
 __global__ void k_assemble_u(const double *__restrict__ ux, const double *__restrict__ uy,
                              const double *__restrict__ uz, const double *__restrict__ Jt,
-                             double *__restrict__ b, Dims d, int zper, double h,
+                             double *__restrict__ b, Dims d, int zper, int kb0, double h,
                              double *__restrict__ partial) {
+  // kb0: z-block offset of this launch (a slab of the z-blocks); partial is
+  // indexed by the global block
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
+  int k0 = (blockIdx.z + kb0) * zper, k1 = min(d.nz, k0 + zper);
   double acc = 0.0;
   if (i < d.nx && j < d.ny)
     for (int k = k0; k < k1; ++k) {
@@ -1294,7 +1296,7 @@ __global__ void k_assemble_u(const double *__restrict__ ux, const double *__rest
       acc += v;
     }
   double t = block_sum(acc);
-  if (thread0()) partial[block_linear_id()] = t;
+  if (thread0()) partial[block_linear_id() + (size_t)kb0 * gridDim.x * gridDim.y] = t;
 }
 
 // div_h u = sum over axes of (u_high - u_low) / h
@@ -1311,13 +1313,13 @@ __global__ void k_divergence(const double *__restrict__ ux, const double *__rest
 
 // ------------------------------------------------- A15: velocity correction
 // u_f -= beta_f (p_b - p_a - [p]_{a->b}) / h on the three low faces of each
-// cell; wall faces have beta = 0 and keep u*.
+// cell; wall faces have beta = 0 and keep u*.  Planes k0 .. k0 + gridDim.z - 1.
 __global__ void k_project(const double *__restrict__ p, const double *__restrict__ phi,
                           const double *__restrict__ kap, const double *__restrict__ bx,
                           const double *__restrict__ by, const double *__restrict__ bz,
                           double *__restrict__ ux, double *__restrict__ uy,
-                          double *__restrict__ uz, Dims d, double sig, double ih) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+                          double *__restrict__ uz, Dims d, int k0, double sig, double ih) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z + k0;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
   double pc = p[c], fc = phi[c], kc = kap[c];

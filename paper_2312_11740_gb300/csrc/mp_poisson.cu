@@ -67,6 +67,7 @@ const char *const kKernelNames[K_COUNT] = {
 constexpr int MAX_LEVELS = 16;
 constexpr int TAIL32_NU_MAX = 4;  // sweeps per level in the one-CTA FP32 tail
 constexpr int EVENT_POOL = 4096;
+constexpr int MAX_SLABS = 8;  // z-slabs of the host-buffer step's copy pipeline
 
 struct ProfEntry {
   long long launches = 0;
@@ -134,6 +135,10 @@ struct mp_poisson {
   };
   std::vector<Graph> graphs;
   cudaStream_t cap = nullptr;  // private stream used only for capture
+  // host-buffer step: copy stream and the events that order its z-slab copies
+  // against the assembly and the velocity correction on st
+  cudaStream_t cs = nullptr;
+  cudaEvent_t xev[2 * MAX_SLABS + 2] = {};
   // first level of the one-CTA coarse tail per precision, and its smem bytes
   int tail64 = 0, tail32 = 0;
   size_t tail64_bytes = 0, tail32_bytes = 0;
@@ -923,9 +928,25 @@ mp_status assemble_rhs(mp_poisson *hd, const double *rhs) {
 mp_status assemble_rhs_u(mp_poisson *hd, const double *ux, const double *uy, const double *uz) {
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_ASSEMBLE_U, 0, hd->n * 40.0, k_assemble_u, zgrid(l0.d), kBlock, ux, uy, uz,
-         hd->Jt, hd->b, l0.d, zper_of(l0.d), hd->h, hd->partial);
+         hd->Jt, hd->b, l0.d, zper_of(l0.d), 0, hd->h, hd->partial);
   CKS(launch_ok());
   return finish_rhs(hd, zblocks(l0.d));
+}
+
+// z-slabs of the host-buffer step: groups of whole z-blocks of zgrid(l0)
+struct Slabs {
+  int count = 1, per = 1, zper = 1, zb = 1;  // slabs, z-blocks per slab, planes per z-block
+  int kb_lo(int s) const { return s * per; }
+  int kb_hi(int s) const { return std::min(zb, (s + 1) * per); }
+};
+Slabs slabs_of(const Dims &d) {
+  Slabs q;
+  q.zper = zper_of(d);
+  q.zb = (int)zgrid(d).z;
+  q.count = std::min(q.zb, MAX_SLABS);
+  q.per = (q.zb + q.count - 1) / q.count;
+  q.count = (q.zb + q.per - 1) / q.per;
+  return q;
 }
 
 mp_status diag_fields(mp_poisson *hd, int mode);
@@ -1356,6 +1377,8 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
     return MP_ERR_OOM;
   }
   CK(cudaStreamCreateWithFlags(&hd->cap, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&hd->cs, cudaStreamNonBlocking));
+  for (cudaEvent_t &e : hd->xev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   // coarse tail: the coarsest levels whose iterate, rhs and faces fit the
   // shared-memory budget of one block (coarsest level always included)
   for (int pass = 0; pass < 2; ++pass) {
@@ -1495,8 +1518,86 @@ mp_status mp_poisson_project_step(mp_handle hd, double *ux, double *uy, double *
   if (s != MP_OK) return s;
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
-         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, 1.0 / hd->h);
+         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, 0, hd->sigma, 1.0 / hd->h);
   CKS(launch_ok());
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
+// The host-buffer step as a z-slab pipeline on two streams.  Uploads of u*
+// run on the copy stream slab by slab; the assembly of a slab starts once it
+// and the next slab (the z-high faces of its last plane) have arrived.  After
+// the solve p is downloaded while the velocity correction runs slab by slab,
+// each slab's three components downloaded as soon as it is corrected.  One
+// cudaMemcpyAsync per array and slab.
+mp_status project_step_host(mp_poisson *hd, double *ux_h, double *uy_h, double *uz_h, double *p_h,
+                            double tol, int *iterations) {
+  Level &l0 = hd->L[0];
+  const Dims d = l0.d;
+  const Slabs q = slabs_of(d);
+  const size_t plane = (size_t)d.nx * d.ny;
+  cudaEvent_t *in = hd->xev, *out = hd->xev + MAX_SLABS, ready = hd->xev[2 * MAX_SLABS],
+              solved = hd->xev[2 * MAX_SLABS + 1];
+  // the copy stream starts after the work already queued on st
+  CK(cudaEventRecord(ready, hd->st));
+  CK(cudaStreamWaitEvent(hd->cs, ready, 0));
+  auto planes = [&](int s, size_t &k0, size_t &cnt) {
+    k0 = (size_t)q.kb_lo(s) * q.zper;
+    cnt = std::min((size_t)d.nz, (size_t)q.kb_hi(s) * q.zper) - k0;
+  };
+  for (int s = 0; s < q.count; ++s) {
+    size_t k0, cnt;
+    planes(s, k0, cnt);
+    const size_t off = k0 * plane, bytes = cnt * plane * sizeof(double);
+    CK(cudaMemcpyAsync(hd->ux + off, ux_h + off, bytes, cudaMemcpyHostToDevice, hd->cs));
+    CK(cudaMemcpyAsync(hd->uy + off, uy_h + off, bytes, cudaMemcpyHostToDevice, hd->cs));
+    CK(cudaMemcpyAsync(hd->uz + off, uz_h + off, bytes, cudaMemcpyHostToDevice, hd->cs));
+    CK(cudaEventRecord(in[s], hd->cs));
+  }
+  if (hd->opts.initial_guess == 1) {
+    CK(cudaMemcpyAsync(hd->pst, p_h, hd->n * sizeof(double), cudaMemcpyHostToDevice, hd->cs));
+    CK(cudaEventRecord(solved, hd->cs));
+  }
+  const dim3 g = zgrid(d);
+  for (int s = 0; s < q.count; ++s) {
+    // the slab's last plane reads the z-high faces in the next slab (plane 0
+    // after the last: the periodic image or the shared wall face)
+    CK(cudaStreamWaitEvent(hd->st, in[s], 0));
+    CK(cudaStreamWaitEvent(hd->st, in[s + 1 < q.count ? s + 1 : 0], 0));
+    const int kb0 = q.kb_lo(s), nb = q.kb_hi(s) - kb0;
+    size_t k0, cnt;
+    planes(s, k0, cnt);
+    LAUNCH(hd, K_ASSEMBLE_U, 0, cnt * plane * 40.0, k_assemble_u, dim3(g.x, g.y, nb), kBlock,
+           (const double *)hd->ux, (const double *)hd->uy, (const double *)hd->uz,
+           (const double *)hd->Jt, hd->b, d, q.zper, kb0, hd->h, hd->partial);
+  }
+  CKS(launch_ok());
+  if (hd->opts.initial_guess == 1) CK(cudaStreamWaitEvent(hd->st, solved, 0));
+  CKS(finish_rhs(hd, zblocks(d)));
+  mp_status s = solve_assembled(hd, hd->pst, tol, nullptr);
+  if (iterations) *iterations = hd->stats.iterations;
+  if (s != MP_OK) return s;
+  CK(cudaEventRecord(solved, hd->st));
+  CK(cudaStreamWaitEvent(hd->cs, solved, 0));
+  CK(cudaMemcpyAsync(p_h, hd->pst, hd->n * sizeof(double), cudaMemcpyDeviceToHost, hd->cs));
+  for (int s2 = 0; s2 < q.count; ++s2) {
+    size_t k0, cnt;
+    planes(s2, k0, cnt);
+    LAUNCH(hd, K_PROJECT, 0, cnt * plane * 96.0, k_project,
+           dim3(cell_grid(d).x, cell_grid(d).y, (unsigned)cnt), kBlock, (const double *)hd->pst,
+           (const double *)hd->phi, (const double *)hd->kap, (const double *)l0.bx,
+           (const double *)l0.by, (const double *)l0.bz, hd->ux, hd->uy, hd->uz, d, (int)k0,
+           hd->sigma, 1.0 / hd->h);
+    CKS(launch_ok());
+    CK(cudaEventRecord(out[s2], hd->st));
+    CK(cudaStreamWaitEvent(hd->cs, out[s2], 0));
+    const size_t off = k0 * plane, bytes = cnt * plane * sizeof(double);
+    CK(cudaMemcpyAsync(ux_h + off, hd->ux + off, bytes, cudaMemcpyDeviceToHost, hd->cs));
+    CK(cudaMemcpyAsync(uy_h + off, hd->uy + off, bytes, cudaMemcpyDeviceToHost, hd->cs));
+    CK(cudaMemcpyAsync(uz_h + off, hd->uz + off, bytes, cudaMemcpyDeviceToHost, hd->cs));
+  }
+  CK(cudaStreamSynchronize(hd->cs));
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);
   return MP_OK;
@@ -1505,21 +1606,12 @@ mp_status mp_poisson_project_step(mp_handle hd, double *ux, double *uy, double *
 mp_status mp_poisson_project_step_host(mp_handle hd, double *ux_h, double *uy_h, double *uz_h,
                                        double *p_h, double tol, int *iterations) {
   if (!hd || !ux_h || !uy_h || !uz_h || !p_h || !(tol > 0.0)) return MP_ERR_INVALID_ARG;
-  size_t bytes = hd->n * sizeof(double);
-  CK(cudaMemcpyAsync(hd->ux, ux_h, bytes, cudaMemcpyHostToDevice, hd->st));
-  CK(cudaMemcpyAsync(hd->uy, uy_h, bytes, cudaMemcpyHostToDevice, hd->st));
-  CK(cudaMemcpyAsync(hd->uz, uz_h, bytes, cudaMemcpyHostToDevice, hd->st));
-  if (hd->opts.initial_guess == 1)
-    CK(cudaMemcpyAsync(hd->pst, p_h, bytes, cudaMemcpyHostToDevice, hd->st));
-  mp_status s = mp_poisson_project_step(hd, hd->ux, hd->uy, hd->uz, hd->pst, tol, iterations);
-  if (s != MP_OK) return s;
-  CK(cudaMemcpyAsync(ux_h, hd->ux, bytes, cudaMemcpyDeviceToHost, hd->st));
-  CK(cudaMemcpyAsync(uy_h, hd->uy, bytes, cudaMemcpyDeviceToHost, hd->st));
-  CK(cudaMemcpyAsync(uz_h, hd->uz, bytes, cudaMemcpyDeviceToHost, hd->st));
-  CK(cudaMemcpyAsync(p_h, hd->pst, bytes, cudaMemcpyDeviceToHost, hd->st));
-  CK(cudaStreamSynchronize(hd->st));
-  prof_resolve(hd);
-  return MP_OK;
+  if (hd->outflow) return MP_ERR_INVALID_ARG;  // one boundary face slot per axis
+  const mp_status s = project_step_host(hd, ux_h, uy_h, uz_h, p_h, tol, iterations);
+  // no copy may touch the caller's buffers after the call returns
+  const cudaError_t e = cudaStreamSynchronize(hd->cs);
+  if (s == MP_OK && e != cudaSuccess) return MP_ERR_CUDA;
+  return s;
 }
 
 mp_status mp_poisson_apply(mp_handle hd, const double *x, double *y) {
@@ -1564,7 +1656,7 @@ mp_status mp_poisson_project(mp_handle hd, const double *p, double *ux, double *
   if (hd->outflow) return MP_ERR_INVALID_ARG;  // one boundary face slot per axis
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
-         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, hd->sigma, 1.0 / hd->h);
+         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, 0, hd->sigma, 1.0 / hd->h);
   CKS(launch_ok());
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);
@@ -1667,6 +1759,12 @@ void mp_poisson_destroy(mp_handle hd) {
   for (cudaEvent_t e : hd->events) cudaEventDestroy(e);
   destroy_graphs(hd);
   if (hd->cap) cudaStreamDestroy(hd->cap);
+  if (hd->cs) {
+    cudaStreamSynchronize(hd->cs);
+    cudaStreamDestroy(hd->cs);
+  }
+  for (cudaEvent_t e : hd->xev)
+    if (e) cudaEventDestroy(e);
   if (hd->scal_h) cudaFreeHost(hd->scal_h);
   if (hd->hint) cudaFreeHost(hd->hint);
   delete hd;

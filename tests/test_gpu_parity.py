@@ -186,9 +186,19 @@ def test_project_step_matches_oracle(precision):
     hx, hy, hz = [torch.from_numpy(np.ascontiguousarray(c)).pin_memory() for c in u]
     hp = torch.zeros(phi.shape, dtype=torch.float64).pin_memory()
     from paper_2312_11740_gb300 import mp_poisson_project_step_host
+    # (z-slab copy pipeline on a second stream: slabs of whole z-blocks, the
+    # assembly of a slab after it and the next have arrived)
     mp_poisson_project_step_host(s.handle, hx, hy, hz, hp, TOL)
     assert np.array_equal(hp.numpy(), host(p))
-    assert np.array_equal(hx.numpy(), host(ux)) and np.array_equal(hz.numpy(), host(uz))
+    for hc, dc in zip((hx, hy, hz), (ux, uy, uz)):
+        assert np.array_equal(hc.numpy(), host(dc))
+    # pageable host buffers: the same bits
+    gx, gy, gz = [torch.from_numpy(np.ascontiguousarray(c)) for c in u]
+    gp = torch.zeros(phi.shape, dtype=torch.float64)
+    mp_poisson_project_step_host(s.handle, gx, gy, gz, gp, TOL)
+    assert np.array_equal(gp.numpy(), host(p))
+    for hc, dc in zip((gx, gy, gz), (ux, uy, uz)):
+        assert np.array_equal(hc.numpy(), host(dc))
     s.close()
 
 
