@@ -66,6 +66,8 @@ def _load():
         lib.oracle_gs.restype = i
         lib.oracle_divergence.argtypes = [i, i, i, d, D, D, D, D]
         lib.oracle_project.argtypes = [i, i, i, d, I3, D, D, D, D, D, d, D, D, D, D]
+        lib.oracle_flux_jump.argtypes = [i, i, i, d, I3, D, D, D, D, D, d, d, D]
+        lib.oracle_project_flux.argtypes = [i, i, i, I3, D, D, D, D, D, d, d, D, D, D]
         _lib = lib
     return _lib
 
@@ -186,31 +188,50 @@ def divergence_full(fx, fy, fz, h):
     return out
 
 
-def project(phi, kappa, f, p, ux, uy, uz, h, sigma, bc):
-    """Corrected face velocities (n+1 faces per axis) u = u* - beta (grad p - jump)."""
+def flux_jump(phi, mdot, f, h, rho_l, rho_g, bc):
+    """Phase-change source: the flux jump B = -mdot [1/rho] of every interface
+    face split between its two rows (see mp_oracle.c).  mdot: cell values."""
+    phi, mdot = _f64(phi), _f64(mdot)
+    nz, ny, nx = phi.shape
+    out = np.zeros_like(phi)
+    _load().oracle_flux_jump(nx, ny, nz, h, _per(bc), _p(phi), _p(mdot), _p(f.fx), _p(f.fy),
+                             _p(f.fz), rho_l, rho_g, _p(out))
+    return out
+
+
+def project(phi, kappa, f, p, ux, uy, uz, h, sigma, bc, mdot=None, rho_l=1.0, rho_g=1e-3):
+    """Corrected face velocities (n+1 faces per axis) u = u* - beta (grad p - jump);
+    with a phase-change mass flux mdot, interface faces get the liquid-side
+    velocity."""
     fx, fy, fz = owned_to_full(ux, 0), owned_to_full(uy, 1), owned_to_full(uz, 2)
     phi, kappa, p = _f64(phi), _f64(kappa), _f64(p)
     nz, ny, nx = phi.shape
     _load().oracle_project(nx, ny, nz, h, _per(bc), _p(phi), _p(kappa), _p(f.fx), _p(f.fy),
                            _p(f.fz), sigma, _p(p), _p(fx), _p(fy), _p(fz))
+    if mdot is not None:
+        _load().oracle_project_flux(nx, ny, nz, _per(bc), _p(phi), _p(_f64(mdot)), _p(f.fx),
+                                    _p(f.fy), _p(f.fz), rho_l, rho_g, _p(fx), _p(fy), _p(fz))
     return fx, fy, fz
 
 
-def assemble(phi, rhs, h, rho_l, rho_g, sigma, bc):
+def assemble(phi, rhs, h, rho_l, rho_g, sigma, bc, mdot=None):
     """kappa, faces, J and the right-hand side b = rhs + J, minus its mean
-    when the operator is singular (no outflow side)."""
+    when the operator is singular (no outflow side).  With a phase-change
+    mass flux mdot, J includes its flux-jump source."""
     kappa = curvature(phi, h, bc)
     f = faces(phi, rho_l, rho_g, bc)
     J = jump(phi, kappa, f, h, sigma, bc)
+    if mdot is not None:
+        J = J + flux_jump(phi, mdot, f, h, rho_l, rho_g, bc)
     b = _f64(rhs) + J
     if singular(bc):
         b = b - b.mean()
     return kappa, f, J, b
 
 
-def solve(phi, rhs, h, rho_l, rho_g, sigma, bc, tol=1e-12, maxit=200000):
+def solve(phi, rhs, h, rho_l, rho_g, sigma, bc, tol=1e-12, maxit=200000, mdot=None):
     """Full oracle solve: returns dict with p (mean-free when singular), b, kappa,
     faces, iters, relres."""
-    kappa, f, J, b = assemble(phi, rhs, h, rho_l, rho_g, sigma, bc)
+    kappa, f, J, b = assemble(phi, rhs, h, rho_l, rho_g, sigma, bc, mdot=mdot)
     x, it, rel = cg(f, b, h, bc, tol=tol, maxit=maxit)
     return dict(p=x, b=b, kappa=kappa, faces=f, J=J, iters=it, relres=rel)

@@ -241,6 +241,112 @@ void oracle_jump(int nx, int ny, int nz, double h, const int bc[3], const double
       }
 }
 
+/*
+ * Phase change (evaporation; the MultiphaseEvap unit of Section 3, which
+ * adds mass transfer at the interface to the main multiphase unit).  The
+ * paper prints no formulas; this is the ghost-fluid reading.  A mass flux
+ * mdot (per unit interface area, liquid -> gas) makes the normal velocity
+ * jump, [u.n] = u_gas.n - u_liquid.n = mdot [1/rho], [1/rho] = 1/rho_g -
+ * 1/rho_l, n the normal from liquid into gas.  With u = u* - beta grad p
+ * (Delta t = 1) and u* continuous, the pressure flux jumps by
+ *   B = [beta dp/dn] = beta_g dp_g/dn - beta_l dp_l/dn = -mdot [1/rho],
+ * a quantity that does not depend on which side of a face is which.
+ *
+ * On a face between cells a and b with the interface at fraction theta_a =
+ * |phi_a| / (|phi_a| + |phi_b|) of the way from a (theta_b = 1 - theta_a),
+ * p linear on each side with the two jump conditions gives the flux on a's
+ * side F_a = beta (p_b - p_a - [p]_{a->b}) / h - beta theta_b rho_b B and on
+ * b's side F_b = F_a + B = beta (p_b - p_a - [p]_{a->b}) / h + beta theta_a
+ * rho_a B (beta the face coefficient, 1 / (theta_a rho_a + theta_b rho_b)).
+ * Each row takes the flux of its own side, so the face adds
+ *   beta theta_b rho_b B / h  to row a,   beta theta_a rho_a B / h  to row b,
+ * B / h in total: the volume the phase change creates.  The interface value
+ * of mdot interpolates the cell values like the curvature:
+ *   mdot_G = (|phi_b| mdot_a + |phi_a| mdot_b) / (|phi_a| + |phi_b|).
+ */
+static double face_flux_jump(double pa, double pb, double ma, double mb, double jinv) {
+  if (is_gas(pa) == is_gas(pb)) return 0.0;
+  double mg = (fabs(pb) * ma + fabs(pa) * mb) / (fabs(pa) + fabs(pb));
+  return -mg * jinv;
+}
+
+/* beta theta_nb rho_nb: the part of B that the row of cell c carries for its
+ * face to nb (the fraction of the c-nb segment in nb's fluid, times nb's
+ * density, times the face coefficient). */
+static double flux_share(double pc, double pnb, double beta, double rho_l, double rho_g) {
+  double rnb = is_gas(pnb) ? rho_g : rho_l;
+  return beta * fabs(pnb) / (fabs(pc) + fabs(pnb)) * rnb;
+}
+
+/* J += the phase-change flux-jump source of every interface face (above);
+ * mdot: cell values (N). */
+void oracle_flux_jump(int nx, int ny, int nz, double h, const int bc[3], const double *phi,
+                      const double *mdot, const double *fx, const double *fy, const double *fz,
+                      double rho_l, double rho_g, double *J) {
+  const int periodic[3] = {PER(bc, 0), PER(bc, 1), PER(bc, 2)};
+  const double jinv = 1.0 / rho_g - 1.0 / rho_l;
+  /* serial: each face updates two rows */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t b = IDX(i, j, k);
+        size_t a[3] = {0, 0, 0};
+        int has[3] = {i > 0 || periodic[0], j > 0 || periodic[1], k > 0 || periodic[2]};
+        double beta[3] = {fx[FX(i, j, k)], fy[FY(i, j, k)], fz[FZ(i, j, k)]};
+        a[0] = IDX(i > 0 ? i - 1 : nx - 1, j, k);
+        a[1] = IDX(i, j > 0 ? j - 1 : ny - 1, k);
+        a[2] = IDX(i, j, k > 0 ? k - 1 : nz - 1);
+        for (int ax = 0; ax < 3; ++ax) {
+          if (!has[ax]) continue;
+          double B = face_flux_jump(phi[a[ax]], phi[b], mdot[a[ax]], mdot[b], jinv);
+          if (B == 0.0) continue;
+          J[a[ax]] += flux_share(phi[a[ax]], phi[b], beta[ax], rho_l, rho_g) * B / h;
+          J[b] += flux_share(phi[b], phi[a[ax]], beta[ax], rho_l, rho_g) * B / h;
+        }
+      }
+}
+
+/*
+ * The phase-change part of the velocity correction.  A face crossing the
+ * interface has a liquid-side and a gas-side velocity (they differ by the
+ * jump mdot [1/rho]); the face stores the liquid-side one, u*_f - F_liquid
+ * (F_a when a is liquid, F_b when b is): on top of oracle_project's
+ * correction that adds +beta theta_b rho_b B when a is liquid and
+ * -beta theta_a rho_a B when b is.  The gas-side velocity is the stored one
+ * plus the jump.  Updates ux, uy, uz (n+1 faces per axis) in place.
+ */
+void oracle_project_flux(int nx, int ny, int nz, const int bc[3], const double *phi,
+                         const double *mdot, const double *fx, const double *fy,
+                         const double *fz, double rho_l, double rho_g, double *ux, double *uy,
+                         double *uz) {
+  const int periodic[3] = {PER(bc, 0), PER(bc, 1), PER(bc, 2)};
+  const double jinv = 1.0 / rho_g - 1.0 / rho_l;
+  for (int k = 0; k <= nz; ++k)
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i <= nx; ++i)
+        for (int ax = 0; ax < 3; ++ax) {
+          int idx3[3] = {i, j, k}, n3[3] = {nx, ny, nz};
+          int in = 1; /* the face exists on this axis (other indices in range) */
+          for (int q = 0; q < 3; ++q)
+            if (q != ax && idx3[q] >= n3[q]) in = 0;
+          if (!in) continue;
+          int f = idx3[ax];
+          if ((f == 0 || f == n3[ax]) && !periodic[ax]) continue; /* boundary face */
+          int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+          lo[ax] = f == 0 ? n3[ax] - 1 : f - 1;
+          hi[ax] = f == n3[ax] ? 0 : f;
+          size_t a = IDX(lo[0], lo[1], lo[2]), b = IDX(hi[0], hi[1], hi[2]);
+          double B = face_flux_jump(phi[a], phi[b], mdot[a], mdot[b], jinv);
+          if (B == 0.0) continue;
+          double *u = ax == 0 ? &ux[FX(i, j, k)] : (ax == 1 ? &uy[FY(i, j, k)] : &uz[FZ(i, j, k)]);
+          double beta = ax == 0 ? fx[FX(i, j, k)] : (ax == 1 ? fy[FY(i, j, k)] : fz[FZ(i, j, k)]);
+          if (!is_gas(phi[a]))
+            *u += flux_share(phi[a], phi[b], beta, rho_l, rho_g) * B;
+          else
+            *u -= flux_share(phi[b], phi[a], beta, rho_l, rho_g) * B;
+        }
+}
+
 /* The cell across the low (low = 1) or high face of cell i on an axis of n
  * cells with boundary code `code`, given inb = i - 1 or i + 1: its index
  * inside the grid (wrapped on a periodic axis), -1 at an outflow face (the

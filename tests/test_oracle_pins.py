@@ -442,3 +442,124 @@ def test_outflow_solvers_agree_and_projection_is_divergence_free():
     assert np.linalg.norm(div) <= 1e-10 * np.linalg.norm(rhs)
     assert np.all(fz[0] == 0.0)          # wall bottom keeps u* = 0
     assert np.abs(fz[-1]).max() > 0.0    # the outflow top carries the flux out
+
+
+# ------------------------------------------- phase change: the flux jump
+def _layer(orient, n=24, s0=0.37):
+    """A planar interface across one axis, the gas side open (outflow) and
+    the liquid side closed (wall); mdot = 0.5 + 0.3 s (s the coordinate
+    along that axis), so the interface value is 0.5 + 0.3 s0 exactly."""
+    h = 1.0 / n
+    if orient == "x":
+        shape, bc, ax = (4, 4, n), (ND, P, P), 0
+    else:
+        shape, bc, ax = (n, 4, 4), ((P, P, ND) if orient == "z_up" else (P, P, DN)), 2
+    x, y, z = centres(shape, h)
+    s = x if ax == 0 else z
+    phi = s0 - s if orient == "z_down" else s - s0
+    mdot = 0.5 + 0.3 * s
+    return shape, h, bc, ax, s, np.ascontiguousarray(phi), np.ascontiguousarray(mdot)
+
+
+@pytest.mark.parametrize("orient", ["z_up", "z_down", "x"])
+def test_flux_jump_planar_layer_is_exact(orient):
+    """Evaporation from a flat liquid layer, u* = 0.  The liquid (closed by a
+    wall) stays at rest with uniform pressure; the gas leaves through the
+    outflow side with the velocity jump mdot_G [1/rho] and a linear pressure
+    falling to 0 on the outflow face.  That piecewise-linear pressure is
+    reproduced by the ghost-fluid flux-jump discretisation to rounding (both
+    sides linear, jumps imposed at the interface point), and so are the
+    velocities: 0 on every liquid face and on the interface face (stored
+    liquid side), the jump on every gas face."""
+    rho_l, rho_g, s0 = 1.0, 1e-3, 0.37
+    shape, h, bc, ax, s, phi, mdot = _layer(orient, s0=s0)
+    jinv = 1.0 / rho_g - 1.0 / rho_l
+    mg = 0.5 + 0.3 * s0
+    res = oracle.solve(phi, np.zeros(shape), h, rho_l, rho_g, 0.07, bc, tol=1e-14, mdot=mdot)
+    # gas velocity along +s (z_up, x) or -s (z_down); p = 0 on the outflow face
+    if orient == "z_down":
+        exact = np.where(phi > 0, rho_g * mg * jinv * s, rho_g * mg * jinv * s0)
+    else:
+        exact = np.where(phi > 0, rho_g * mg * jinv * (1.0 - s), rho_g * mg * jinv * (1.0 - s0))
+    assert np.abs(res["p"] - exact).max() < 1e-10 * np.abs(exact).max()
+    zero = [np.zeros(shape)] * 3
+    fx, fy, fz = oracle.project(phi, res["kappa"], res["faces"], res["p"], *zero, h, 0.07, bc,
+                                mdot=mdot, rho_l=rho_l, rho_g=rho_g)
+    un = fx if ax == 0 else fz
+    # face f sits at s = f h; the gas faces (outflow face included) carry the jump
+    fcoord = np.arange(un.shape[2 - ax]) * h
+    shp = [1, 1, 1]
+    shp[2 - ax] = -1
+    fcoord = fcoord.reshape(shp)
+    # a gas face has gas on both sides; the interface face stores the liquid side
+    gasface = (fcoord + 0.5 * h < s0) if orient == "z_down" else (fcoord - 0.5 * h > s0)
+    want = np.where(gasface, (-mg if orient == "z_down" else mg) * jinv, 0.0)
+    want = np.broadcast_to(want, un.shape)
+    assert np.abs(un - want).max() < 1e-9 * mg * jinv
+    for other in ((fy, fz) if ax == 0 else (fx, fy)):
+        assert np.abs(other).max() < 1e-9 * mg * jinv
+
+
+def _crossing_faces(gas, bc):
+    """Faces whose two cells lie in different fluids (periodic wrap faces
+    included, boundary faces of other axes excluded)."""
+    count = 0
+    for ax in range(3):
+        npax = 2 - ax
+        d = np.diff(gas.astype(np.int8), axis=npax) != 0
+        count += int(d.sum())
+        if bc[ax] == P:
+            first = np.take(gas, [0], axis=npax)
+            last = np.take(gas, [-1], axis=npax)
+            count += int((first != last).sum())
+    return count
+
+
+@pytest.mark.parametrize("bc", [(P, P, N), (P, P, ND), (D, D, D)])
+def test_flux_jump_source_is_the_created_volume(bc):
+    """Uniform mdot: every interface face adds B / h = -mdot [1/rho] / h to
+    the right-hand side in total (split between its two rows), so the source
+    sums to -mdot [1/rho] (interface faces) / h; each row's share is
+    positive (B < 0 for evaporation) and the gas row carries almost all of
+    it (its share is 1 / (1 + theta_l rho_l / (theta_g rho_g)))."""
+    shape, h = (12, 10, 8), 1.0 / 12
+    rho_l, rho_g, md = 1.0, 1e-3, 0.3
+    phi = synth.level_set(shape, h, [((0.3, 0.4, 0.5), 0.2), ((0.45, 0.4, 0.2), 0.12)],
+                          bc=(P, P, N) if bc[0] == P else (N, N, N))
+    f = oracle.faces(phi, rho_l, rho_g, bc)
+    Jf = oracle.flux_jump(phi, np.full(shape, md), f, h, rho_l, rho_g, bc)
+    B = -md * (1.0 / rho_g - 1.0 / rho_l)
+    ncross = _crossing_faces(phi > 0, bc)
+    assert ncross > 20
+    assert abs(Jf.sum() - B * ncross / h) < 1e-12 * abs(B) * ncross / h
+    band = Jf != 0.0
+    assert np.all(Jf[band] * B > 0)
+    gas_part = Jf[(phi > 0) & band].sum() / Jf[band].sum()
+    assert gas_part > 0.9
+
+
+def test_flux_jump_projection_keeps_liquid_divergence_free():
+    """An evaporating bubble under an outflow top with a smooth u*: after the
+    solve and the correction (liquid-side velocity on interface faces) every
+    liquid cell is divergence-free to the solve's tolerance, while the
+    phase change's volume leaves through the outflow face."""
+    shape, h = (16, 12, 12), 1.0 / 16
+    bc = (P, P, ND)
+    rho_l, rho_g = 1.0, 1e-3
+    phi = synth.level_set(shape, h, [((0.4, 0.5, 0.45), 0.2)], bc=bc)
+    x, y, z = centres(shape, h)
+    mdot = np.ascontiguousarray(0.02 * (1.0 + x + 0.5 * y * z))
+    u = synth.velocity(4, shape, h, bc=(P, P, N))
+    rhs = oracle.divergence(*u, h)
+    res = oracle.solve(phi, rhs, h, rho_l, rho_g, 0.02, bc, tol=1e-13, mdot=mdot)
+    fx, fy, fz = oracle.project(phi, res["kappa"], res["faces"], res["p"], *u, h, 0.02, bc,
+                                mdot=mdot, rho_l=rho_l, rho_g=rho_g)
+    div = oracle.divergence_full(fx, fy, fz, h)
+    liquid = phi <= 0
+    scale = np.linalg.norm(res["b"])
+    assert np.abs(div[liquid]).max() < 1e-9 * scale
+    assert np.abs(div[~liquid]).max() > 1e-3 * scale  # gas cells hold the created volume
+    # the outflow face carries the created volume plus nothing else (div u* = 0 in total)
+    created = -oracle.flux_jump(phi, mdot, res["faces"], h, rho_l, rho_g, bc).sum() * h ** 3
+    out = fz[-1].sum() * h * h
+    assert created > 0 and abs(out - created) < 1e-8 * created
