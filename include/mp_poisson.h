@@ -171,6 +171,32 @@ mp_status mp_poisson_setup(mp_handle *out, mp_grid g, double h, const mp_bc bc[3
 mp_status mp_poisson_set_geometry(mp_handle hd, const double *phi_dev, double rho_l, double rho_g,
                                   double sigma);
 
+/*
+ * Defines: the phase-change variant (evaporation, the MultiphaseEvap unit
+ * of Section 3, which adds interface mass transfer to the main multiphase
+ * unit); the paper prints no formula, the reading is the ghost-fluid one.
+ *
+ * Set (mdot_dev != NULL) or clear (NULL) a phase-change mass flux: mdot_dev
+ * is device memory, N f64 cell values of the mass flux per unit interface
+ * area from liquid to gas (copied; the caller keeps ownership).  The normal
+ * velocity then jumps by mdot [1/rho], [1/rho] = 1/rho_g - 1/rho_l, so the
+ * pressure flux jumps by B = -mdot_G [1/rho] across every interface face
+ * (mdot_G: the cell values interpolated to the interface point like the
+ * curvature).  With p linear on each side of the interface the two jump
+ * conditions give each of the face's two rows a share of B / h: the row of
+ * cell c takes beta theta_nb rho_nb B / h, theta_nb the fraction of the
+ * c-nb segment lying in the neighbour's fluid.  These shares join the jump
+ * source J (mp_poisson_get_fields returns the sum); the velocity correction
+ * (mp_poisson_project*, wall and periodic boundaries) stores the
+ * liquid-side velocity on interface faces (the gas side is that plus the
+ * jump).  The source sums to the created volume, which an outflow side lets
+ * out; without one the operator is singular and the mean of b, the net
+ * source included, is removed.  The mass flux stays set across
+ * mp_poisson_set_geometry (J is recomputed with it) until cleared.  The
+ * first call allocates N f64 on the device; later calls allocate nothing.
+ */
+mp_status mp_poisson_set_mass_flux(mp_handle hd, const double *mdot_dev);
+
 /* Defines: no paper passage (solver configuration, see mp_opts).
  * Replace the options (stream, precision, method, ...). */
 mp_status mp_poisson_set_opts(mp_handle hd, const mp_opts *opts);

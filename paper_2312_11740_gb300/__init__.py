@@ -22,6 +22,7 @@ from .poisson import (  # noqa: F401
     mp_poisson_rhs,
     mp_poisson_rhs_noalloc,
     mp_poisson_set_geometry,
+    mp_poisson_set_mass_flux,
     mp_poisson_set_opts,
     mp_poisson_set_profiling,
     mp_poisson_setup,

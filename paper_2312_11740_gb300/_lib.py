@@ -90,6 +90,7 @@ SIGNATURES = {
     "mp_poisson_setup": (_I, [ctypes.POINTER(_P), mp_grid, _D, _IP, _P, _D, _D, _D,
                               ctypes.POINTER(mp_opts)]),
     "mp_poisson_set_geometry": (_I, [_P, _P, _D, _D, _D]),
+    "mp_poisson_set_mass_flux": (_I, [_P, _P]),
     "mp_poisson_set_opts": (_I, [_P, ctypes.POINTER(mp_opts)]),
     "mp_poisson_solve": (_I, [_P, _P, _P, _D, _IP, _DP, _I, _IP]),
     "mp_poisson_project_step": (_I, [_P, _P, _P, _P, _P, _D, _IP]),

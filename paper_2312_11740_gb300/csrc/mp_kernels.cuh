@@ -159,14 +159,35 @@ __global__ void k_faces(const double *__restrict__ phi, double *__restrict__ bx,
                                  : gfm_beta(phi[at(d, i, j, wlo(k, d.nz))], pc, rl, rg, irl, irg);
 }
 
+// Phase change (evaporation): a liquid-to-gas mass flux mdot makes the
+// normal velocity jump by mdot [1/rho], [1/rho] = 1/rho_g - 1/rho_l, so the
+// pressure flux jumps by B = -mdot_G [1/rho] across an interface face, mdot_G
+// interpolated to the interface point like the curvature.  Solving the two
+// jump conditions with p linear on each side, the row of cell c takes the
+// share beta theta_nb rho_nb B / h of a face to nb (theta_nb the fraction of
+// the c-nb segment in nb's fluid); the two rows of a face take B / h in all.
+__device__ __forceinline__ double flux_jump_B(double pa, double pb, double ma, double mb,
+                                              double jinv) {
+  const double aa = fabs(pa), ab = fabs(pb);
+  return -((ab * ma + aa * mb) / (aa + ab)) * jinv;
+}
+// beta theta_nb rho_nb for the row of cell c (value pc) across a face to nb
+__device__ __forceinline__ double flux_share(double pc, double pnb, double beta, double rl,
+                                             double rg) {
+  return beta * (fabs(pnb) / (fabs(pc) + fabs(pnb))) * (gas(pnb) ? rg : rl);
+}
+
 // -------------------------------------------------------- A3: jump source
 // Flux across a face a->b is beta (p_b - p_a - [p]_{a->b}); moving the known
 // jump to the right-hand side adds +beta [p]_{a->b} to row a and -beta
-// [p]_{a->b} to row b.  Gathered per cell (no atomics); h^2-scaled.
+// [p]_{a->b} to row b.  Gathered per cell (no atomics); h^2-scaled.  With a
+// mass flux (mdot not null) every interface face also adds the row's share
+// of the flux jump (flux_share * B * h after the h^2 scaling).
 __global__ void k_jump(const double *__restrict__ phi, const double *__restrict__ kap,
                        const double *__restrict__ bx, const double *__restrict__ by,
                        const double *__restrict__ bz, double *__restrict__ Jt, Dims d,
-                       double sig) {
+                       double sig, const double *__restrict__ mdot, double rl, double rg,
+                       double h) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
@@ -185,6 +206,19 @@ __global__ void k_jump(const double *__restrict__ phi, const double *__restrict_
   s += bx[xh] * gfm_jump(pc, phi[xh], kc, kap[xh], sig) - bx[c] * gfm_jump(phi[xl], pc, kap[xl], kc, sig);
   s += by[yh] * gfm_jump(pc, phi[yh], kc, kap[yh], sig) - by[c] * gfm_jump(phi[yl], pc, kap[yl], kc, sig);
   s += bz[zh] * gfm_jump(pc, phi[zh], kc, kap[zh], sig) - bz[c] * gfm_jump(phi[zl], pc, kap[zl], kc, sig);
+  if (mdot) {
+    const double jinv = 1.0 / rg - 1.0 / rl, mc = mdot[c];
+    const size_t nb[6] = {xl, xh, yl, yh, zl, zh};
+    const double bf[6] = {bx[c], bx[xh], by[c], by[yh], bz[c], bz[zh]};
+    double f = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const double pn = phi[nb[q]];
+      if (gas(pn) == g || bf[q] == 0.0) continue;  // no interface, or a wall face
+      f += flux_share(pc, pn, bf[q], rl, rg) * flux_jump_B(pc, pn, mc, mdot[nb[q]], jinv);
+    }
+    s = fma(f, h, s);
+  }
   Jt[c] = s;
 }
 
@@ -1314,11 +1348,16 @@ __global__ void k_divergence(const double *__restrict__ ux, const double *__rest
 // ------------------------------------------------- A15: velocity correction
 // u_f -= beta_f (p_b - p_a - [p]_{a->b}) / h on the three low faces of each
 // cell; wall faces have beta = 0 and keep u*.  Planes k0 .. k0 + gridDim.z - 1.
+// With a mass flux (mdot not null) an interface face stores its liquid-side
+// velocity: the flux-jump share of the liquid row is removed from the
+// correction (+share B when the low cell is liquid, -share B when the high
+// cell is).
 __global__ void k_project(const double *__restrict__ p, const double *__restrict__ phi,
                           const double *__restrict__ kap, const double *__restrict__ bx,
                           const double *__restrict__ by, const double *__restrict__ bz,
                           double *__restrict__ ux, double *__restrict__ uy,
-                          double *__restrict__ uz, Dims d, int k0, double sig, double ih) {
+                          double *__restrict__ uz, Dims d, int k0, double sig, double ih,
+                          const double *__restrict__ mdot, double rl, double rg) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z + k0;
   if (i >= d.nx || j >= d.ny) return;
   size_t c = at(d, i, j, k);
@@ -1330,9 +1369,28 @@ __global__ void k_project(const double *__restrict__ p, const double *__restrict
   if (gas(phi[xl]) != g) dx -= gfm_jump(phi[xl], fc, kap[xl], kc, sig);
   if (gas(phi[yl]) != g) dy -= gfm_jump(phi[yl], fc, kap[yl], kc, sig);
   if (gas(phi[zl]) != g) dz -= gfm_jump(phi[zl], fc, kap[zl], kc, sig);
-  ux[c] = fma(-bx[c] * ih, dx, ux[c]);
-  uy[c] = fma(-by[c] * ih, dy, uy[c]);
-  uz[c] = fma(-bz[c] * ih, dz, uz[c]);
+  double vx = fma(-bx[c] * ih, dx, ux[c]);
+  double vy = fma(-by[c] * ih, dy, uy[c]);
+  double vz = fma(-bz[c] * ih, dz, uz[c]);
+  if (mdot) {
+    const double jinv = 1.0 / rg - 1.0 / rl, mc = mdot[c];
+    const size_t nb[3] = {xl, yl, zl};
+    const double bf[3] = {bx[c], by[c], bz[c]};
+    double *v[3] = {&vx, &vy, &vz};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double pa = phi[nb[q]];
+      if (gas(pa) == g || bf[q] == 0.0) continue;
+      const double B = flux_jump_B(pa, fc, mdot[nb[q]], mc, jinv);
+      if (!gas(pa))  // low cell liquid: its side's flux
+        *v[q] += flux_share(pa, fc, bf[q], rl, rg) * B;
+      else           // high cell (this one) liquid
+        *v[q] -= flux_share(fc, pa, bf[q], rl, rg) * B;
+    }
+  }
+  ux[c] = vx;
+  uy[c] = vy;
+  uz[c] = vz;
 }
 
 // ------------------------------------------------ outflow boundary planes

@@ -92,6 +92,8 @@ struct mp_poisson {
   size_t n = 0;
   // fine-level FP64 fields
   double *phi = nullptr, *kap = nullptr, *Jt = nullptr, *b = nullptr;
+  double *mdot = nullptr;  // phase-change mass flux per cell (mp_poisson_set_mass_flux)
+  int has_mdot = 0;
   double *r = nullptr, *z = nullptr, *dv = nullptr, *q = nullptr;
   // fine-level FP32 inner-solve vectors
   float *r32 = nullptr, *e32 = nullptr, *z32 = nullptr, *d32 = nullptr, *q32 = nullptr;
@@ -302,6 +304,9 @@ constexpr int kid(int id64, int id32) {
 }
 
 // ---- reductions
+// the phase-change mass flux the kernels read (null when none is set)
+const double *mdot_of(const mp_poisson *hd) { return hd->has_mdot ? hd->mdot : nullptr; }
+
 mp_status reduce(mp_poisson *hd, int np, int op, int slot, double count = 0.0) {
   LAUNCH(hd, K_REDUCE, 0, np * 8.0, k_reduce, 1, 1024, hd->partial, np, hd->scal, op, slot, count);
   return launch_ok();
@@ -1168,8 +1173,9 @@ mp_status geometry(mp_poisson *hd, const double *phi, double rho_l, double rho_g
          hd->h, hd->per);
   LAUNCH(hd, K_FACES, 0, n0 * 32.0, k_faces, cell_grid(l0.d), kBlock, hd->phi, l0.bx, l0.by,
          l0.bz, l0.d, rho_l, rho_g, 1.0 / rho_l, 1.0 / rho_g, hd->per);
-  LAUNCH(hd, K_JUMP, 0, n0 * 48.0, k_jump, cell_grid(l0.d), kBlock, hd->phi, hd->kap, l0.bx,
-         l0.by, l0.bz, hd->Jt, l0.d, sigma);
+  LAUNCH(hd, K_JUMP, 0, n0 * (hd->has_mdot ? 56.0 : 48.0), k_jump, cell_grid(l0.d), kBlock,
+         hd->phi, hd->kap, l0.bx, l0.by, l0.bz, hd->Jt, l0.d, sigma, mdot_of(hd), rho_l, rho_g,
+         hd->h);
   CKS(launch_ok());
   // faces never exceed 1 / min(rho): scale them so the largest sits in (2^13, 2^14]
   hd->beta_max = std::max(1.0 / rho_l, 1.0 / rho_g);
@@ -1482,6 +1488,25 @@ mp_status mp_poisson_set_geometry(mp_handle hd, const double *phi_dev, double rh
   return geometry(hd, phi_dev, rho_l, rho_g, sigma);
 }
 
+mp_status mp_poisson_set_mass_flux(mp_handle hd, const double *mdot_dev) {
+  if (!hd) return MP_ERR_INVALID_ARG;
+  if (mdot_dev) {
+    if (!hd->mdot) CKS(dalloc(hd, &hd->mdot, hd->n));
+    CK(cudaMemcpyAsync(hd->mdot, mdot_dev, hd->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                       hd->st));
+  }
+  hd->has_mdot = mdot_dev != nullptr;
+  // the jump source of the current geometry, with or without the flux jump
+  Level &l0 = hd->L[0];
+  LAUNCH(hd, K_JUMP, 0, hd->n * (hd->has_mdot ? 56.0 : 48.0), k_jump, cell_grid(l0.d), kBlock,
+         hd->phi, hd->kap, l0.bx, l0.by, l0.bz, hd->Jt, l0.d, hd->sigma, mdot_of(hd), hd->rho_l,
+         hd->rho_g, hd->h);
+  CKS(launch_ok());
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
+}
+
 mp_status mp_poisson_set_opts(mp_handle hd, const mp_opts *opts) {
   if (!hd || !opts || !valid_opts(*opts)) return MP_ERR_INVALID_ARG;
   CK(cudaStreamSynchronize(hd->st));
@@ -1518,7 +1543,8 @@ mp_status mp_poisson_project_step(mp_handle hd, double *ux, double *uy, double *
   if (s != MP_OK) return s;
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
-         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, 0, hd->sigma, 1.0 / hd->h);
+         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, 0, hd->sigma, 1.0 / hd->h, mdot_of(hd),
+         hd->rho_l, hd->rho_g);
   CKS(launch_ok());
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);
@@ -1588,7 +1614,7 @@ mp_status project_step_host(mp_poisson *hd, double *ux_h, double *uy_h, double *
            dim3(cell_grid(d).x, cell_grid(d).y, (unsigned)cnt), kBlock, (const double *)hd->pst,
            (const double *)hd->phi, (const double *)hd->kap, (const double *)l0.bx,
            (const double *)l0.by, (const double *)l0.bz, hd->ux, hd->uy, hd->uz, d, (int)k0,
-           hd->sigma, 1.0 / hd->h);
+           hd->sigma, 1.0 / hd->h, mdot_of(hd), hd->rho_l, hd->rho_g);
     CKS(launch_ok());
     CK(cudaEventRecord(out[s2], hd->st));
     CK(cudaStreamWaitEvent(hd->cs, out[s2], 0));
@@ -1656,7 +1682,8 @@ mp_status mp_poisson_project(mp_handle hd, const double *p, double *ux, double *
   if (hd->outflow) return MP_ERR_INVALID_ARG;  // one boundary face slot per axis
   Level &l0 = hd->L[0];
   LAUNCH(hd, K_PROJECT, 0, hd->n * 96.0, k_project, cell_grid(l0.d), kBlock, p, hd->phi, hd->kap,
-         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, 0, hd->sigma, 1.0 / hd->h);
+         l0.bx, l0.by, l0.bz, ux, uy, uz, l0.d, 0, hd->sigma, 1.0 / hd->h, mdot_of(hd),
+         hd->rho_l, hd->rho_g);
   CKS(launch_ok());
   CK(cudaStreamSynchronize(hd->st));
   prof_resolve(hd);

@@ -140,6 +140,42 @@ def pg_forced(solver, rhs):
     return pg
 
 
+def deflated_errors(solver, guess, p):
+    """Energy errors of a guess against the converged pressure p, for the
+    deflated solver.  Deflated CG corrects any start exactly along the gas
+    components' indicator vectors Z, so what it inherits from a guess is the
+    error in the deflated energy ||e||_D^2 = ||e||_A^2 - (Z^T A e)^T E^-1
+    (Z^T A e), E = Z^T A Z (the A-energy left after the best correction along
+    Z).  Returns (eps_A, eps_D, share): ||e||_A / ||p||_A, ||e||_D / ||p||_D
+    and ||p||_D^2 / ||p||_A^2, the part of the solution's energy that
+    deflation leaves to the iterations.  Diagnostic: A applied through the
+    library, the small dense E and the component sums in torch."""
+    comp, m = solver.components()
+    comp = comp.reshape(-1).long()
+    mask = comp >= 0
+
+    def zt(v):
+        out = torch.zeros(m, dtype=torch.float64, device=v.device)
+        out.index_add_(0, comp[mask], v.reshape(-1)[mask])
+        return out
+
+    E = torch.zeros((m, m), dtype=torch.float64, device=p.device)
+    for a in range(m):
+        E[:, a] = zt(solver.apply((comp == a).to(torch.float64).view(p.shape)))
+
+    def energies(v):
+        Av = solver.apply(v)
+        ea = -float((v * Av).sum())  # A is negative semidefinite
+        if m == 0:
+            return ea, ea
+        y = zt(Av)
+        return ea, ea + float(y @ torch.linalg.solve(E, y))
+
+    pa, pd = energies(p)
+    ea, ed = energies(guess - p)
+    return float(np.sqrt(ea / pa)), float(np.sqrt(max(ed, 0.0) / pd)), pd / pa
+
+
 def evaluate(net, seeds, n, precision=0, stream=None, log=print, deflate=0):
     """Iterations to 1e-10 from the zero guess and from the learned guess,
     and the learned guess's relative error against the converged pressure.
@@ -175,11 +211,16 @@ def evaluate(net, seeds, n, precision=0, stream=None, log=print, deflate=0):
         e = pg - p0
         relA = float(torch.sqrt(torch.abs((e * solver.apply(e)).sum()) /
                                 torch.abs((p0 * solver.apply(p0)).sum())))
+        defl = {}
+        if deflate and st["components"] > 0:
+            eA, eD, share = deflated_errors(solver, pg, p0)
+            defl = dict(guess_rel_energy_err_deflated=eD, deflated_energy_share=share)
         rows.append(dict(seed=seed, zero_iters=it0, net_iters=it1, used_net=st["used_net"],
                          net_relres=st["net_relres"], guess_rel_err=guess_err,
                          diff_vs_zero_guess=err, energy_iters=it2,
                          energy_used=st2["used_net"], guess_rel_energy_err=relA,
-                         diff_energy=float(torch.linalg.norm(p2 - p0) / torch.linalg.norm(p0))))
+                         diff_energy=float(torch.linalg.norm(p2 - p0) / torch.linalg.norm(p0)),
+                         **defl))
     mp_poisson_set_net(solver.handle, None)
     solver.close()
     zero = np.array([r["zero_iters"] for r in rows])
@@ -197,6 +238,12 @@ def evaluate(net, seeds, n, precision=0, stream=None, log=print, deflate=0):
                    energy_check_iterations_saved=float((zero - en).mean()),
                    energy_check_fallback_rate=float(
                        1.0 - np.mean([r["energy_used"] for r in rows])))
+    dl = [r for r in rows if "guess_rel_energy_err_deflated" in r]
+    if dl:
+        summary["median_guess_rel_energy_err_deflated"] = float(
+            np.median([r["guess_rel_energy_err_deflated"] for r in dl]))
+        summary["median_deflated_energy_share"] = float(
+            np.median([r["deflated_energy_share"] for r in dl]))
     if log:
         log("  eval: " + json.dumps(summary))
     return summary, rows

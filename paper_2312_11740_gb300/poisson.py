@@ -83,6 +83,12 @@ def mp_poisson_set_geometry(handle, phi, rho_l, rho_g, sigma):
                                                   float(sigma)), "mp_poisson_set_geometry")
 
 
+def mp_poisson_set_mass_flux(handle, mdot):
+    """Phase-change mass flux per cell (device f64 tensor), or None to clear."""
+    ptr = None if mdot is None else _ptr(mdot)
+    return _check(_lib_().mp_poisson_set_mass_flux(handle, ptr), "mp_poisson_set_mass_flux")
+
+
 def mp_poisson_set_opts(handle, opts):
     return _check(_lib_().mp_poisson_set_opts(handle, ctypes.byref(opts)), "mp_poisson_set_opts")
 
@@ -208,6 +214,11 @@ class Poisson:
 
     def set_geometry(self, phi, rho_l, rho_g, sigma):
         mp_poisson_set_geometry(self.handle, phi.contiguous(), rho_l, rho_g, sigma)
+
+    def set_mass_flux(self, mdot):
+        if mdot is not None and tuple(mdot.shape) != tuple(self.shape):
+            raise ValueError("mass flux must have the grid's shape %s" % (tuple(self.shape),))
+        mp_poisson_set_mass_flux(self.handle, None if mdot is None else mdot.contiguous())
 
     def solve(self, rhs, p=None, tol=1e-10, allow_not_converged=False):
         if p is None:
