@@ -433,22 +433,23 @@ def run_mine(args, rank, world, local_rank):
             traffic = None
     total_prof_ms = sum(e["total_ms"] for e in prof)
 
-    def mode_line(r, k):
+    def mode_line(r, k, name):
         d = {"solves_per_s": job_value(world, k, r["ms"]), "ms_per_step": r["ms"] / k,
              "iterations": r["iters"], "outer_steps_last": r["outer"],
              "max_relres": r["relres"], "levels": r["levels"], "components": r["components"]}
-        if r["guess_used"] and any(r["guess_used"]):
-            d["learned_guess_kept"] = sum(r["guess_used"])
+        if name == "learned":  # timed steps whose learned guess passed the residual check
+            d["learned_guess_kept"] = int(sum(r["guess_used"] or []))
+            d["learned_guess_offered"] = len(r["guess_used"] or [])
         return d
 
-    modes_out = {k: mode_line(v, K) for k, v in results.items()}
+    modes_out = {k: mode_line(v, K, k) for k, v in results.items()}
     if "fp64" in results:
         for k in results:
             if k != "fp64":
                 modes_out["%s_over_fp64" % k] = results["fp64"]["ms"] / results[k]["ms"]
     if secondary:
         k2 = min(K, 10)
-        sec = {k: mode_line(v, k2) for k, v in secondary.items()}
+        sec = {k: mode_line(v, k2, k) for k, v in secondary.items()}
         for k in ("mixed", "learned"):
             sec["%s_over_fp64" % k] = secondary["fp64"]["ms"] / secondary[k]["ms"]
         sec["workload"] = workload_desc(SECONDARY, n)

@@ -138,6 +138,15 @@ mp_status mp_net_forward(mp_net_handle net, float *q_dev);
 mp_status mp_net_train_step(mp_net_handle net, const float *q_target_dev, float lr, int step,
                             double *loss_out);
 
+/* Defines: no paper passage (the paper has no learned component); training
+ * checkpoint and resume.
+ * Adam's first and second moment estimates (device FP32, param_count each):
+ * get copies them out, set restores them (call after mp_net_set_params,
+ * which zeroes them).  With the parameters, the step count and the sample
+ * order they make a checkpoint from which training resumes exactly. */
+mp_status mp_net_get_adam(mp_net_handle net, float *m_dev, float *v_dev);
+mp_status mp_net_set_adam(mp_net_handle net, const float *m_dev, const float *v_dev);
+
 /*
  * Defines: no paper passage (the paper has no learned component); the training loss;
  * the energy norm uses the ghost-fluid operator of the solve (varDens,

@@ -114,6 +114,8 @@ SIGNATURES = {
     "mp_net_param_count": (ctypes.c_size_t, [_P]),
     "mp_net_launches": (ctypes.c_ulonglong, [_P]),
     "mp_net_set_params": (_I, [_P, _P]),
+    "mp_net_get_adam": (_I, [_P, _P, _P]),
+    "mp_net_set_adam": (_I, [_P, _P, _P]),
     "mp_net_get_params": (_I, [_P, _P]),
     "mp_net_features": (_I, [_P, _P, _P, _D, _D, _DP]),
     "mp_net_get_input2": (_I, [_P, _P]),

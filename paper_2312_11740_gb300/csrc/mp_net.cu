@@ -1606,6 +1606,26 @@ mp_status mp_net_get_params(mp_net_handle net, float *p) {
   return MP_OK;
 }
 
+mp_status mp_net_get_adam(mp_net_handle net, float *m, float *v) {
+  if (!net || !m || !v) return MP_ERR_INVALID_ARG;
+  NCK(cudaMemcpyAsync(m, net->adam_m, net->nparam * sizeof(float), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCK(cudaMemcpyAsync(v, net->adam_v, net->nparam * sizeof(float), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
+mp_status mp_net_set_adam(mp_net_handle net, const float *m, const float *v) {
+  if (!net || !m || !v) return MP_ERR_INVALID_ARG;
+  NCK(cudaMemcpyAsync(net->adam_m, m, net->nparam * sizeof(float), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCK(cudaMemcpyAsync(net->adam_v, v, net->nparam * sizeof(float), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  return MP_OK;
+}
+
 mp_status mp_net_set_loss(mp_net_handle net, int kind, double rho_l, double rho_g,
                           const mp_bc bc[3]) {
   if (!net || !(kind == 0 || kind == 1) || !(rho_l > 0.0) || !(rho_g > 0.0) || !bc)

@@ -1432,7 +1432,7 @@ void mp_opts_default(mp_opts *o) {
   o->nu1 = 2;
   o->nu2 = 2;
   o->nu_growth = 2;
-  o->nu_max = 8;
+  o->nu_max = 12;
   o->inner_rtol = 3e-3;
   o->inner_max = 12;
   o->net_check = 0;

@@ -22,6 +22,10 @@ guess's relative L2 and A-norm errors.
 
     python -m paper_2312_11740_gb300.learn --n 128 --train 2000 --epochs 3 \\
         --eval 200 --out net128.npz
+
+--checkpoint PATH writes a checkpoint after every epoch (parameters, Adam's
+moments, step, sample-order generator state, losses); --resume PATH continues
+such a run at its epoch boundary, bit for bit as if it had not stopped.
 """
 from __future__ import annotations
 
@@ -111,16 +115,51 @@ def init_params(net, seed):
     return torch.from_numpy(vec).cuda()
 
 
-def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None, loss="energy"):
-    """Adam over shuffled samples; returns the loss history (one per step)."""
+def save_checkpoint(path, net, step, epoch, rng, losses, config):
+    """Everything training needs to resume exactly at an epoch boundary:
+    parameters, Adam's moments, the step count (Adam's bias correction and
+    the learning-rate schedule), the epochs done, the sample-order generator's
+    state, the loss history and the run's configuration.  Written to a
+    temporary file and renamed, so a crash leaves the previous checkpoint."""
+    m, v = net.get_adam()
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, params=net.get_params().cpu().numpy(), adam_m=m.cpu().numpy(),
+             adam_v=v.cpu().numpy(), step=np.int64(step), epoch=np.int64(epoch),
+             rng=np.array(json.dumps(rng.bit_generator.state)), losses=np.array(losses),
+             config=np.array(json.dumps(config, sort_keys=True)))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path, net, device="cuda"):
+    """Restore parameters and Adam's moments into net; returns (step, epoch,
+    rng state, losses, config)."""
+    d = np.load(path)
+    net.set_params(torch.from_numpy(d["params"]).to(device))
+    net.set_adam(torch.from_numpy(d["adam_m"]).to(device), torch.from_numpy(d["adam_v"]).to(device))
+    return (int(d["step"]), int(d["epoch"]), json.loads(str(d["rng"])), list(d["losses"]),
+            json.loads(str(d["config"])))
+
+
+def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None, loss="energy",
+          checkpoint=None, resume=None, device="cuda"):
+    """Adam over shuffled samples; returns the loss history (one per step).
+    checkpoint: path written after every epoch; resume: a checkpoint of the
+    same run (same samples, epochs, schedule and seed) to continue from."""
     rng = np.random.Generator(np.random.PCG64(seed))
     count = X.shape[0]
+    config = dict(count=int(count), epochs=int(epochs), lr=float(lr), seed=int(seed),
+                  lr_final=None if lr_final is None else float(lr_final), loss=loss)
     net.set_loss(1 if loss == "energy" else 0, RHO_L, RHO_G, BC)
     losses = []
-    step = 0
+    step, first = 0, 0
+    if resume:
+        step, first, state, losses, saved = load_checkpoint(resume, net, device)
+        if saved != config:
+            raise ValueError("checkpoint of a different run: %s vs %s" % (saved, config))
+        rng.bit_generator.state = state
     total = epochs * count
     t0 = time.time()
-    for ep in range(epochs):
+    for ep in range(first, epochs):
         order = rng.permutation(count)
         for k in order:
             step += 1
@@ -130,6 +169,8 @@ def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None, loss="energy"):
         if log:
             log("  epoch %d  mean loss %.4e  %.1fs" % (ep + 1, float(np.mean(losses[-count:])),
                                                        time.time() - t0))
+        if checkpoint:
+            save_checkpoint(checkpoint, net, step, ep + 1, rng, losses, config)
     return losses
 
 
@@ -264,6 +305,8 @@ def main(argv=None):
     ap.add_argument("--deflate", type=int, choices=(0, 1), default=0,
                     help="solver form the evaluation compares against (0: plain MG-PCG)")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--checkpoint", default=None, help="written after every epoch")
+    ap.add_argument("--resume", default=None, help="checkpoint of this run to continue from")
     ap.add_argument("--report", default=None)
     a = ap.parse_args(argv)
     torch.cuda.set_device(0)
@@ -276,7 +319,8 @@ def main(argv=None):
     net.set_params(init_params(net, a.init_seed))
     print("train: %d epochs" % a.epochs, flush=True)
     t1 = time.time()
-    losses = train(net, X, Q, a.epochs, a.lr, a.init_seed, lr_final=a.lr_final, loss=a.loss)
+    losses = train(net, X, Q, a.epochs, a.lr, a.init_seed, lr_final=a.lr_final, loss=a.loss,
+                   checkpoint=a.checkpoint, resume=a.resume)
     t_train = time.time() - t1
     del X, Q
     torch.cuda.empty_cache()

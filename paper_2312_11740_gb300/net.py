@@ -82,6 +82,20 @@ class Net:
         _check(_lib_().mp_net_get_params(self.handle, _ptr(p, torch.float32)), "mp_net_get_params")
         return p
 
+    def get_adam(self):
+        """Adam's moment estimates (m, v), device FP32 copies."""
+        m = torch.empty(self.param_count(), dtype=torch.float32, device="cuda")
+        v = torch.empty_like(m)
+        _check(_lib_().mp_net_get_adam(self.handle, _ptr(m, torch.float32),
+                                       _ptr(v, torch.float32)), "mp_net_get_adam")
+        return m, v
+
+    def set_adam(self, m, v):
+        """Restore Adam's moments (after set_params, which zeroes them)."""
+        n = self.param_count()
+        _check(_lib_().mp_net_set_adam(self.handle, _ptr(m, torch.float32, n),
+                                       _ptr(v, torch.float32, n)), "mp_net_set_adam")
+
     def set_input(self, x16):
         _check(_lib_().mp_net_set_input(self.handle, _ptr(x16, torch.bfloat16, self.n * 16)),
                "mp_net_set_input")

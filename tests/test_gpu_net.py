@@ -563,6 +563,45 @@ def test_learned_guess_cannot_pay_against_the_deflated_solver():
         assert r["good_start"] < r["zero"]
 
 
+def test_training_resumes_bit_for_bit_from_a_checkpoint(tmp_path, monkeypatch):
+    """A two-epoch training run stopped after its first epoch and resumed
+    from the checkpoint in a fresh network ends with the same parameters,
+    Adam moments and losses, bit for bit, as the run that did not stop (the
+    kernels reduce in a fixed order)."""
+    from paper_2312_11740_gb300 import learn
+    n = 32
+    X, Q, _ = learn.make_dataset([10000, 10001, 10002], n, log=None)
+    ref = Net(n, n, n)
+    ref.set_params(learn.init_params(ref, 7))
+    l_ref = learn.train(ref, X, Q, 2, 1e-3, 7, log=None, lr_final=1e-4)
+    ck1 = str(tmp_path / "after_epoch1.npz")
+    orig = learn.save_checkpoint
+
+    class Stop(Exception):
+        pass
+
+    def save_then_stop(path, net, step, epoch, rng, losses, config):
+        orig(ck1, net, step, epoch, rng, losses, config)
+        raise Stop()
+
+    first = Net(n, n, n)
+    first.set_params(learn.init_params(first, 7))
+    monkeypatch.setattr(learn, "save_checkpoint", save_then_stop)
+    with pytest.raises(Stop):
+        learn.train(first, X, Q, 2, 1e-3, 7, log=None, lr_final=1e-4,
+                    checkpoint=str(tmp_path / "ck.npz"))
+    monkeypatch.setattr(learn, "save_checkpoint", orig)
+    first.close()
+    res = Net(n, n, n)
+    l_res = learn.train(res, X, Q, 2, 1e-3, 7, log=None, lr_final=1e-4, resume=ck1)
+    assert l_res == l_ref
+    assert torch.equal(res.get_params(), ref.get_params())
+    for u, w in zip(res.get_adam(), ref.get_adam()):
+        assert torch.equal(u, w)
+    ref.close()
+    res.close()
+
+
 def test_conv_wait_timeout_is_reported_and_the_network_stays_usable():
     """The bounded waits of the tcgen05 convolution: with the test switch the
     first staging-barrier wait of every CTA of the next launch counts as timed
