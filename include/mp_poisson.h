@@ -113,6 +113,11 @@ typedef struct {
                         labelling (default 8192; walks are a few steps long in practice).
                         A geometry whose labelling reaches it is solved without deflation
                         (mp_stats.components = 0). */
+  int coarse_cluster; /* FP32 V-cycle: 1 (default) runs the level above the one-CTA tail and
+                        every coarser level as one launch of an 8-CTA thread-block cluster
+                        (distributed shared memory, cluster barriers between steps) where
+                        the levels' z-planes split evenly; 0 = per-level launches down to
+                        the one-CTA tail.  Same method, slightly different rounding. */
   void *stream;      /* cudaStream_t; NULL = legacy default stream. */
 } mp_opts;
 

@@ -48,6 +48,7 @@ class mp_opts(ctypes.Structure):
         ("deflate", ctypes.c_int),
         ("smoother", ctypes.c_int),
         ("label_limit", ctypes.c_int),
+        ("coarse_cluster", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 

@@ -20,6 +20,7 @@
 #include "../../include/mp_poisson.h"
 #include "mp_kernels.cuh"
 #include "mp_sweep.cuh"
+#include "mp_ctail.cuh"
 #include "mp_deflate.cuh"
 
 using namespace mp;
@@ -50,7 +51,7 @@ struct Level {
 
 enum KernelId {
   K_CURV, K_FACES, K_JUMP, K_DIAG, K_COARSEN, K_DENSE, K_GJ,
-  K_RBGS64, K_RBGS32, K_RBGS32F, K_TAIL64, K_TAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
+  K_RBGS64, K_RBGS32, K_RBGS32F, K_TAIL64, K_TAIL32, K_CTAIL32, K_RESTR64, K_RESTR32, K_PROL64, K_PROL32, K_COARSE64, K_COARSE32,
   K_APPLY64, K_APPLY32, K_RESID64, K_RESID32, K_RESIDMIX, K_DOT64, K_DOT32, K_AXPY64, K_AXPY32,
   K_XPBY64, K_XPBY32, K_ADD64, K_ADD32, K_ADDF32, K_SUM, K_SUBMEAN, K_REDUCE, K_ASSEMBLE,
   K_ASSEMBLE_U, K_PROJECT, K_DIV, K_SCALE, K_DEFL, K_DEFL_LABEL, K_DEFL_DOT, K_COUNT
@@ -58,6 +59,7 @@ enum KernelId {
 const char *const kKernelNames[K_COUNT] = {
   "curvature", "gfm_faces", "jump", "diag", "coarsen_faces", "dense_build", "gauss_jordan",
   "rbgs_f64", "rbgs_f32", "rbgs_f32_fused", "coarse_tail_f64", "coarse_tail_f32",
+  "coarse_cluster_f32",
   "resid_restrict_f64", "resid_restrict_f32", "prolong_f64",
   "prolong_f32", "coarse_solve_f64", "coarse_solve_f32io", "apply_dot_f64", "apply_dot_f32",
   "residual_f64", "residual_f32", "residual_mixed", "dot_f64", "dot_f32", "axpy2_f64",
@@ -66,6 +68,7 @@ const char *const kKernelNames[K_COUNT] = {
   "deflation_band", "deflation_label", "deflation_dot"};
 constexpr int MAX_LEVELS = 16;
 constexpr int TAIL32_NU_MAX = 4;  // sweeps per level in the one-CTA FP32 tail
+constexpr size_t CT_SMEM_MAX = 200 * 1024;  // shared memory per CTA of the cluster tail
 constexpr int EVENT_POOL = 4096;
 constexpr int MAX_SLABS = 8;  // z-slabs of the host-buffer step's copy pipeline
 
@@ -143,6 +146,10 @@ struct mp_poisson {
   cudaEvent_t xev[2 * MAX_SLABS + 2] = {};
   // first level of the one-CTA coarse tail per precision, and its smem bytes
   int tail64 = 0, tail32 = 0;
+  // FP32 cluster tail (mp_ctail.cuh): its top level (-1: not used), shared memory per
+  // CTA and the offset of its coarsest-rhs scratch
+  int ctail32 = -1, ctail_scratch = 0;
+  size_t ctail_bytes = 0;
   size_t tail64_bytes = 0, tail32_bytes = 0;
   bool capturing = false;
   std::vector<int> cap_ids, cap_levels;
@@ -343,6 +350,50 @@ template <> struct LV<float> {
   static float *dd(Level &l) { return l.dd32; }
 };
 
+// The FP32 cluster tail from level l down (one launch of a CT_CTAS cluster).
+mp_status ctail_launch(mp_poisson *hd, int l, const float *rhs, float *x) {
+  CtArgs a{};
+  a.nlev = (int)hd->L.size() - l;
+  a.Minv = hd->Minv;
+  a.singular = hd->outflow == 0;
+  int off = 0;
+  double bytes = 0.0;
+  for (int q = 0; q < a.nlev; ++q) {
+    Level &t = hd->L[l + q];
+    // the levels the one-CTA tail would take keep its sweep cap
+    const int cap = l + q >= hd->tail32 ? TAIL32_NU_MAX : 1 << 20;
+    const int ppc = std::max(1, t.d.nz / CT_CTAS);
+    a.lv[q] = CtLevel{t.d, (int)t.n, std::min(t.nu1, cap), std::min(t.nu2, cap), ppc, off,
+                      t.bx32, t.by32, t.bz32, t.idiag32, hd->outflow ? t.dd32 : nullptr};
+    off += ct_slab_floats(t.d, ppc, hd->outflow != 0);
+    bytes += 16.0 * t.n;
+  }
+  prof_begin(hd, K_CTAIL32, l);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CT_CTAS);
+  cfg.blockDim = dim3(CTL_THREADS);
+  cfg.dynamicSmemBytes = hd->ctail_bytes;
+  cfg.stream = hd->st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CT_CTAS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = hd->prof_on ? 1 : 2;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_ctail, a, hd->ctail_scratch, rhs, x);
+  if (e != cudaSuccess && cfg.numAttrs == 2) {  // without the programmatic launch
+    cudaGetLastError();
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_ctail, a, hd->ctail_scratch, rhs, x);
+  }
+  prof_end(hd, K_CTAIL32, l, bytes);
+  if (e != cudaSuccess) return MP_ERR_CUDA;
+  return launch_ok();
+}
+
 // One symmetric V-cycle with zero initial guess: x ~= At^-1 rhs on level l.
 // Pre-smoothing sweeps red then black, post-smoothing black then red (the
 // adjoint), so the cycle is a symmetric preconditioner.  Each colour is one
@@ -351,6 +402,9 @@ template <> struct LV<float> {
 template <typename T>
 mp_status vcycle(mp_poisson *hd, int l, const T *rhs, T *x) {
   Level &lv = hd->L[l];
+  if constexpr (sizeof(T) == 4) {
+    if (l == hd->ctail32 && hd->opts.coarse_cluster) return ctail_launch(hd, l, rhs, x);
+  }
   const int tail = sizeof(T) == 8 ? hd->tail64 : hd->tail32;
   if (l == tail && l < (int)hd->L.size() - 1) {
     TailArgs a{};
@@ -1128,7 +1182,7 @@ bool valid_opts(const mp_opts &o) {
          o.nu2 >= 1 && o.nu_growth >= 1 && o.nu_max >= 1 && o.inner_rtol > 0.0 &&
          o.inner_rtol < 1.0 && o.inner_max >= 1 && (o.net_check == 0 || o.net_check == 1) &&
          (o.deflate == 0 || o.deflate == 1) && (o.smoother == 0 || o.smoother == 1) &&
-         o.label_limit >= 1;
+         o.label_limit >= 1 && (o.coarse_cluster == 0 || o.coarse_cluster == 1);
 }
 
 void apply_nu(mp_poisson *hd) {
@@ -1260,6 +1314,49 @@ mp_status fused_setup(mp_poisson *hd) {
     }
     CKS(dalloc(hd, &lv.t32, lv.n));
   }
+  return MP_OK;
+}
+
+// FP32 cluster tail (mp_ctail.cuh): the level above the one-CTA tail and every
+// level below it in the shared memory of a CT_CTAS-CTA cluster, when every
+// level's z-planes split evenly, the slabs fit and the device runs the cluster
+mp_status ctail_setup(mp_poisson *hd) {
+  hd->ctail32 = -1;
+  const int nl = (int)hd->L.size(), top = hd->tail32 - 1;
+  if (top < 0 || hd->tail32 >= nl - 1 || nl - top > CT_MAX_LEVELS) return MP_OK;
+  if (hd->L.back().n > (size_t)CT_MAX_COARSE) return MP_OK;
+  size_t floats = 0;
+  for (int l = top; l < nl; ++l) {
+    const Dims &d = hd->L[l].d;
+    if (d.nz > CT_CTAS && d.nz % CT_CTAS != 0) return MP_OK;
+    floats += ct_slab_floats(d, std::max(1, d.nz / CT_CTAS), hd->outflow != 0);
+  }
+  const size_t bytes = (floats + CT_MAX_COARSE) * sizeof(float);
+  if (bytes > CT_SMEM_MAX) return MP_OK;
+  if (cudaFuncSetAttribute(k_ctail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return MP_OK;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CT_CTAS);
+  cfg.blockDim = dim3(CTL_THREADS);
+  cfg.dynamicSmemBytes = bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CT_CTAS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_ctail, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return MP_OK;
+  }
+  hd->ctail32 = top;
+  hd->ctail_bytes = bytes;
+  hd->ctail_scratch = (int)floats;
   return MP_OK;
 }
 
@@ -1407,6 +1504,7 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
   }
   // fused FP32 sweep: levels above the one-CTA tail with nx a multiple of 8
   CKS(fused_setup(hd));
+  CKS(ctail_setup(hd));
   CK(cudaFuncSetAttribute(k_inverse_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)((GJ_SMEM_MAX + 1) * GJ_SMEM_MAX * sizeof(double))));
   CK(cudaFuncSetAttribute(k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1439,6 +1537,7 @@ void mp_opts_default(mp_opts *o) {
   o->deflate = 1;
   o->smoother = 1;
   o->label_limit = 8192;
+  o->coarse_cluster = 1;
   o->stream = nullptr;
 }
 

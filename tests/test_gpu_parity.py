@@ -510,11 +510,13 @@ def test_fused_sweep_bitwise_equals_per_colour_launches(name, opts):
     tiles that overhang the grid (nx = 40 < 64, ny = 24 = 3 tiles), wall and
     periodic axes in x, y and z, an odd number of sweeps (the last one per
     colour), a 128^3 pool with many z-chunks per tile, and the stationary
-    V-cycle iteration."""
+    V-cycle iteration.  The small grids run without the cluster tail, which
+    would otherwise take every level the fused sweep runs on."""
     if name == "pool128":
         phi, u, prm = _pool_case(128)
     else:
         phi, u, prm = case(name)
+        opts = dict(opts, coarse_cluster=0)
     rhs = dev(oracle.divergence(*u, prm["h"]))
     out = []
     for smoother in (1, 0):
@@ -716,3 +718,38 @@ def test_mass_flux_projection_matches_oracle(name):
     # singular problem: the mean of b (the created volume) is spread over every cell
     assert np.abs(div[liquid] - div[liquid].mean()).max() <= 1e-8 * np.linalg.norm(ref["b"])
     s.close()
+
+
+# ------------------------------------------------ cluster coarse tail
+@pytest.mark.parametrize("name", ["bubble32", "periodic", "pool128"])
+def test_cluster_tail_matches_per_level_launches(name):
+    """The FP32 coarse tail on an 8-CTA thread-block cluster (coarse_cluster
+    = 1) runs the same V-cycle as the per-level launches down to the one-CTA
+    tail, except that its top level smooths on FP32 instead of FP16 faces:
+    one stationary V-cycle from zero agrees to 1e-2, the kernel does run, and
+    both forms solve to the target with the oracle's pressure and iteration
+    counts within two."""
+    if name == "pool128":
+        phi, u, prm = _pool_case(128)
+    else:
+        phi, u, prm = case(name)
+    h, bc = prm["h"], prm["bc"]
+    rhs = dev(oracle.divergence(*u, h))
+    out = {}
+    for cl in (1, 0):
+        s = make(phi, prm, precision=1, coarse_cluster=cl, method=1, max_iters=1)
+        p1, _, _ = s.solve(rhs, tol=TOL, allow_not_converged=True)
+        ran = sum(e["launches"] for e in s.profile() if e["name"] == "coarse_cluster_f32")
+        s.set_opts(precision=1, coarse_cluster=cl, method=0, max_iters=200)
+        p, it, _ = s.solve(rhs, tol=TOL)
+        assert s.stats()["relres"] <= TOL
+        out[cl] = (host(p1), host(p), it, ran)
+        s.close()
+    assert out[1][3] > 0 and out[0][3] == 0
+    assert rel_l2(out[1][0], out[0][0]) < 1e-2
+    assert abs(out[1][2] - out[0][2]) <= 2
+    if name != "pool128":
+        ref = oracle.solve(phi, oracle.divergence(*u, h), h, prm["rho_l"], prm["rho_g"],
+                           prm["sigma"], bc, tol=REF_TOL)
+        for cl in (1, 0):
+            assert rel_l2(out[cl][1], ref["p"]) < PARITY
