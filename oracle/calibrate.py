@@ -41,7 +41,7 @@ def measure(name):
     return {"n": int(phi.shape[0]), "iterations": int(res["iters"]), "relres": float(res["relres"]),
             "seconds": dt,
             "threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
-            "host": "%s %s" % (platform.machine(), platform.processor() or ""),
+            "host": platform.machine(),
             "tol": TOL}
 
 
