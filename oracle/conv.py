@@ -331,3 +331,77 @@ def energy_loss(q, t, f0, rho_l, rho_g, bc):
     L = 1.0 - a * a / (c * d)
     grad = -2.0 * a * At / (c * d) + 2.0 * a * a * Aq / (c * c * d)
     return L, grad
+
+
+def gas_components(phi, bc):
+    """Connected gas regions (phi > 0) with face neighbours, periodic axes
+    wrapped: (labels, m), labels -1 in liquid and 0..m-1 in gas, numbered in
+    the order of each component's lowest cell index (C order).  The labelling
+    is scipy.ndimage.label (6-connectivity); components that touch across a
+    periodic boundary are merged with a small union-find over label pairs."""
+    from scipy import ndimage
+    gas = np.asarray(phi) > 0.0
+    lab, m = ndimage.label(gas)
+    parent = list(range(m + 1))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for axis in range(3):
+        if bc[axis] != 0:  # not periodic
+            continue
+        ax = 2 - axis
+        lo, hi = np.take(lab, 0, axis=ax), np.take(lab, -1, axis=ax)
+        for a, b in zip(lo[(lo > 0) & (hi > 0)], hi[(lo > 0) & (hi > 0)]):
+            ra, rb = find(int(a)), find(int(b))
+            if ra != rb:
+                parent[max(ra, rb)] = min(ra, rb)
+    roots = np.array([find(int(v)) for v in range(m + 1)])
+    flat = np.where(lab.ravel() > 0, roots[lab.ravel()], 0)
+    order, first = [], {}
+    for c, r in enumerate(flat):
+        if r and r not in first:
+            first[r] = len(order)
+            order.append(r)
+    out = np.full(flat.shape, -1, dtype=np.int64)
+    for r, k in first.items():
+        out[flat == r] = k
+    return out.reshape(lab.shape), len(order)
+
+
+def deflated_energy_loss(q, t, phi, h, rho_l, rho_g, bc):
+    """The training loss of a guess for the deflated solver: deflated CG
+    corrects any start exactly along the gas components' indicator vectors Z,
+    so what it inherits is the error's energy in D = A - A Z E^-1 Z^T A,
+    E = Z^T A Z (A the positive semidefinite ghost-fluid operator, minus the
+    C oracle's).  With a = q.Dt, c = q.Dq, d = t.Dt:
+
+        L = 1 - a^2 / (c d),   dL/dq = -2 a Dt / (c d) + 2 a^2 Dq / (c^2 d),
+
+    the relative D-energy error of the best multiple of q.  The component
+    projection is formed with a dense solve of the small E.  Returns (L, dL/dq)."""
+    from . import apply, faces
+    q = np.asarray(q, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    f = faces(np.asarray(phi, dtype=np.float64), rho_l, rho_g, bc)
+    A = lambda v: -apply(f, v, h, bc)  # noqa: E731
+    lab, m = gas_components(phi, bc)
+    Z = np.stack([(lab == j).astype(np.float64) for j in range(m)]) if m else np.zeros((0,) + q.shape)
+    AZ = np.stack([A(z) for z in Z]) if m else Z
+    E = np.einsum("ixyz,jxyz->ij", Z, AZ) if m else np.zeros((0, 0))
+
+    def D(v):
+        Av = A(v)
+        if not m:
+            return Av
+        c = np.linalg.solve(E, np.einsum("ixyz,xyz->i", AZ, v))
+        return Av - np.einsum("i,ixyz->xyz", c, AZ)
+
+    Dq, Dt = D(q), D(t)
+    a, c, d = float(np.sum(q * Dt)), float(np.sum(q * Dq)), float(np.sum(t * Dt))
+    L = 1.0 - a * a / (c * d)
+    grad = -2.0 * a * Dt / (c * d) + 2.0 * a * a * Dq / (c * c * d)
+    return L, grad

@@ -287,3 +287,112 @@ def test_adam_two_steps_closed_form():
     vhat = (0.999 * 0.001 * g1 * g1 + 0.001 * g2 * g2) / (1 - 0.999 ** 2)
     assert p1[0] == pytest.approx(p0 - lr * g1 / (abs(g1) + 1e-8), rel=1e-14)
     assert p2[0] == pytest.approx(p1[0] - lr * mhat / (np.sqrt(vhat) + 1e-8), rel=1e-14)
+
+
+# ------------------------------------------- the deflated energy loss
+def _bfs_components(gas, bc):
+    """Brute-force flood fill with face neighbours (periodic axes wrapped):
+    the partition of the gas cells, as a set of frozensets of flat indices."""
+    nz, ny, nx = gas.shape
+    seen = np.zeros_like(gas, dtype=bool)
+    comps = set()
+    for start in zip(*np.nonzero(gas)):
+        if seen[start]:
+            continue
+        stack, members = [start], []
+        seen[start] = True
+        while stack:
+            k, j, i = stack.pop()
+            members.append((k * ny + j) * nx + i)
+            for ax, n in ((2, nx), (1, ny), (0, nz)):
+                for s in (-1, 1):
+                    c = [k, j, i]
+                    c[ax] += s
+                    axis = 2 - ax
+                    if not 0 <= c[ax] < n:
+                        if bc[axis] != 0:
+                            continue
+                        c[ax] %= n
+                    c = tuple(c)
+                    if gas[c] and not seen[c]:
+                        seen[c] = True
+                        stack.append(c)
+        comps.add(frozenset(members))
+    return comps
+
+
+def _defl_case(seed=3, n=8):
+    import synth
+    h = 1.0 / n
+    bc = (0, 0, 1)
+    # a bubble across the periodic x boundary, one inside, one touching the z wall
+    phi = synth.level_set((n, n, n), h, [((0.02, 0.5, 0.5), 0.2), ((0.5, 0.4, 0.45), 0.18),
+                                         ((0.6, 0.75, 0.12), 0.15)], bc=bc)
+    g = rng(seed)
+    return phi, h, bc, g.standard_normal(phi.shape), g.standard_normal(phi.shape)
+
+
+def test_gas_components_match_flood_fill():
+    phi, h, bc, _, _ = _defl_case()
+    lab, m = conv.gas_components(phi, bc)
+    ours = {frozenset(np.flatnonzero(lab.ravel() == j)) for j in range(m)}
+    assert m >= 2 and ours == _bfs_components(phi > 0, bc)
+    # numbered by each component's lowest cell
+    firsts = [np.flatnonzero(lab.ravel() == j)[0] for j in range(m)]
+    assert firsts == sorted(firsts)
+
+
+def test_deflated_energy_invariances_and_plain_limit():
+    """D annihilates the component indicators (and constants), so adding any
+    Z c + const to q changes nothing; scaling q changes nothing; with no gas
+    the loss is the plain energy loss."""
+    phi, h, bc, q, t = _defl_case(5)
+    L, _ = conv.deflated_energy_loss(q, t, phi, h, 1.0, 1e-3, bc)
+    lab, m = conv.gas_components(phi, bc)
+    shift = sum(float(c) * (lab == j) for j, c in enumerate(rng(6).standard_normal(m))) + 0.7
+    assert conv.deflated_energy_loss(q + shift, t, phi, h, 1.0, 1e-3, bc)[0] == pytest.approx(L, rel=1e-9)
+    assert conv.deflated_energy_loss(-3.5 * q, t, phi, h, 1.0, 1e-3, bc)[0] == pytest.approx(L, rel=1e-12)
+    liquid = -np.ones_like(phi)
+    Ld, gd = conv.deflated_energy_loss(q, t, liquid, h, 1.0, 1e-3, bc)
+    Lp, gp = conv.energy_loss(q, t, liquid, 1.0, 1e-3, bc)
+    # (the gradient does not depend on the scale of the operator)
+    assert Ld == pytest.approx(Lp, rel=1e-12) and np.allclose(gd, gp, rtol=1e-9, atol=1e-12)
+
+
+def test_deflated_energy_is_the_best_correction_by_brute_force():
+    """L = min over (alpha, c) of ||alpha q - t - Z c||_A^2 / min over c of
+    ||t - Z c||_A^2, both minima found by a general-purpose optimiser (no E)."""
+    from scipy.optimize import minimize
+    from oracle import apply, faces
+    phi, h, bc, q, t = _defl_case(7)
+    L, _ = conv.deflated_energy_loss(q, t, phi, h, 1.0, 1e-3, bc)
+    f = faces(phi, 1.0, 1e-3, bc)
+    lab, m = conv.gas_components(phi, bc)
+    Z = [(lab == j).astype(float) for j in range(m)]
+
+    def en(v):
+        return float(np.sum(v * -apply(f, v, h, bc)))
+
+    def num(x):
+        return en(x[0] * q - t - sum(c * z for c, z in zip(x[1:], Z)))
+
+    def den(x):
+        return en(t - sum(c * z for c, z in zip(x, Z)))
+
+    top = minimize(num, np.zeros(m + 1), method="BFGS", options={"gtol": 1e-10}).fun
+    bot = minimize(den, np.zeros(m), method="BFGS", options={"gtol": 1e-10}).fun
+    assert top / bot == pytest.approx(L, rel=1e-6)
+
+
+def test_deflated_energy_gradient_finite_difference():
+    phi, h, bc, q, t = _defl_case(9)
+    q = t + 0.5 * q
+    L, gq = conv.deflated_energy_loss(q, t, phi, h, 1.0, 1e-3, bc)
+    assert 0.05 < L < 0.95
+    eps = 1e-5
+    g = rng(10)
+    for _ in range(3):
+        d = g.standard_normal(q.shape)
+        fd = (conv.deflated_energy_loss(q + eps * d, t, phi, h, 1.0, 1e-3, bc)[0] -
+              conv.deflated_energy_loss(q - eps * d, t, phi, h, 1.0, 1e-3, bc)[0]) / (2 * eps)
+        assert fd == pytest.approx(np.sum(gq * d), rel=1e-6)
