@@ -176,6 +176,13 @@ mp_status mp_net_set_loss(mp_net_handle net, int kind, double rho_l, double rho_
 mp_status mp_net_loss_grad(mp_net_handle net, const float *q_target_dev, float *gq_dev,
                            double *loss_out);
 
+/* Defines: no paper passage (the paper has no learned component); training on a
+ * loss formed outside the network (the deflated energy of mp_poisson_deflated_energy).
+ * One Adam step (as mp_net_train_step) from the gradient gq_dev = dL/dq (device FP32,
+ * N) of the network output for the current input: forward, backward from gq_dev,
+ * update. */
+mp_status mp_net_train_step_grad(mp_net_handle net, const float *gq_dev, float lr, int step);
+
 /* Defines: no paper passage (the paper has no learned component); input transfer.
  * Set the 16-channel BF16 input directly (device pointer, N*16 bf16). */
 mp_status mp_net_set_input(mp_net_handle net, const void *x16_dev);

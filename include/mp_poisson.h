@@ -370,6 +370,26 @@ mp_status mp_poisson_get_profile(mp_handle hd, mp_kernel_prof *out, int cap, int
 mp_status mp_poisson_rhs_noalloc(long long ncells, const double *rhs_dev, const double *J_dev,
                                  double *b_dev, void *stream);
 
+/*
+ * Defines: no paper passage (the paper has no learned component); the training loss
+ * of a learned initial guess for the deflated solver.
+ *
+ * Deflated CG corrects any start exactly along the gas components' indicator vectors
+ * Z, so what it inherits from a guess is the error in the deflated energy
+ * ||e||_D^2 = e^T D e with D = A - A Z E^-1 Z^T A, E = Z^T A Z (the A-energy left after
+ * the best correction along Z).  For the network output q and the target t (device
+ * FP32, N each; t a multiple of the solution) this returns the relative D-energy
+ * error of the best multiple of q,
+ *   L = 1 - (q.D t)^2 / ((q.D q)(t.D t)),
+ * in loss_out (host) and, when gq_dev (device FP32, N) is not NULL, its gradient
+ * dL/dq = -2 (q.Dt)/((q.Dq)(t.Dt)) D t + 2 (q.Dt)^2/((q.Dq)^2 (t.Dt)) D q.  A and Z are
+ * the current geometry's (FP64).  MP_ERR_INVALID_ARG when the handle has no deflation
+ * vectors (deflate off, no gas, or an outflow side); MP_ERR_DIVERGED when q or t has no
+ * deflated energy.  Uses the handle's solver scratch (not during a solve).
+ */
+mp_status mp_poisson_deflated_energy(mp_handle hd, const float *q_dev, const float *t_dev,
+                                     float *gq_dev, double *loss_out);
+
 /* Defines: no paper passage (resource release).
  * Free everything the handle owns.  NULL is ignored. */
 void mp_poisson_destroy(mp_handle hd);

@@ -23,6 +23,7 @@ from .poisson import (  # noqa: F401
     mp_poisson_rhs_noalloc,
     mp_poisson_set_geometry,
     mp_poisson_set_mass_flux,
+    mp_poisson_deflated_energy,
     mp_poisson_set_opts,
     mp_poisson_set_profiling,
     mp_poisson_setup,

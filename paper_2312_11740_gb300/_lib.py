@@ -92,6 +92,7 @@ SIGNATURES = {
                               ctypes.POINTER(mp_opts)]),
     "mp_poisson_set_geometry": (_I, [_P, _P, _D, _D, _D]),
     "mp_poisson_set_mass_flux": (_I, [_P, _P]),
+    "mp_poisson_deflated_energy": (_I, [_P, _P, _P, _P, _DP]),
     "mp_poisson_set_opts": (_I, [_P, ctypes.POINTER(mp_opts)]),
     "mp_poisson_solve": (_I, [_P, _P, _P, _D, _IP, _DP, _I, _IP]),
     "mp_poisson_project_step": (_I, [_P, _P, _P, _P, _P, _D, _IP]),
@@ -115,6 +116,7 @@ SIGNATURES = {
     "mp_net_param_count": (ctypes.c_size_t, [_P]),
     "mp_net_launches": (ctypes.c_ulonglong, [_P]),
     "mp_net_set_params": (_I, [_P, _P]),
+    "mp_net_train_step_grad": (_I, [_P, _P, ctypes.c_float, _I]),
     "mp_net_get_adam": (_I, [_P, _P, _P]),
     "mp_net_set_adam": (_I, [_P, _P, _P]),
     "mp_net_get_params": (_I, [_P, _P]),

@@ -1234,6 +1234,21 @@ __global__ void k_add_f32(double *__restrict__ x, float *__restrict__ e, size_t 
   }
 }
 
+// y = (double) x
+__global__ void k_f32_to_f64(const float *__restrict__ x, double *__restrict__ y, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    y[k] = (double)x[k];
+}
+
+// g = fl32(a u + b v)
+__global__ void k_lincomb_f32(float *__restrict__ g, double a, const double *__restrict__ u,
+                              double b, const double *__restrict__ v, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    g[k] = (float)fma(a, u[k], b * v[k]);
+}
+
 // dst32 = fl32(src64), per-block partial of src.src (FP64)
 __global__ void k_to_f32_norm(const double *__restrict__ src, float *__restrict__ dst, size_t n,
                               double *__restrict__ partial) {

@@ -1813,6 +1813,22 @@ mp_status mp_net_train_step(mp_net_handle net, const float *target, float lr, in
   return MP_OK;
 }
 
+mp_status mp_net_train_step_grad(mp_net_handle net, const float *gq, float lr, int step) {
+  if (!net || !gq || step < 1 || !(lr > 0.f)) return MP_ERR_INVALID_ARG;
+  NCKS(forward(net));
+  NCK(cudaMemcpyAsync(net->gq, gq, net->nv[0] * sizeof(float), cudaMemcpyDeviceToDevice,
+                      net->st));
+  NCKS(backward(net));
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);
+  k_adam<<<grid_for(net->nparam), 256, 0, net->st>>>(net->param, net->grad, net->adam_m,
+                                                     net->adam_v, net->nparam, lr, b1, b2, 1e-8f,
+                                                     c1, c2);
+  NCKS(pack_all(net));
+  NCK(cudaStreamSynchronize(net->st));
+  return check_err(net);
+}
+
 mp_status mp_net_test_wait_timeout(int n) {
   if (n < 0) return MP_ERR_INVALID_ARG;
   g_wait_failures.store(n);

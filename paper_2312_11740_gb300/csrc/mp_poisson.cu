@@ -1517,6 +1517,26 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
   return MP_OK;
 }
 
+// D v = At v - At Z E^-1 Z^T At v (the deflated operator) of FP64 v (device,
+// hd->n), into out; v and out distinct handle scratch vectors
+mp_status deflated_apply(mp_poisson *hd, double *v, double *out) {
+  Level &l0 = hd->L[0];
+  LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, v, out, l0.bx,
+         l0.by, l0.bz, l0.diag, (const double *)nullptr, l0.d, zper_of(l0.d), hd->partial);
+  CKS(launch_ok());
+  CKS((defl_coef<double, double>(hd, v, l0.bx, l0.by, l0.bz, false)));
+  return defl_sub<double, double>(hd, out, l0.bx, l0.by, l0.bz);
+}
+
+mp_status dot64(mp_poisson *hd, const double *a, const double *b, double *out) {
+  LAUNCH(hd, K_DOT64, 0, hd->n * 16.0, k_dot<double>, VEC_BLOCKS, VEC_THREADS, a, b, hd->n,
+         hd->partial);
+  CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_TMP));
+  CKS(read_scalars(hd));
+  *out = hd->scal_h[S_TMP];
+  return MP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1585,6 +1605,36 @@ mp_status mp_poisson_set_geometry(mp_handle hd, const double *phi_dev, double rh
                                   double sigma) {
   if (!hd) return MP_ERR_INVALID_ARG;
   return geometry(hd, phi_dev, rho_l, rho_g, sigma);
+}
+
+mp_status mp_poisson_deflated_energy(mp_handle hd, const float *q_dev, const float *t_dev,
+                                     float *gq_dev, double *loss_out) {
+  if (!hd || !q_dev || !t_dev || !loss_out) return MP_ERR_INVALID_ARG;
+  if (!hd->opts.deflate || hd->defl_m <= 0 || hd->outflow) return MP_ERR_INVALID_ARG;
+  if ((hd->diag_mode & 1) != 1) CKS(diag_fields(hd, 1));
+  const size_t n = hd->n;
+  CK(cudaMemsetAsync(hd->acc_a, 0, defl_acc_bytes(hd->defl_m), hd->st));
+  CK(cudaMemsetAsync(hd->dmax, 0, sizeof(unsigned long long), hd->st));
+  LAUNCH(hd, K_SCALE, 0, n * 12.0, k_f32_to_f64, VEC_BLOCKS, VEC_THREADS, q_dev, hd->dv, n);
+  LAUNCH(hd, K_SCALE, 0, n * 12.0, k_f32_to_f64, VEC_BLOCKS, VEC_THREADS, t_dev, hd->r, n);
+  CKS(launch_ok());
+  CKS(deflated_apply(hd, hd->dv, hd->q));  // D q
+  CKS(deflated_apply(hd, hd->r, hd->z));   // D t
+  double qdq, qdt, tdt;
+  CKS(dot64(hd, hd->dv, hd->q, &qdq));
+  CKS(dot64(hd, hd->dv, hd->z, &qdt));
+  CKS(dot64(hd, hd->r, hd->z, &tdt));
+  if (!(qdq != 0.0 && tdt != 0.0) || !std::isfinite(qdq * tdt)) return MP_ERR_DIVERGED;
+  *loss_out = 1.0 - qdt * qdt / (qdq * tdt);
+  if (gq_dev) {
+    const double a = -2.0 * qdt / (qdq * tdt), b = 2.0 * qdt * qdt / (qdq * qdq * tdt);
+    LAUNCH(hd, K_SCALE, 0, n * 20.0, k_lincomb_f32, VEC_BLOCKS, VEC_THREADS, gq_dev, a,
+           (const double *)hd->z, b, (const double *)hd->q, n);
+    CKS(launch_ok());
+  }
+  CK(cudaStreamSynchronize(hd->st));
+  prof_resolve(hd);
+  return MP_OK;
 }
 
 mp_status mp_poisson_set_mass_flux(mp_handle hd, const double *mdot_dev) {

@@ -141,15 +141,23 @@ def load_checkpoint(path, net, device="cuda"):
 
 
 def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None, loss="energy",
-          checkpoint=None, resume=None, device="cuda"):
+          checkpoint=None, resume=None, device="cuda", phi_of=None, n=None):
     """Adam over shuffled samples; returns the loss history (one per step).
     checkpoint: path written after every epoch; resume: a checkpoint of the
-    same run (same samples, epochs, schedule and seed) to continue from."""
+    same run (same samples, epochs, schedule and seed) to continue from.
+    loss "energy_deflated": the deflated energy of the guess
+    (mp_poisson_deflated_energy) on each sample's geometry, phi_of(k) giving
+    sample k's level set on the device (n^3 grid); the gradient it returns
+    drives mp_net_train_step_grad."""
     rng = np.random.Generator(np.random.PCG64(seed))
     count = X.shape[0]
     config = dict(count=int(count), epochs=int(epochs), lr=float(lr), seed=int(seed),
                   lr_final=None if lr_final is None else float(lr_final), loss=loss)
-    net.set_loss(1 if loss == "energy" else 0, RHO_L, RHO_G, BC)
+    solver = None
+    if loss == "energy_deflated":
+        solver = Poisson(phi_of(0), 1.0 / n, BC, RHO_L, RHO_G, SIGMA, precision=0)
+    else:
+        net.set_loss(1 if loss == "energy" else 0, RHO_L, RHO_G, BC)
     losses = []
     step, first = 0, 0
     if resume:
@@ -165,12 +173,20 @@ def train(net, X, Q, epochs, lr, seed, log=print, lr_final=None, loss="energy",
             step += 1
             cur = lr if lr_final is None else lr * (lr_final / lr) ** (step / total)
             net.set_input2(X[k])
-            losses.append(net.train_step(Q[k], cur, step))
+            if solver is None:
+                losses.append(net.train_step(Q[k], cur, step))
+            else:
+                solver.set_geometry(phi_of(int(k)), RHO_L, RHO_G, SIGMA)
+                L, gq = solver.deflated_energy(net.forward(), Q[k])
+                net.train_step_grad(gq, cur, step)
+                losses.append(L)
         if log:
             log("  epoch %d  mean loss %.4e  %.1fs" % (ep + 1, float(np.mean(losses[-count:])),
                                                        time.time() - t0))
         if checkpoint:
             save_checkpoint(checkpoint, net, step, ep + 1, rng, losses, config)
+    if solver is not None:
+        solver.close()
     return losses
 
 
@@ -301,7 +317,9 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lr-final", type=float, default=1e-4)
     ap.add_argument("--init-seed", type=int, default=7)
-    ap.add_argument("--loss", choices=("energy", "mse"), default="energy")
+    ap.add_argument("--loss", choices=("energy", "mse", "energy_deflated"), default="energy")
+    ap.add_argument("--init-from", default=None,
+                    help="start from these weights (.npz) instead of random initialisation")
     ap.add_argument("--deflate", type=int, choices=(0, 1), default=0,
                     help="solver form the evaluation compares against (0: plain MG-PCG)")
     ap.add_argument("--out", default=None)
@@ -316,11 +334,20 @@ def main(argv=None):
     X, Q, its = make_dataset(list(range(a.train_seed0, a.train_seed0 + a.train)), n)
     t_data = time.time() - t0
     net = Net(n, n, n)
-    net.set_params(init_params(net, a.init_seed))
+    if a.init_from:
+        net.load(a.init_from)
+    else:
+        net.set_params(init_params(net, a.init_seed))
+    seeds = list(range(a.train_seed0, a.train_seed0 + a.train))
+    dev = torch.device("cuda")
+
+    def phi_of(k):
+        return geometry(seeds[k], n, dev)[0]
+
     print("train: %d epochs" % a.epochs, flush=True)
     t1 = time.time()
     losses = train(net, X, Q, a.epochs, a.lr, a.init_seed, lr_final=a.lr_final, loss=a.loss,
-                   checkpoint=a.checkpoint, resume=a.resume)
+                   checkpoint=a.checkpoint, resume=a.resume, phi_of=phi_of, n=n)
     t_train = time.time() - t1
     del X, Q
     torch.cuda.empty_cache()

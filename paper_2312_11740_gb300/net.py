@@ -195,6 +195,12 @@ class Net:
                "mp_net_train_step")
         return loss.value
 
+    def train_step_grad(self, gq, lr, step):
+        """One Adam step from an externally formed gradient dL/dq (FP32, device)."""
+        _check(_lib_().mp_net_train_step_grad(self.handle, _ptr(gq, torch.float32, self.n),
+                                              ctypes.c_float(lr), int(step)),
+               "mp_net_train_step_grad")
+
     def close(self):
         if getattr(self, "handle", None):
             _lib_().mp_net_destroy(self.handle)

@@ -89,6 +89,18 @@ def mp_poisson_set_mass_flux(handle, mdot):
     return _check(_lib_().mp_poisson_set_mass_flux(handle, ptr), "mp_poisson_set_mass_flux")
 
 
+def mp_poisson_deflated_energy(handle, q, t, gq=None):
+    """Deflated energy loss of q against t (FP32 device tensors) and, into gq, its
+    gradient; returns the loss."""
+    loss = ctypes.c_double(0.0)
+    n = q.numel()
+    _check(_lib_().mp_poisson_deflated_energy(
+        handle, _ptr(q, torch.float32), _ptr(t, torch.float32, n),
+        None if gq is None else _ptr(gq, torch.float32, n), ctypes.byref(loss)),
+        "mp_poisson_deflated_energy")
+    return loss.value
+
+
 def mp_poisson_set_opts(handle, opts):
     return _check(_lib_().mp_poisson_set_opts(handle, ctypes.byref(opts)), "mp_poisson_set_opts")
 
@@ -214,6 +226,12 @@ class Poisson:
 
     def set_geometry(self, phi, rho_l, rho_g, sigma):
         mp_poisson_set_geometry(self.handle, phi.contiguous(), rho_l, rho_g, sigma)
+
+    def deflated_energy(self, q, t, grad=True):
+        """(loss, dL/dq) of the deflated energy loss (mp_poisson_deflated_energy)."""
+        gq = torch.empty_like(q) if grad else None
+        loss = mp_poisson_deflated_energy(self.handle, q.contiguous(), t.contiguous(), gq)
+        return loss, gq
 
     def set_mass_flux(self, mdot):
         if mdot is not None and tuple(mdot.shape) != tuple(self.shape):

@@ -622,3 +622,52 @@ def test_conv_wait_timeout_is_reported_and_the_network_stays_usable():
     q = net.forward()
     assert torch.equal(q, q_ref)
     net.close()
+
+
+@pytest.mark.parametrize("name", ["bubble32", "ragged"])
+def test_deflated_energy_loss_matches_oracle(name):
+    """mp_poisson_deflated_energy (the training loss for the deflated solver,
+    FP64 on the solver's operator, components and band kernels) against the
+    oracle's dense-E formulation: loss to 1e-9, gradient to 1e-5 of its
+    largest entry; and the loss is blind to adding the component indicators."""
+    import oracle
+    from oracle import conv as oconv
+    from test_gpu_parity import case, make
+    phi, u, prm = case(name)
+    h, bc = prm["h"], prm["bc"]
+    s = make(phi, prm)
+    g = np.random.Generator(np.random.PCG64(4))
+    t = g.standard_normal(phi.shape)
+    q = t + 0.5 * g.standard_normal(phi.shape)
+    qd = torch.from_numpy(q.astype(np.float32)).cuda()
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    L, gq = s.deflated_energy(qd, td)
+    Lo, go = oconv.deflated_energy_loss(qd.cpu().double().numpy(), td.cpu().double().numpy(),
+                                        phi, h, prm["rho_l"], prm["rho_g"], bc)
+    assert s.stats()["components"] >= 0
+    assert L == pytest.approx(Lo, rel=1e-9)
+    gq = gq.cpu().double().numpy()
+    assert np.abs(gq - go).max() <= 1e-5 * np.abs(go).max()
+    comp, m = s.components()
+    assert m >= 1
+    shifted = qd + sum(float(c) * (comp == j).to(torch.float32)
+                       for j, c in enumerate(np.linspace(-2.0, 3.0, m)))
+    L2, _ = s.deflated_energy(shifted.contiguous(), td, grad=False)
+    assert L2 == pytest.approx(L, rel=1e-5)
+    s.close()
+
+
+def test_train_step_from_an_external_gradient_equals_the_fused_step():
+    """mp_net_train_step_grad (the Adam step of the deflated-energy training,
+    whose loss is formed outside the network) given the energy loss's own
+    gradient makes the same update as mp_net_train_step, bit for bit."""
+    a, _, _, _ = _energy_setup(seed=21)
+    b, _, _, _ = _energy_setup(seed=21)
+    t = torch.from_numpy(rng(22).standard_normal((32, 32, 32)).astype(np.float32)).cuda()
+    for step in (1, 2):
+        _, gq = b.loss_grad(t)
+        b.train_step_grad(gq, 1e-3, step)
+        a.train_step(t, 1e-3, step)
+        assert torch.equal(a.get_params(), b.get_params()), step
+    a.close()
+    b.close()
