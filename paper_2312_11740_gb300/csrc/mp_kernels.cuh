@@ -998,11 +998,35 @@ __global__ void k_apply_dot(const T *__restrict__ dv, T *__restrict__ q, const T
 
 // q = At d (FP32 difference form, op_at's arithmetic per cell) and per-block
 // partials of d.q, with 16-byte rows (nx a multiple of 4): a thread owns a
-// 4-cell x-chunk in each of its zper planes and loads it as vectors
+// 4-cell x-chunk in each of its zper planes and loads it as vectors.
+// XPBY: the CG direction update d = z + beta d (k_xpby's operation, d = z on
+// the first iteration) fused in: every value of d the stencil needs is formed
+// from z and the old direction dv, and the thread's own chunk of the new
+// direction is stored to dnew (a second buffer: other blocks still read dv).
+__device__ __forceinline__ float4 xpby4(const float *__restrict__ z, const float *__restrict__ d,
+                                        size_t c, float beta, int first) {
+  const float4 zz = *reinterpret_cast<const float4 *>(z + c);
+  if (first) return zz;
+  const float4 dd = *reinterpret_cast<const float4 *>(d + c);
+  return make_float4(fmaf(beta, dd.x, zz.x), fmaf(beta, dd.y, zz.y), fmaf(beta, dd.z, zz.z),
+                     fmaf(beta, dd.w, zz.w));
+}
+template <bool XPBY>
 __global__ void __launch_bounds__(BX * BY)
 k_apply_dot4(const float *__restrict__ dv, float *__restrict__ q, const float *__restrict__ bx,
              const float *__restrict__ by, const float *__restrict__ bz,
-             const float *__restrict__ dd32, Dims d, int zper, double *__restrict__ partial) {
+             const float *__restrict__ dd32, Dims d, int zper, double *__restrict__ partial,
+             const float *__restrict__ z, float *__restrict__ dnew,
+             const double *__restrict__ scal, int first) {
+  const float beta = XPBY && !first ? (float)scal[S_BETA] : 0.f;
+  auto ld4 = [&](size_t c) -> float4 {
+    if (XPBY) return xpby4(z, dv, c, beta, first);
+    return *reinterpret_cast<const float4 *>(dv + c);
+  };
+  auto ld1 = [&](size_t c) -> float {
+    if (XPBY) return first ? z[c] : fmaf(beta, dv[c], z[c]);
+    return dv[c];
+  };
   const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   const int k0 = blockIdx.z * zper, k1 = min(d.nz, k0 + zper);
   float acc = 0.f;
@@ -1013,17 +1037,15 @@ k_apply_dot4(const float *__restrict__ dv, float *__restrict__ q, const float *_
       const size_t cyl = at(d, i0, wlo(j, d.ny), k), cyh = at(d, i0, whi(j, d.ny), k);
       const size_t czl = at(d, i0, j, wlo(k, d.nz)), czh = at(d, i0, j, whi(k, d.nz));
       const size_t ce = at(d, whi(i0 + 3, d.nx), j, k);
-      const float4 xc = *reinterpret_cast<const float4 *>(dv + c0);
-      const float4 xyl = *reinterpret_cast<const float4 *>(dv + cyl);
-      const float4 xyh = *reinterpret_cast<const float4 *>(dv + cyh);
-      const float4 xzl = *reinterpret_cast<const float4 *>(dv + czl);
-      const float4 xzh = *reinterpret_cast<const float4 *>(dv + czh);
+      const float4 xc = ld4(c0);
+      const float4 xyl = ld4(cyl), xyh = ld4(cyh), xzl = ld4(czl), xzh = ld4(czh);
+      if (XPBY) *reinterpret_cast<float4 *>(dnew + c0) = xc;
       const float4 fx = *reinterpret_cast<const float4 *>(bx + c0);
       const float4 fy = *reinterpret_cast<const float4 *>(by + c0);
       const float4 fyh = *reinterpret_cast<const float4 *>(by + cyh);
       const float4 fz = *reinterpret_cast<const float4 *>(bz + c0);
       const float4 fzh = *reinterpret_cast<const float4 *>(bz + czh);
-      const float fxe = bx[ce], xp = dv[ce], xm = dv[at(d, wlo(i0, d.nx), j, k)];
+      const float fxe = bx[ce], xp = ld1(ce), xm = ld1(at(d, wlo(i0, d.nx), j, k));
       float4 out;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {

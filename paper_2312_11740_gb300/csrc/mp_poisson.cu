@@ -100,6 +100,7 @@ struct mp_poisson {
   double *r = nullptr, *z = nullptr, *dv = nullptr, *q = nullptr;
   // fine-level FP32 inner-solve vectors
   float *r32 = nullptr, *e32 = nullptr, *z32 = nullptr, *d32 = nullptr, *q32 = nullptr;
+  float *d32b = nullptr;  // second direction buffer (fused direction update + operator)
   // host-buffer step staging
   double *ux = nullptr, *uy = nullptr, *uz = nullptr, *pst = nullptr;
   // coarsest level
@@ -891,14 +892,20 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
       LAUNCH(hd, K_DOT32, 0, 2.0 * nsz, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, z, n,
              hd->partial);
     CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
-    LAUNCH(hd, K_XPBY32, 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<float>, VEC_BLOCKS, VEC_THREADS,
-           dv, z, n, hd->scal, it == 0);
-    if (l0.d.nx % 4 == 0) {  // 16-byte rows
+    const bool fused = l0.d.nx % 4 == 0;  // 16-byte rows
+    if (fused) {
+      // d_new = z + beta d in the operator's loads, stored to the other buffer
       const Dims dq = chunk_dims(l0.d);
-      LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot4, zgrid(dq), kBlock, dv, q, l0.bx32,
-             l0.by32, l0.bz32, (const float *)l0.dd32, l0.d, zper_of(dq), hd->partial);
+      float *dnew = dv == hd->d32 ? hd->d32b : hd->d32;
+      LAUNCH(hd, K_APPLY32, 0, (it == 0 ? 6.0 : 7.0) * nsz, k_apply_dot4<true>, zgrid(dq), kBlock,
+             (const float *)dv, q, l0.bx32, l0.by32, l0.bz32, (const float *)l0.dd32, l0.d,
+             zper_of(dq), hd->partial, (const float *)z, dnew, (const double *)hd->scal,
+             it == 0 ? 1 : 0);
       CKS(reduce(hd, zblocks(dq), OP_ALPHA, 0));
+      dv = dnew;
     } else {
+      LAUNCH(hd, K_XPBY32, 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<float>, VEC_BLOCKS, VEC_THREADS,
+             dv, z, n, hd->scal, it == 0);
       LAUNCH(hd, K_APPLY32, 0, 5.0 * nsz, k_apply_dot<float>, zgrid(l0.d), kBlock, dv, q,
              l0.bx32, l0.by32, l0.bz32, (float *)nullptr, (const float *)l0.dd32, l0.d,
              zper_of(l0.d), hd->partial);
@@ -1053,8 +1060,10 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
       LAUNCH(hd, K_RESIDMIX, 0, hd->n * 12.0, k_to_f32_norm, VEC_BLOCKS, VEC_THREADS, p, hd->z32,
              hd->n, hd->partial);
       const Dims dq = chunk_dims(l0.d);
-      LAUNCH(hd, K_APPLY32, 0, hd->n * 20.0, k_apply_dot4, zgrid(dq), kBlock, hd->z32, hd->q32,
-             l0.bx32, l0.by32, l0.bz32, (const float *)l0.dd32, l0.d, zper_of(dq), hd->partial);
+      LAUNCH(hd, K_APPLY32, 0, hd->n * 20.0, k_apply_dot4<false>, zgrid(dq), kBlock,
+             (const float *)hd->z32, hd->q32, l0.bx32, l0.by32, l0.bz32, (const float *)l0.dd32,
+             l0.d, zper_of(dq), hd->partial, (const float *)nullptr, (float *)nullptr,
+             (const double *)nullptr, 0);
       CKS(reduce(hd, zblocks(dq), OP_STORE, S_TMP));
     } else {
       LAUNCH(hd, K_APPLY64, 0, hd->n * 48.0, k_apply_dot<double>, zgrid(l0.d), kBlock, p, hd->q,
@@ -1441,6 +1450,7 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
   CKS(dalloc(hd, &hd->e32, n));
   CKS(dalloc(hd, &hd->z32, n));
   CKS(dalloc(hd, &hd->d32, n));
+  CKS(dalloc(hd, &hd->d32b, n));
   CKS(dalloc(hd, &hd->q32, n));
   CKS(dalloc(hd, &hd->ux, n));
   CKS(dalloc(hd, &hd->uy, n));
