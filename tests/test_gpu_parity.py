@@ -753,3 +753,54 @@ def test_cluster_tail_matches_per_level_launches(name):
                            prm["sigma"], bc, tol=REF_TOL)
         for cl in (1, 0):
             assert rel_l2(out[cl][1], ref["p"]) < PARITY
+
+
+def test_all_gas_and_all_liquid_domains():
+    """A domain that is one gas component (its indicator is the operator's
+    null space, so its E entry is zero and the component is left out of the
+    deflation) and an all-liquid domain (no components): both solve to the
+    oracle's pressure, FP64 and mixed, with and without deflation."""
+    shape, h = (24, 16, 32), 1.0 / 32
+    bc = (P, P, N)
+    g = np.random.Generator(np.random.PCG64(8))
+    rhs = g.standard_normal(shape)
+    for sign in (1.0, -1.0):
+        phi = sign * (0.5 + g.random(shape))  # gas everywhere / liquid everywhere
+        prm = dict(h=h, rho_l=1.0, rho_g=1e-3, sigma=0.05, bc=bc)
+        ref = oracle.solve(phi, rhs, h, 1.0, 1e-3, 0.05, bc, tol=REF_TOL)
+        for precision in (0, 1):
+            for deflate in (1, 0):
+                s = make(phi, prm, precision=precision, deflate=deflate)
+                p, _, _ = s.solve(dev(rhs), tol=TOL)
+                assert s.stats()["relres"] <= TOL
+                assert rel_l2(host(p), ref["p"]) < PARITY, (sign, precision, deflate)
+                s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_outflow_mass_flux_properties(precision):
+    """256^3 pool + 32 bubbles under an outflow top with an evaporating mass
+    flux (the bench geometry with the paper's outflow and phase-change
+    options): the oracle's own assembly (flux-jump source included) and
+    operator confirm the GPU pressure solves its system to the target; the
+    jump source agrees at sampled cells."""
+    phi, u, prm = synth.workload("pool256")
+    h = prm["h"]
+    bc = (P, P, oracle.NEUMANN_DIRICHLET)
+    nz, ny, nx = phi.shape
+    z = (np.arange(nz) + 0.5)[:, None, None] * h
+    md = np.ascontiguousarray(np.broadcast_to(0.02 * (1.0 + z), phi.shape))
+    rhs = oracle.divergence(*u, h)
+    prm = dict(prm, bc=bc)
+    kap, f, J, b = oracle.assemble(phi, rhs, h, prm["rho_l"], prm["rho_g"], prm["sigma"], bc,
+                                   mdot=md)
+    s = make(phi, prm, precision=precision)
+    s.set_mass_flux(dev(md))
+    p, it, _ = s.solve(dev(rhs), tol=TOL)
+    _, rn = oracle.residual(f, b, host(p), h, bc)
+    assert rn / np.linalg.norm(b) <= 1.5 * TOL
+    idx = np.flatnonzero(band(phi, bc).ravel())
+    idx = idx[np.random.Generator(np.random.PCG64(5)).integers(0, idx.size, 4096)]
+    got = host(s.fields()["J"]).ravel()[idx]
+    assert np.max(np.abs(got - J.ravel()[idx])) <= 1e-11 * np.abs(J).max()
+    s.close()
