@@ -124,9 +124,12 @@ __device__ void ct_unite(int *L, int a, int b, int *err, int limit) {
   atomicExch(err, 1);
 }
 
+// (troots: every tile root's cell index, the first cap of them; *ntroots
+// counts all)
 __global__ void __launch_bounds__(CT_THREADS) k_ccl_tile(const double *__restrict__ phi,
                                                          int *__restrict__ lab, Dims d, int *err,
-                                                         int limit) {
+                                                         int limit, int *__restrict__ troots,
+                                                         int *ntroots, int cap) {
   __shared__ int L[CT_CELLS];
   const int tx = blockIdx.x * CT_X, ty = blockIdx.y * CT_Y, tz = blockIdx.z * CT_Z;
   // local index li = x + CT_X (y + CT_Y z); cells outside the grid are liquid
@@ -151,6 +154,10 @@ __global__ void __launch_bounds__(CT_THREADS) k_ccl_tile(const double *__restric
     if (L[li] >= 0) {
       const int r = ct_find(L, li, err, limit);
       v = (int)at(d, tx + r % CT_X, ty + (r / CT_X) % CT_Y, tz + r / (CT_X * CT_Y));
+      if (r == li) {
+        const int q = atomicAdd(ntroots, 1);
+        if (q < cap) troots[q] = v;
+      }
     }
     lab[at(d, x, y, z)] = v;
   }
@@ -190,7 +197,38 @@ __global__ void __launch_bounds__(CT_THREADS) k_ccl_faces(int *lab, Dims d, int 
 
 // lab[c] <- root of c for every gas cell; every root appends its index to
 // roots (first DEFL_MAX of them; *nroots counts all)
-__global__ void k_ccl_flatten(int *lab, size_t n, int *err, int *roots, int *nroots, int limit) {
+//
+// Two passes when every tile root is listed (*ntroots <= cap): the tile roots
+// find their roots first (k_ccl_flatten_roots), then every cell takes one
+// hop -- after the tile pass each cell points at its tile root, and the
+// unions and path halving only ever re-point a cell at another tile root, so
+// lab[lab[c]] is c's root.  Otherwise every cell walks to its root.
+__global__ void k_ccl_flatten_roots(int *lab, const int *__restrict__ troots,
+                                    const int *__restrict__ ntroots, int cap, int *err,
+                                    int *roots, int *nroots, int limit) {
+  const int nt = *ntroots;
+  if (nt > cap) return;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x) {
+    const int t = troots[q];
+    const int r = ccl_find(lab, t, err, limit);
+    lab[t] = r;
+    if (r == t) {
+      const int w = atomicAdd(nroots, 1);
+      if (w < DEFL_MAX) roots[w] = r;
+    }
+  }
+}
+
+__global__ void k_ccl_flatten(int *lab, size_t n, int *err, int *roots, int *nroots, int limit,
+                              const int *__restrict__ ntroots, int cap) {
+  if (*ntroots <= cap) {
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x) {
+      const int p = lab[c];
+      if (p >= 0) lab[c] = lab[p];
+    }
+    return;
+  }
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
     if (lab[c] < 0) continue;

@@ -114,6 +114,8 @@ struct mp_poisson {
   // deflation by the gas components (mp_deflate.cuh)
   int *lab = nullptr, *comp = nullptr, *band = nullptr, *cnt = nullptr, *dint = nullptr;
   int *roots = nullptr;
+  int *troots = nullptr;  // tile roots of the labelling (up to tcap)
+  int tcap = 0;
   unsigned char *bflag = nullptr;  // band flag per cell (compaction)
   int defl_m = 0, defl_nband = 0;
   double beta_max = 1.0, ztb_scale = 1.0;
@@ -597,11 +599,14 @@ mp_status deflation_setup(mp_poisson *hd) {
                      (l0.d.nz + CT_Z - 1) / CT_Z);
   const int lim = hd->opts.label_limit;
   LAUNCH(hd, K_DEFL_LABEL, 0, n * 12.0, k_ccl_tile, ct_grid, CT_THREADS, hd->phi, hd->lab, l0.d,
-         hd->dint + 2, lim);
+         hd->dint + 2, lim, hd->troots, hd->dint + 3, hd->tcap);
   LAUNCH(hd, K_DEFL_LABEL, 0, n * 4.0, k_ccl_faces, ct_grid, CT_THREADS, hd->lab, l0.d, hd->per,
          hd->dint + 2, lim);
+  LAUNCH(hd, K_DEFL_LABEL, 0, hd->tcap * 8.0, k_ccl_flatten_roots, VEC_BLOCKS, VEC_THREADS, hd->lab,
+         (const int *)hd->troots, (const int *)(hd->dint + 3), hd->tcap, hd->dint + 2, hd->roots,
+         hd->dint, lim);
   LAUNCH(hd, K_DEFL_LABEL, 0, n * 8.0, k_ccl_flatten, VEC_BLOCKS, VEC_THREADS, hd->lab, n, hd->dint + 2,
-         hd->roots, hd->dint, lim);
+         hd->roots, hd->dint, lim, (const int *)(hd->dint + 3), hd->tcap);
   LAUNCH(hd, K_DEFL_LABEL, 0, DEFL_MAX * 8.0, k_rank_roots, 1, 1024, hd->roots, hd->dint, hd->comp);
   LAUNCH(hd, K_DEFL_LABEL, 0, n * 12.0, k_comp_from_roots, VEC_BLOCKS, VEC_THREADS, hd->lab, hd->comp,
          n);
@@ -1472,6 +1477,8 @@ mp_status create(mp_poisson *hd, mp_grid g, double h, const mp_bc bc[3]) {
   CKS(dalloc(hd, &hd->lab, n));
   CKS(dalloc(hd, &hd->comp, n));
   CKS(dalloc(hd, &hd->band, n));
+  hd->tcap = (int)std::min<size_t>(n / 64 + 1024, (size_t)1 << 30);
+  CKS(dalloc(hd, &hd->troots, (size_t)hd->tcap));
   CKS(dalloc(hd, &hd->cnt, nblk));
   CKS(dalloc(hd, &hd->dint, 4));
   CKS(dalloc(hd, &hd->roots, (size_t)DEFL_MAX));
