@@ -133,12 +133,30 @@ __global__ void __launch_bounds__(CT_THREADS) k_ccl_tile(const double *__restric
   __shared__ int L[CT_CELLS];
   const int tx = blockIdx.x * CT_X, ty = blockIdx.y * CT_Y, tz = blockIdx.z * CT_Z;
   // local index li = x + CT_X (y + CT_Y z); cells outside the grid are liquid
+  int mine_gas = 1, mine_liq = 1;
   for (int li = threadIdx.x; li < CT_CELLS; li += CT_THREADS) {
     const int x = tx + li % CT_X, y = ty + (li / CT_X) % CT_Y, z = tz + li / (CT_X * CT_Y);
     const bool in = x < d.nx && y < d.ny && z < d.nz;
-    L[li] = in && gas(phi[at(d, x, y, z)]) ? li : -1;
+    const bool g = in && gas(phi[at(d, x, y, z)]);
+    L[li] = g ? li : -1;
+    mine_gas &= g ? 1 : 0;
+    mine_liq &= g ? 0 : 1;
   }
-  __syncthreads();
+  // a tile that is all gas (one component, rooted at its first cell) or all
+  // liquid needs no unions (most tiles of a pool or a large bubble)
+  const int all_gas = __syncthreads_and(mine_gas), all_liq = __syncthreads_and(mine_liq);
+  if (all_gas || all_liq) {
+    const int root = all_gas ? (int)at(d, tx, ty, tz) : -1;
+    for (int li = threadIdx.x; li < CT_CELLS; li += CT_THREADS) {
+      const int x = tx + li % CT_X, y = ty + (li / CT_X) % CT_Y, z = tz + li / (CT_X * CT_Y);
+      if (x < d.nx && y < d.ny && z < d.nz) lab[at(d, x, y, z)] = root;
+    }
+    if (all_gas && threadIdx.x == 0) {
+      const int q = atomicAdd(ntroots, 1);
+      if (q < cap) troots[q] = root;
+    }
+    return;
+  }
   for (int li = threadIdx.x; li < CT_CELLS; li += CT_THREADS) {
     if (L[li] < 0) continue;
     const int lx = li % CT_X, ly = (li / CT_X) % CT_Y, lz = li / (CT_X * CT_Y);
