@@ -85,6 +85,19 @@ def case(name):
         phi = synth.level_set(shape, h, [((0.5, 0.5, 0.25), 0.2)], bc=bc)
         u = synth.velocity(11, shape, h, bc=bc)
         return phi, u, dict(h=h, rho_l=1.0, rho_g=1e-3, sigma=0.03, bc=bc)
+    if name == "wide":  # 128 x 24 x 40: whole 64-cell x tiles; level 1 (ny = 12) overhangs a wall
+        shape, h = (40, 24, 128), 1.0 / 128
+        bc = (P, N, N)
+        bub = [((0.3, 0.09, 0.1), 0.06), ((0.8, 0.1, 0.12), 0.05)]
+        phi = synth.level_set(shape, h, bub, pool_z0=0.25, bc=bc)
+        u = synth.velocity(13, shape, h, bc=bc)
+        return phi, u, dict(h=h, rho_l=1.0, rho_g=1e-3, sigma=0.07, bc=bc)
+    if name == "slab":  # 128 x 12 x 16: the finest level's second tile row wraps (periodic y)
+        shape, h = (16, 12, 128), 1.0 / 128
+        bc = (P, P, N)
+        phi = synth.level_set(shape, h, [((0.5, 0.05, 0.06), 0.035)], pool_z0=0.1, bc=bc)
+        u = synth.velocity(15, shape, h, bc=bc)
+        return phi, u, dict(h=h, rho_l=1.0, rho_g=1e-3, sigma=0.07, bc=bc)
     raise KeyError(name)
 
 
@@ -499,7 +512,8 @@ def _pool_case(n, seed=5):
 
 
 @pytest.mark.parametrize("name,opts", [("ragged", {}), ("walls", {}), ("periodic", {}),
-                                       ("bubble32", {"nu1": 3, "nu2": 3}),
+                                       ("bubble32", {"nu1": 3, "nu2": 3}), ("wide", {}),
+                                       ("slab", {}),
                                        ("pool128", {}),
                                        ("pool128", {"deflate": 0, "method": 1, "max_iters": 20})])
 def test_fused_sweep_bitwise_equals_per_colour_launches(name, opts):
@@ -510,7 +524,10 @@ def test_fused_sweep_bitwise_equals_per_colour_launches(name, opts):
     tiles that overhang the grid (nx = 40 < 64, ny = 24 = 3 tiles), wall and
     periodic axes in x, y and z, an odd number of sweeps (the last one per
     colour), a 128^3 pool with many z-chunks per tile, and the stationary
-    V-cycle iteration.  The small grids run without the cluster tail, which
+    V-cycle iteration; both staging modes: tensor copies of the main rows
+    (nx a multiple of 64: pool128; wide, whose level 1 overhangs a wall in
+    y; slab, whose finest level wraps a periodic y) and 16-byte copies (the
+    other grids and the coarser levels).  The small grids run without the cluster tail, which
     would otherwise take every level the fused sweep runs on."""
     if name == "pool128":
         phi, u, prm = _pool_case(128)
