@@ -179,6 +179,15 @@ struct HaloArgs {
   int *err;
 };
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
                "r"(bytes)
@@ -276,32 +285,24 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
                   a.wimg + ((size_t)split * a.nchunk + c) * (size_t)(WB / 2), (uint32_t)WB,
                   &full[buf]);
     }
+    // inputs read through nearest upsampling: one 16-byte cp.async per halo
+    // voxel from its parent voxel, zeros outside the grid; all threads, one
+    // commit group per stage, complete before the stage's barrier
     for (int g = 0; g < 2; ++g) {
       const int cc = 16 * c + 8 * g;
       if (!(a.up_a && cc < a.ca)) continue;
       uint8_t *dst = st + g * HPLANE;
-      for (int v0 = 0; v0 < HVOX; v0 += 4 * CONV_THREADS) {
-        uint4 val[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int v = v0 + u * CONV_THREADS + tid;
-          val[u] = make_uint4(0, 0, 0, 0);
-          if (v < HVOX) {
-            const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
-            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
-            if (gx >= 0 && gy >= 0 && gz >= 0 && gx < a.nx && gy < a.ny && gz < a.nz)
-              val[u] = __ldg(reinterpret_cast<const uint4 *>(
-                  a.xa + (((size_t)(gz >> 1) * any + (gy >> 1)) * anx + (gx >> 1)) * a.ca + cc));
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int v = v0 + u * CONV_THREADS + tid;
-          if (v < HVOX) *reinterpret_cast<uint4 *>(dst + v * 16) = val[u];
-        }
+      for (int v = tid; v < HVOX; v += CONV_THREADS) {
+        const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+        if (gx >= 0 && gy >= 0 && gz >= 0 && gx < a.nx && gy < a.ny && gz < a.nz)
+          cp_async16(dst + v * 16,
+                     a.xa + (((size_t)(gz >> 1) * any + (gy >> 1)) * anx + (gx >> 1)) * a.ca + cc);
+        else
+          *reinterpret_cast<uint4 *>(dst + v * 16) = make_uint4(0, 0, 0, 0);
       }
     }
-    fence_async_smem();
+    cp_async_commit();
   };
 
   auto epilogue = [&](int lt) {
@@ -346,10 +347,22 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
     tc_fence_before();
   };
 
+  // one cp.async group per stage slot: NS - 1 in the prologue and one per
+  // iteration (empty past the last stage), so that stage s's gathers are the
+  // group NS - 2 behind the newest at the top of iteration s
   int produced = 0, waited_full = 0, committed = 0, waited_done = 0;
-  for (; produced < NS - 1 && produced < nst; ++produced) produce(produced);
+  for (int p = 0; p < NS - 1; ++p) {
+    if (produced < nst) {
+      produce(produced);
+      ++produced;
+    } else {
+      cp_async_commit();
+    }
+  }
   for (int s = 0; s < nst; ++s) {
     const int buf = s % NS;
+    cp_async_wait<NS - 2>();  // this thread's gathers of stage s have landed ...
+    fence_async_smem();       // ... and are visible to the tensor core's reads
     // one thread polls the barriers (127 pollers would load the shared-memory
     // pipe that feeds the tensor core); the others wait at the CTA barrier
     if (tid == 0) {
@@ -390,13 +403,18 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
           abort_flag = 1;
       }
       __syncthreads();
-      if (!abort_flag && (s - 1) % a.nchunk == a.nchunk - 1) epilogue((s - 1) / a.nchunk);
     }
+    // refill the buffer of stage s-1 (its MMAs are done) before the epilogue
+    // of the tile stage s-1 ended, so the copies overlap the epilogue
     if (!abort_flag && produced < nst) {
       produce(produced);
       ++produced;
+    } else {
+      cp_async_commit();
     }
+    if (s >= 1 && !abort_flag && (s - 1) % a.nchunk == a.nchunk - 1) epilogue((s - 1) / a.nchunk);
   }
+  cp_async_wait<0>();  // no copy into shared memory outlives the CTA
   if (!abort_flag && nst > 0) {
     if (tid == 0) {
       if (mbar_wait(&done[(nst - 1) % NS], (uint32_t)(((nst - 1) / NS) & 1)))
