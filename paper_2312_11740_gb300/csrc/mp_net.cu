@@ -124,12 +124,18 @@ __host__ __device__ constexpr int conv_smem_bytes() {
 // plane).  For each 16-channel chunk of the input the tile's halo
 // (10 x 18 x (HT_Z + 2) voxels) is staged ONCE in shared memory, as two
 // 8-channel planes laid out [z][y][x][8 ch] (the box order of a 4D TMA
-// load, whose out-of-range fill supplies the zero padding).  Each of the 27
-// taps is then one MMA per plane whose A descriptor starts at the tap's
-// shifted voxel: a core matrix (8 rows x 16 bytes) is 8 x-consecutive
-// voxels, the next core matrix along M is the next y row (stride 10 x 16
-// bytes), the next along K the other 8-channel plane.  The weights of the
-// chunk arrive as one bulk copy of a pre-packed image [t][k/8][co/8][co%8][8].
+// load, whose out-of-range fill supplies the zero padding).  An MMA's A
+// descriptor starts at a shifted voxel of one input plane: a core matrix
+// (8 rows x 16 bytes) is 8 x-consecutive voxels, the next core matrix along
+// M is the next y row (stride 10 x 16 bytes), the next along K the other
+// 8-channel plane.  For an in-plane tap (dy, dx) the shifted input plane zi
+// contributes to output planes zi + 1, zi, zi - 1 through the z-taps -1, 0,
+// +1, and those planes' accumulators are adjacent in TMEM: one MMA with the
+// three z-taps' weights side by side along N (up to 3 NC) covers them, so the
+// 27 taps take 6 MMAs per tap pair instead of 3 x HT_Z, and each A tile is
+// read from shared memory once instead of three times (at NC = 16 the A
+// reads bound the kernel).  The weights of the chunk arrive as one bulk
+// copy of a pre-packed image [dy dx][k/8][z-tap][co/8][co%8][8].
 // A persistent CTA walks its tiles chunk by chunk through an NS-deep ring of
 // stages (TMA -> mbarrier -> MMA issued by one thread -> commit -> refill),
 // with two TMEM accumulator sets so that the epilogue of one tile overlaps
@@ -220,6 +226,10 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
   constexpr int WB = himg_bytes<NC>();
   constexpr int TM = h_tmem_cols<NC>();
   constexpr uint32_t IDESC = idesc_bf16(128, NC, 0, 0);
+  constexpr uint32_t IDESC2 = idesc_bf16(128, 2 * NC, 0, 0);
+  constexpr uint32_t IDESC3 = idesc_bf16(128, 3 * NC, 0, 0);
+  static_assert(3 * NC <= 256 && NC % 16 == 0, "N of the folded z-taps: a multiple of 16, <= 256");
+  static_assert(HT_Z >= 3, "the folded z-taps assume at least three output planes");
   extern __shared__ __align__(1024) uint8_t hsm_raw[];
   uint8_t *sm = hsm_raw + ((1024 - (smem_u32(hsm_raw) & 1023)) & 1023);
   __shared__ __align__(8) uint64_t full[NS], done[NS];
@@ -378,16 +388,36 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
       tc_fence_after();
       const uint32_t hbase = smem_u32(sm + buf * SB), wbase = hbase + HALO_BYTES;
       const uint32_t acc = taddr + (uint32_t)((lt & 1) * HT_Z * NC);
-      const uint64_t a0 = sdesc(hbase, HPLANE, HX * 16), b0 = sdesc(wbase, NC * 16, 128);
+      // B of tap pair p: rows (b, co), b = 0, 1, 2 for dz = +1, 0, -1
+      const uint64_t a0 = sdesc(hbase, HPLANE, HX * 16), b0 = sdesc(wbase, 3 * NC * 16, 128);
+      constexpr uint64_t BLK = (uint64_t)(NC * 16) >> 4;  // one z-tap block of B
 #pragma unroll 1
-      for (int t = 0; t < 27; ++t) {
-        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        const uint64_t db = b0 + (uint64_t)((t * NC * 32) >> 4);
+      for (int p = 0; p < 9; ++p) {
+        const int dy = p / 3, dx = p % 3;
+        const uint64_t db = b0 + (uint64_t)((p * 96 * NC) >> 4);
+        // A of input plane zi (-1 .. HT_Z: the tile's planes and their halo)
+        auto ad = [&](int zi) {
+          return a0 + (uint64_t)(((((zi + 1) * HY + dy) * HX + dx) * 16) >> 4);
+        };
+        if (c == 0 && p == 0) {
+          // first taps of a tile: one output plane per MMA, dz = 0 first
+          // so that each accumulator starts from its own product
 #pragma unroll
-        for (int zp = 0; zp < HT_Z; ++zp) {
-          const uint32_t off = (uint32_t)((((zp + dz) * HY + dy) * HX + dx) * 16);
-          mma_bf16(acc + zp * NC, a0 + (uint64_t)(off >> 4), db, IDESC,
-                   (c > 0 || t > 0) ? 1u : 0u);
+          for (int zo = 0; zo < HT_Z; ++zo) {
+            mma_bf16(acc + zo * NC, ad(zo), db + BLK, IDESC, 0u);
+            mma_bf16(acc + zo * NC, ad(zo - 1), db + 2 * BLK, IDESC, 1u);
+            mma_bf16(acc + zo * NC, ad(zo + 1), db, IDESC, 1u);
+          }
+        } else {
+          // input plane zi feeds output planes zi+1, zi, zi-1 (z-taps -1, 0,
+          // +1), whose accumulators are adjacent: one MMA of N = NC per
+          // output plane it reaches inside the tile
+          mma_bf16(acc, ad(-1), db + 2 * BLK, IDESC, 1u);
+          mma_bf16(acc, ad(0), db + BLK, IDESC2, 1u);
+#pragma unroll
+          for (int zi = 1; zi < HT_Z - 1; ++zi) mma_bf16(acc + (zi - 1) * NC, ad(zi), db, IDESC3, 1u);
+          mma_bf16(acc + (HT_Z - 2) * NC, ad(HT_Z - 1), db, IDESC2, 1u);
+          mma_bf16(acc + (HT_Z - 1) * NC, ad(HT_Z), db, IDESC, 1u);
         }
       }
       mma_commit(&done[buf]);
@@ -437,10 +467,12 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
   if (warp == 0) tmem_free(taddr, TM);
 }
 
-// packed weight image of a convolution for k_conv3d_halo:
-// img[sp][c][t][kg][co/8][co%8][ci%8] = W(co = sp*NC + co_l, t, ci = 16c + 8kg + ci%8)
-// with W(co, t, ci) = src[co][t][ci] (src [cout][27][cin]) or, for the input
-// gradient (flip != 0), W(co, t, ci) = src[ci][26 - t][co] (src [cin'][27][cout'] of the layer).
+// packed weight image of a convolution for k_conv3d_halo, the three z-taps
+// of each in-plane tap pair p = 3 dy + dx side by side along N:
+// img[sp][c][p][kg][b][co/8][co%8][ci%8] = W(co = sp*NC + co_l, t, ci = 16c + 8kg + ci%8)
+// with t = 9 (2 - b) + p (block b holds dz = 1 - b) and W(co, t, ci) =
+// src[co][t][ci] (src [cout][27][cin]) or, for the input gradient
+// (flip != 0), W(co, t, ci) = src[ci][26 - t][co] (src [cin'][27][cout'] of the layer).
 template <typename S>
 __global__ void k_pack_img(const S *__restrict__ src, int cout, int cin, int flip, int nc,
                            bf16 *__restrict__ img) {
@@ -455,10 +487,13 @@ __global__ void k_pack_img(const S *__restrict__ src, int cout, int cin, int fli
     r /= 8;
     const int cog = (int)(r % (nc / 8));
     r /= nc / 8;
+    const int b = (int)(r % 3);
+    r /= 3;
     const int kg = (int)(r % 2);
     r /= 2;
-    const int t = (int)(r % 27);
-    r /= 27;
+    const int p = (int)(r % 9);
+    r /= 9;
+    const int t = 9 * (2 - b) + p;
     const int c = (int)(r % nchunk);
     const int sp = (int)(r / nchunk);
     const int co = sp * nc + cog * 8 + col, ci = 16 * c + 8 * kg + cil;
