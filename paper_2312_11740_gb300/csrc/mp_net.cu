@@ -229,7 +229,7 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
   constexpr uint32_t IDESC2 = idesc_bf16(128, 2 * NC, 0, 0);
   constexpr uint32_t IDESC3 = idesc_bf16(128, 3 * NC, 0, 0);
   static_assert(3 * NC <= 256 && NC % 16 == 0, "N of the folded z-taps: a multiple of 16, <= 256");
-  static_assert(HT_Z >= 3, "the folded z-taps assume at least three output planes");
+  static_assert(HT_Z == 4, "the folded z-tap sequence is written for four output planes");
   extern __shared__ __align__(1024) uint8_t hsm_raw[];
   uint8_t *sm = hsm_raw + ((1024 - (smem_u32(hsm_raw) & 1023)) & 1023);
   __shared__ __align__(8) uint64_t full[NS], done[NS];
@@ -399,26 +399,18 @@ k_conv3d_halo(const __grid_constant__ CUtensorMap map_a, const __grid_constant__
         auto ad = [&](int zi) {
           return a0 + (uint64_t)(((((zi + 1) * HY + dy) * HX + dx) * 16) >> 4);
         };
-        if (c == 0 && p == 0) {
-          // first taps of a tile: one output plane per MMA, dz = 0 first
-          // so that each accumulator starts from its own product
-#pragma unroll
-          for (int zo = 0; zo < HT_Z; ++zo) {
-            mma_bf16(acc + zo * NC, ad(zo), db + BLK, IDESC, 0u);
-            mma_bf16(acc + zo * NC, ad(zo - 1), db + 2 * BLK, IDESC, 1u);
-            mma_bf16(acc + zo * NC, ad(zo + 1), db, IDESC, 1u);
-          }
-        } else {
-          // input plane zi feeds output planes zi+1, zi, zi-1 (z-taps -1, 0,
-          // +1), whose accumulators are adjacent: one MMA of N = NC per
-          // output plane it reaches inside the tile
-          mma_bf16(acc, ad(-1), db + 2 * BLK, IDESC, 1u);
-          mma_bf16(acc, ad(0), db + BLK, IDESC2, 1u);
-#pragma unroll
-          for (int zi = 1; zi < HT_Z - 1; ++zi) mma_bf16(acc + (zi - 1) * NC, ad(zi), db, IDESC3, 1u);
-          mma_bf16(acc + (HT_Z - 2) * NC, ad(HT_Z - 1), db, IDESC2, 1u);
-          mma_bf16(acc + (HT_Z - 1) * NC, ad(HT_Z), db, IDESC, 1u);
-        }
+        // input plane zi feeds output planes zi+1, zi, zi-1 (z-taps -1, 0,
+        // +1), whose accumulators are adjacent: one MMA of N = NC per output
+        // plane it reaches inside the tile.  Planes 1 and 4 come first: they
+        // reach output planes 0-2 and 3, so on a tile's first taps they
+        // overwrite every accumulator before the others add to them
+        const uint32_t keep = (c > 0 || p > 0) ? 1u : 0u;
+        mma_bf16(acc, ad(1), db, IDESC3, keep);
+        mma_bf16(acc + 3 * NC, ad(4), db, IDESC, keep);
+        mma_bf16(acc, ad(-1), db + 2 * BLK, IDESC, 1u);
+        mma_bf16(acc, ad(0), db + BLK, IDESC2, 1u);
+        mma_bf16(acc + NC, ad(2), db, IDESC3, 1u);
+        mma_bf16(acc + 2 * NC, ad(3), db, IDESC2, 1u);
       }
       mma_commit(&done[buf]);
     }
