@@ -845,9 +845,12 @@ mp_status defl_true_residual32(mp_poisson *hd, const double *p, int p_is_zero, d
 // true FP64 residual bt - At p (rounded to FP32).  The search direction is
 // kept across replacements (no restart), so the iteration count stays close
 // to that of FP64 PCG while every stencil sweep moves 4-byte values.
-// On entry r32 holds the true residual of p with norm rn; p_zero: p is zero.
+// On entry r32 holds the true residual of p with norm rn; p_zero: p is zero;
+// r_projected: r32 is already the deflated residual (rn its norm) and Z^T bt
+// is formed.
 mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int maxit, int *iters,
-                    int *outer, std::vector<double> *hist, double inv_b, bool p_zero) {
+                    int *outer, std::vector<double> *hist, double inv_b, bool p_zero,
+                    bool r_projected) {
   Level &l0 = hd->L[0];
   const mp_opts &o = hd->opts;
   const size_t n = hd->n;
@@ -862,7 +865,7 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
   auto project_true = [&](double &rnorm, int p_is_zero) -> mp_status {
     return defl_true_residual32(hd, p, p_is_zero, &rnorm);
   };
-  if (defl) {
+  if (defl && !r_projected) {
     CKS(defl_ztb(hd));
     CKS(project_true(rn, p_zero ? 1 : 0));
   }
@@ -1044,8 +1047,10 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     if (hist) hist->push_back(0.0);
     return MP_OK;
   }
-  // the residual of a learned guess, once formed, is the solve's initial residual
-  bool have_r = false;
+  // the residual of a learned guess, once formed, is the solve's initial
+  // residual; r_projected: r32 and S_RR already hold the deflated residual of
+  // the zero guess (and Z^T bt is formed) after a rejected guess
+  bool have_r = false, r_projected = false;
   if (o.initial_guess == 2) {
     // learned guess: features from phi and the assembled rhs, network output q
     // (the shape), scaled by the energy-optimal alpha = (q . bt) / (q . At q),
@@ -1086,11 +1091,12 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     double rnet = 0.0, rzero = hd->bnorm;
     const bool defl_mixed = defl_active(hd) && o.net_check == 0 && o.precision == 1;
     if (defl_mixed) {
-      // deflated residuals of the zero guess and of the guess (mixed PCG forms
-      // the guess's again at its start when the guess is kept)
+      // deflated residuals of the guess and of the zero guess, the latter
+      // last: a rejected guess leaves r32 = fl32(P bt), the start of the
+      // zero-guess solve (mixed PCG forms a kept guess's again at its start)
       CKS(defl_ztb(hd));
-      CKS(defl_true_residual32(hd, p, 1, &rzero));
       CKS(defl_true_residual32(hd, p, 0, &rnet));
+      CKS(defl_true_residual32(hd, p, 1, &rzero));
     } else {
       if (o.precision == 0)
         LAUNCH(hd, K_RESID64, 0, hd->n * 56.0, k_residual<double>, zgrid(l0.d), kBlock, p, hd->b,
@@ -1112,6 +1118,7 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     } else {
       CK(cudaMemsetAsync(p, 0, hd->n * sizeof(double), hd->st));
       zero = 1;
+      r_projected = defl_mixed && o.method == 0;  // (the stationary iteration is not deflated)
     }
   }
   double inv_b = 1.0 / hd->bnorm;
@@ -1138,7 +1145,7 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     hd->stats.outer_steps = iters;
   } else {
     // FP64 iterative refinement around an FP32 inner solve
-    if (!have_r) {
+    if (!have_r && !r_projected) {
       LAUNCH(hd, K_RESIDMIX, 0, hd->n * (zero ? 12.0 : 52.0), k_residual_mixed, zgrid(l0.d),
              kBlock, p, hd->b, hd->r32, l0.bx, l0.by, l0.bz, l0.diag, l0.d, zper_of(l0.d),
              hd->partial, zero);
@@ -1146,7 +1153,7 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
     }
     CKS(read_scalars(hd));
     double rn = std::sqrt(hd->scal_h[S_RR]);
-    hd->stats.r0 = rn * inv_b;
+    hd->stats.r0 = r_projected ? 1.0 : rn * inv_b;  // the zero guess's residual is bt
     if (hist) hist->push_back(hd->stats.r0);
     int total = 0, outer = 0;
     while (true) {
@@ -1156,7 +1163,8 @@ mp_status solve_assembled(mp_poisson *hd, double *p, double tol, std::vector<dou
       if (o.method == 0) {
         // PCG with reliable updates (replaces the refinement loop)
         int pit = 0, pout = 0;
-        st = pcg_mixed(hd, p, rn, tol_abs, o.max_iters, &pit, &pout, hist, inv_b, zero != 0);
+        st = pcg_mixed(hd, p, rn, tol_abs, o.max_iters, &pit, &pout, hist, inv_b, zero != 0,
+                       r_projected);
         total = pit;
         outer = pout;
         if (st != MP_OK && st != MP_ERR_NOT_CONVERGED && st != MP_ERR_DIVERGED) return st;
