@@ -563,6 +563,37 @@ def test_learned_guess_cannot_pay_against_the_deflated_solver():
         assert r["good_start"] < r["zero"]
 
 
+def test_rejected_guess_leaves_the_mixed_solve_unchanged():
+    """Mixed precision with deflation: after the deflated residual check
+    rejects the learned guess, the solve from zero starts from the zero
+    guess's deflated residual that the check formed (instead of forming it
+    again), so it matches a solve from zero bit for bit: pressure,
+    iterations, final residual and every history entry after the first."""
+    from paper_2312_11740_gb300 import Poisson, learn, mp_poisson_set_net
+    n = 128
+    h = 1.0 / n
+    net = Net(n, n, n)
+    net.load()
+    phi, u, _ = learn.geometry(20000, n, torch.device("cuda"))
+    s = Poisson(phi, h, learn.BC, learn.RHO_L, learn.RHO_G, learn.SIGMA, precision=1)
+    mp_poisson_set_net(s.handle, net)
+    rhs = s.divergence(*u)
+    s.set_opts(initial_guess=0, deflate=1, net_check=0)
+    p0, it0, h0 = s.solve(rhs, tol=1e-10)
+    st0 = s.stats()
+    s.set_opts(initial_guess=2)
+    p2, it2, h2 = s.solve(rhs, tol=1e-10)
+    st2 = s.stats()
+    mp_poisson_set_net(s.handle, None)
+    s.close()
+    net.close()
+    assert st0["components"] > 0
+    assert st2["used_net"] == 0 and st2["net_relres"] > 1.0
+    assert it2 == it0 and st2["relres"] == st0["relres"]
+    assert list(h2[1:]) == list(h0[1:])
+    assert torch.equal(p2, p0)
+
+
 def test_training_resumes_bit_for_bit_from_a_checkpoint(tmp_path, monkeypatch):
     """A two-epoch training run stopped after its first epoch and resumed
     from the checkpoint in a fresh network ends with the same parameters,
