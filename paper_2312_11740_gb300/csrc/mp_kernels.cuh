@@ -1248,9 +1248,26 @@ __global__ void k_add(T *__restrict__ x, const T *__restrict__ y, size_t n) {
 }
 
 // x64 += e32, then e32 = 0 (accumulation of an FP32 correction in FP64)
+// x += (double) e, e = 0: four cells per step (16-byte e, two 16-byte x
+// accesses) when both arrays start 16-byte aligned (x may be a caller's
+// view), then the tail
 __global__ void k_add_f32(double *__restrict__ x, float *__restrict__ e, size_t n) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
-       k += (size_t)gridDim.x * blockDim.x) {
+  const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(e)) & 15) == 0;
+  const size_t n4 = vec ? n / 4 : 0, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += stride) {
+    float4 *ep = reinterpret_cast<float4 *>(e) + q;
+    double2 *xp = reinterpret_cast<double2 *>(x) + 2 * q;
+    const float4 v = *ep;
+    double2 a = xp[0], c = xp[1];
+    a.x += (double)v.x;
+    a.y += (double)v.y;
+    c.x += (double)v.z;
+    c.y += (double)v.w;
+    xp[0] = a;
+    xp[1] = c;
+    *ep = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (size_t k = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += stride) {
     x[k] += (double)e[k];
     e[k] = 0.f;
   }
@@ -1462,8 +1479,14 @@ __global__ void k_bnd_coarsen(const double *__restrict__ fine, double *__restric
 // y = scale * v (used to unscale J and the operator for the test API)
 __global__ void k_scale(const double *__restrict__ v, double *__restrict__ y, size_t n,
                         double scale) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x)
+  // two cells per step when both arrays start 16-byte aligned, then the tail
+  const bool vec = ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
+  const size_t n2 = vec ? n / 2 : 0, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n2; q += stride) {
+    const double2 a = reinterpret_cast<const double2 *>(v)[q];
+    reinterpret_cast<double2 *>(y)[q] = make_double2(a.x * scale, a.y * scale);
+  }
+  for (size_t e = 2 * n2 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride)
     y[e] = v[e] * scale;
 }
 
