@@ -1477,8 +1477,8 @@ __global__ void k_bnd_coarsen(const double *__restrict__ fine, double *__restric
 }
 
 // y = scale * v (used to unscale J and the operator for the test API)
-__global__ void k_scale(const double *__restrict__ v, double *__restrict__ y, size_t n,
-                        double scale) {
+// y = scale v; y may be v (in place), so the pointers are not restrict
+__global__ void k_scale(const double *v, double *y, size_t n, double scale) {
   // two cells per step when both arrays start 16-byte aligned, then the tail
   const bool vec = ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
   const size_t n2 = vec ? n / 2 : 0, stride = (size_t)gridDim.x * blockDim.x;
