@@ -549,6 +549,7 @@ __global__ void k_defl_azt(const int *__restrict__ band, int nband, const int *_
                            const F *__restrict__ bz, Dims d, const T *__restrict__ v,
                            const unsigned long long *__restrict__ mx, double beta_max,
                            unsigned long long *acc, double *scale_out) {
+  griddep_wait();
   const double vmax = __longlong_as_double((long long)*mx);
   const double bound = vmax * 6.0 * beta_max * (double)nband;
   const double scale = bound > 0.0 ? ldexp(1.0, 60) / bound : 1.0;
@@ -609,6 +610,7 @@ __global__ void k_defl_coef(int m, unsigned long long *sa, const double *scale_a
                             const double *scale_b, const double *__restrict__ einv,
                             double *__restrict__ coef, float *__restrict__ coef32,
                             unsigned long long *mx) {
+  griddep_wait();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j == 0) *mx = 0ull;
   if (j >= m) return;
@@ -698,6 +700,7 @@ template <typename T>
 __global__ void __launch_bounds__(VEC_THREADS, 4)
 k_dot_zdefl(const T *__restrict__ r, T *__restrict__ z, const int *__restrict__ comp,
             const T *__restrict__ coef, size_t n, double *__restrict__ partial) {
+  griddep_wait();
   using VT = Vec16<T>;
   using V = typename VT::V;
   constexpr int W = VT::W;

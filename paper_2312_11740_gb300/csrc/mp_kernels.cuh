@@ -1018,6 +1018,7 @@ k_apply_dot4(const float *__restrict__ dv, float *__restrict__ q, const float *_
              const float *__restrict__ dd32, Dims d, int zper, double *__restrict__ partial,
              const float *__restrict__ z, float *__restrict__ dnew,
              const double *__restrict__ scal, int first) {
+  griddep_wait();
   const float beta = XPBY && !first ? (float)scal[S_BETA] : 0.f;
   auto ld4 = [&](size_t c) -> float4 {
     if (XPBY) return xpby4(z, dv, c, beta, first);
@@ -1172,6 +1173,7 @@ __global__ void __launch_bounds__(VEC_THREADS, 4)
 k_axpy2(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ dv,
                         const T *__restrict__ q, size_t n, const double *__restrict__ scal,
                         double *__restrict__ partial) {
+  griddep_wait();
   using VT = Vec16<T>;
   using V = typename VT::V;
   constexpr int W = VT::W;
@@ -1331,6 +1333,7 @@ __global__ void k_sub_mean(double *__restrict__ x, size_t n, const double *__res
 // operation on the device scalars.
 __global__ void k_reduce(const double *__restrict__ partial, int np, double *__restrict__ scal,
                          int op, int slot, double count) {
+  griddep_wait();
   double acc = 0.0;
   for (int e = threadIdx.x; e < np; e += blockDim.x) acc += partial[e];
   double s = block_sum(acc);

@@ -321,6 +321,14 @@ mp_status reduce(mp_poisson *hd, int np, int op, int slot, double count = 0.0) {
   LAUNCH(hd, K_REDUCE, 0, np * 8.0, k_reduce, 1, 1024, hd->partial, np, hd->scal, op, slot, count);
   return launch_ok();
 }
+// the same for a reduction whose predecessor on the stream is the kernel that
+// wrote the partials: launched with programmatic serialization (k_reduce waits
+// for that kernel before reading)
+mp_status reduce_after(mp_poisson *hd, int np, int op, int slot) {
+  LAUNCH_PDL(hd, K_REDUCE, 0, np * 8.0, k_reduce, 1, 1024, 0, (const double *)hd->partial, np,
+             hd->scal, op, slot, 0.0);
+  return launch_ok();
+}
 
 mp_status read_scalars(mp_poisson *hd) {
   CK(cudaMemcpyAsync(hd->scal_h, hd->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
@@ -665,18 +673,21 @@ mp_status defl_coef(mp_poisson *hd, const T *v, const F *bx, const F *by, const 
   unsigned long long *acc = with_ztb ? hd->acc_b : hd->acc_a;
   LAUNCH(hd, K_DEFL, 0, nb * (double)sizeof(T), k_defl_maxabs<T>, VEC_BLOCKS, VEC_THREADS,
          hd->band, nb, v, hd->dmax);
+  // k_defl_azt and k_defl_coef follow the kernel launched just before them:
+  // programmatic serialization (both wait for their predecessor first)
   auto kazt = k_defl_azt<T, F>;
-  LAUNCH(hd, K_DEFL, 0, nb * (7.0 * sizeof(T) + 3.0 * sizeof(F) + 28.0), kazt, VEC_BLOCKS,
-         VEC_THREADS, hd->band, nb, hd->comp, bx, by, bz, l0.d, v, hd->dmax, hd->beta_max, acc,
-         hd->dscale);
+  LAUNCH_PDL(hd, K_DEFL, 0, nb * (7.0 * sizeof(T) + 3.0 * sizeof(F) + 28.0), kazt, VEC_BLOCKS,
+             VEC_THREADS, 0, hd->band, nb, hd->comp, bx, by, bz, l0.d, v,
+             (const unsigned long long *)hd->dmax, hd->beta_max, acc, hd->dscale);
   if (with_ztb)
-    LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, hd->acc_ztb,
-           (const double *)nullptr, hd->ztb_scale, 0, acc, hd->dscale, hd->einv, hd->coef,
-           hd->coef32, hd->dmax);
+    LAUNCH_PDL(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, 0, m, hd->acc_ztb,
+               (const double *)nullptr, hd->ztb_scale, 0, acc, (const double *)hd->dscale,
+               (const double *)hd->einv, hd->coef, hd->coef32, hd->dmax);
   else
-    LAUNCH(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, m, acc, hd->dscale, 0.0, 1,
-           (unsigned long long *)nullptr, (const double *)nullptr, hd->einv, hd->coef, hd->coef32,
-           hd->dmax);
+    LAUNCH_PDL(hd, K_DEFL, 0, m * 16.0, k_defl_coef, (m + 255) / 256, 256, 0, m, acc,
+               (const double *)hd->dscale, 0.0, 1, (unsigned long long *)nullptr,
+               (const double *)nullptr, (const double *)hd->einv, hd->coef, hd->coef32,
+               hd->dmax);
   return launch_ok();
 }
 
@@ -742,8 +753,8 @@ mp_status defl_rz(mp_poisson *hd, const T *r, T *z, const F *bx, const F *by, co
     coef = hd->coef;
   else
     coef = hd->coef32;
-  LAUNCH(hd, K_DEFL_DOT, 0, hd->n * (3.0 * sizeof(T) + 4.0), k_dot_zdefl<T>, VEC_BLOCKS, VEC_THREADS,
-         r, z, hd->comp, coef, hd->n, hd->partial);
+  LAUNCH_PDL(hd, K_DEFL_DOT, 0, hd->n * (3.0 * sizeof(T) + 4.0), k_dot_zdefl<T>, VEC_BLOCKS,
+             VEC_THREADS, 0, r, z, (const int *)hd->comp, coef, hd->n, hd->partial);
   return launch_ok();
 }
 
@@ -899,17 +910,20 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
     else
       LAUNCH(hd, K_DOT32, 0, 2.0 * nsz, k_dot<float>, VEC_BLOCKS, VEC_THREADS, r, z, n,
              hd->partial);
-    CKS(reduce(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
+    // from here to the end of the iteration every launch follows a kernel:
+    // programmatic serialization, each kernel waiting for its predecessor
+    CKS(reduce_after(hd, VEC_BLOCKS, it == 0 ? OP_STORE : OP_BETA, S_RZ));
     const bool fused = l0.d.nx % 4 == 0;  // 16-byte rows
     if (fused) {
       // d_new = z + beta d in the operator's loads, stored to the other buffer
       const Dims dq = chunk_dims(l0.d);
       float *dnew = dv == hd->d32 ? hd->d32b : hd->d32;
-      LAUNCH(hd, K_APPLY32, 0, (it == 0 ? 6.0 : 7.0) * nsz, k_apply_dot4<true>, zgrid(dq), kBlock,
-             (const float *)dv, q, l0.bx32, l0.by32, l0.bz32, (const float *)l0.dd32, l0.d,
-             zper_of(dq), hd->partial, (const float *)z, dnew, (const double *)hd->scal,
-             it == 0 ? 1 : 0);
-      CKS(reduce(hd, zblocks(dq), OP_ALPHA, 0));
+      LAUNCH_PDL(hd, K_APPLY32, 0, (it == 0 ? 6.0 : 7.0) * nsz, k_apply_dot4<true>, zgrid(dq),
+                 kBlock, 0, (const float *)dv, q, (const float *)l0.bx32,
+                 (const float *)l0.by32, (const float *)l0.bz32, (const float *)l0.dd32, l0.d,
+                 zper_of(dq), hd->partial, (const float *)z, dnew, (const double *)hd->scal,
+                 it == 0 ? 1 : 0);
+      CKS(reduce_after(hd, zblocks(dq), OP_ALPHA, 0));
       dv = dnew;
     } else {
       LAUNCH(hd, K_XPBY32, 0, (it == 0 ? 2.0 : 3.0) * nsz, k_xpby<float>, VEC_BLOCKS, VEC_THREADS,
@@ -919,9 +933,9 @@ mp_status pcg_mixed(mp_poisson *hd, double *p, double rn, double tol_abs, int ma
              zper_of(l0.d), hd->partial);
       CKS(reduce(hd, zblocks(l0.d), OP_ALPHA, 0));
     }
-    LAUNCH(hd, K_AXPY32, 0, 6.0 * nsz, k_axpy2<float>, VEC_BLOCKS, VEC_THREADS, e, r, dv, q, n,
-           hd->scal, hd->partial);
-    CKS(reduce(hd, VEC_BLOCKS, OP_STORE, S_RR));
+    LAUNCH_PDL(hd, K_AXPY32, 0, 6.0 * nsz, k_axpy2<float>, VEC_BLOCKS, VEC_THREADS, 0, e, r,
+               (const float *)dv, (const float *)q, n, (const double *)hd->scal, hd->partial);
+    CKS(reduce_after(hd, VEC_BLOCKS, OP_STORE, S_RR));
     ++it;
     ++since;
     CKS(read_scalars(hd));
